@@ -1,0 +1,434 @@
+"""Throughput of the adjoint-wavelet FISTA gradient path on GB300.
+
+One step = one pass of the whole hot path over the 2048 x 2048 workload:
+  * one FISTA iteration (W, fused R^*(R W y - b), W^* with the prox epilogue)
+    for each of three deblurring problems: 5-level CDF 9/7 with periodic,
+    half-point symmetric and zero boundaries, 15 x 15 Gaussian PSF (sigma 3)
+    under the same boundary;
+  * the blind-channel gradient of a batch of 256 signals of 65,536 samples with
+    64-tap channels: residual r = h * s - x, then grad_h and grad_s.
+value = algorithmic HBM bytes of the step (each operator reads its inputs and
+writes its outputs once) / device time, summed over ranks, in GB/s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own independent copy of the workload (weak
+scaling, no data-path collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZE, LEVELS, WAVELET = 2048, 5, "cdf97"
+PSF_K, PSF_SIGMA, LAM, NOISE = 15, 3.0, 1e-3, 1e-3
+BCS = ("per", "sym", "zero")
+CH_B, CH_N, CH_K = 256, 65536, 64
+METRIC = "W/W* HBM GB/s; FISTA sec to 1e-4 rel objective, learned/batched vs plain"
+WORKLOAD = ("FISTA iteration on 2048x2048, 5-level CDF 9/7, PER+SYM+ZERO boundaries, 15x15 Gaussian PSF "
+            "sigma=3, lambda=1e-3 (one problem per boundary) + blind-channel gradient 256 x 65536 samples, "
+            "64-tap channels (residual + grad_h + grad_s)")
+
+
+def gaussian_taps(k, sigma):
+    c = (k - 1) / 2.0
+    t = np.exp(-((np.arange(k) - c) ** 2) / (2.0 * sigma * sigma))
+    return t / t.sum()
+
+
+def level_sizes(n, levels, bc, L=10):
+    out = []
+    for _ in range(levels):
+        m = n // 2 if bc == "per" else (n + 3 * (L - 1)) // 2
+        out.append((n, m))
+        n = m
+    return out
+
+
+def fista_bytes(bc):
+    """Algorithmic float32 bytes of one fused FISTA iteration (per kernel family)."""
+    lv = level_sizes(SIZE, LEVELS, bc)
+    N2 = SIZE * SIZE
+    C = sum(3 * m * m for _, m in lv) + lv[-1][1] ** 2
+    I = sum(m * m for _, m in lv[:-1])
+    return {"wt_synth": 4 * (C + N2 + 2 * I), "blur_normal": 4 * 3 * N2,
+            "wt_adjoint_prox": 4 * (4 * C + N2 + 2 * I), "total": 4 * (5 * C + 5 * N2 + 4 * I),
+            "level1": {"wt_synth": 4 * (4 * lv[0][1] ** 2 + N2),
+                       "wt_adjoint_prox": 4 * (N2 + 13 * lv[0][1] ** 2)}}
+
+
+def channel_bytes():
+    B, n, k = CH_B, CH_N, CH_K
+    res = 4 * (B * k + B * n + 2 * B * (n + k - 1))
+    adj = 4 * (B * n + B * k + B * (n + k - 1) + B * n + B * k)
+    return {"conv_residual": res, "conv_adjoint": adj, "total": res + adj,
+            "flops_adjoint": 4 * B * n * k, "flops_residual": 2 * B * (n + k - 1) * k}
+
+
+def step_bytes():
+    return sum(fista_bytes(bc)["total"] for bc in BCS) + channel_bytes()["total"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        try:
+            import tempfile
+            self.path = tempfile.mktemp(suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def build_workload(adj, torch, rank):
+    from synthetic_inputs import channel_problem, gaussian_noise, piecewise_smooth_image, random_vector
+    p = gaussian_taps(PSF_K, PSF_SIGMA)
+    probs = []
+    for i, bc in enumerate(BCS):
+        seed = 2000 + 10 * rank + i
+        wt = adj.WtPlan(SIZE, SIZE, LEVELS, WAVELET, bc)
+        bl = adj.BlurPlan(SIZE, SIZE, p, p, bc)
+        img = wt.image(torch.as_tensor(piecewise_smooth_image(SIZE, SIZE, seed)))
+        b = adj.blur(bl, img)
+        b[:, :SIZE] += torch.as_tensor(gaussian_noise((SIZE, SIZE), seed + 1, NOISE), dtype=torch.float32,
+                                       device="cuda")
+        f = adj.Fista(wt, bl, b, LAM, 1.0)
+        v0 = wt.pack(random_vector(wt.logical_size, seed + 2))
+        f.set_lipschitz(f.lipschitz(v0, iters=30))
+        probs.append({"bc": bc, "wt": wt, "bl": bl, "b": b, "fista": f, "b_host": b.cpu().pin_memory()})
+    cp = channel_problem(CH_B, CH_N, CH_K, seed=3000 + rank)
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float32, device="cuda").contiguous()  # noqa: E731
+    h, s = dev(cp["h"]), dev(cp["s"])
+    x = adj.conv_residual(h, s) + dev(cp["noise"])
+    ch = {"s": dev(cp["s_est"]), "h": dev(cp["h_est"]), "x": x,
+          "r": torch.empty(CH_B, CH_N + CH_K - 1, device="cuda"),
+          "gh": torch.empty(CH_B, CH_K, device="cuda"), "gs": torch.empty(CH_B, CH_N, device="cuda")}
+    ch["ws"] = adj.workspace(adj.lib().adjwt_conv_adjoint_workspace_size(CH_B, CH_N, CH_K))
+    for key in ("s", "h", "x"):
+        ch[key + "_host"] = ch[key].cpu().pin_memory()
+    return probs, ch
+
+
+def run_step(adj, probs, ch):
+    for pr in probs:
+        pr["fista"].step()
+    adj.conv_residual(ch["h"], ch["s"], ch["x"], r=ch["r"])
+    adj.conv_adjoint(ch["s"], ch["h"], ch["r"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
+
+
+def run_e2e_step(adj, torch, probs, ch, out_host):
+    """Same step through the public API with host buffers: inputs copied in, results read back."""
+    for pr in probs:
+        pr["b"].copy_(pr["b_host"], non_blocking=True)
+        pr["fista"].step()
+    for key in ("s", "h", "x"):
+        ch[key].copy_(ch[key + "_host"], non_blocking=True)
+    adj.conv_residual(ch["h"], ch["s"], ch["x"], r=ch["r"])
+    adj.conv_adjoint(ch["s"], ch["h"], ch["r"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
+    out_host["gh"].copy_(ch["gh"], non_blocking=True)
+    for i, pr in enumerate(probs):
+        ll = pr["wt"].band_rows[0] * pr["wt"].band_pitch[0]
+        out_host["ll"][i, :ll].copy_(pr["fista"].x[:ll], non_blocking=True)
+
+
+def fista_time_to_tol(adj, torch, pr, tol=1e-4, ref_iters=3000, check_every=10, max_iters=3000):
+    """Seconds for plain GPU FISTA from x0 = 0 to (F(x_k) - F*)/F* <= tol, checks included.
+    F* = the smallest objective seen along a ref_iters-iteration run."""
+    f = pr["fista"]
+    f.reset()
+    fstar = float("inf")
+    for k in range(1, ref_iters + 1):
+        val = f.step(objective=(k % 50 == 0 or k == ref_iters))
+        if val is not None:
+            fstar = min(fstar, val)
+    f.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, reached = 0, False
+    while it < max_iters:
+        it += 1
+        val = f.step(objective=(it % check_every == 0))
+        if val is not None and (val - fstar) / fstar <= tol:
+            reached = True
+            break
+    torch.cuda.synchronize()
+    return {"seconds": time.perf_counter() - t0, "iterations": it, "reached": reached, "F_star": fstar,
+            "F_star_iterations": ref_iters, "check_every": check_every, "boundary": pr["bc"]}
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1707_02018_gb300 as adj
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    adj.lib()
+    probs, ch = build_workload(adj, torch, rank)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        run_step(adj, probs, ch)
+    torch.cuda.synchronize()
+
+    traced = min(args.steps, 20)
+    stream = torch.cuda.current_stream()
+    clock = ClockSampler(local)
+    clock.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        if k == args.steps - traced:
+            adj.trace_enable(traced * 64)
+        run_step(adj, probs, ch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_local = e0.elapsed_time(e1)
+    clocks = clock.stop()
+    recs = adj.trace_records()
+    adj.trace_enable(0)
+
+    t = torch.tensor([ms_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    bytes_step = step_bytes()
+    value = bytes_step * args.steps * world / (ms * 1e-3) / 1e9
+
+    # per-kernel device time from the traced steps
+    per = {}
+    for name, tag, kms in recs:
+        key = f"{name}.L{tag}" if tag else name
+        d = per.setdefault(key, [0, 0.0])
+        d[0] += 1
+        d[1] += kms
+    launches_per_step = len(recs) / traced
+    pk = peaks()
+    fb = {bc: fista_bytes(bc) for bc in BCS}
+    cb = channel_bytes()
+    alg = {"wt_synth.L1": sum(fb[bc]["level1"]["wt_synth"] for bc in BCS) / 3,
+           "wt_adjoint_prox.L1": sum(fb[bc]["level1"]["wt_adjoint_prox"] for bc in BCS) / 3,
+           "blur_normal": fb["sym"]["blur_normal"], "conv_adjoint": cb["conv_adjoint"],
+           "conv_residual": cb["conv_residual"]}
+    kernels = {}
+    for key, (n, tot) in sorted(per.items(), key=lambda kv: -kv[1][1]):
+        entry = {"launches_per_step": n / traced, "ms_per_launch": tot / n, "share": tot / sum(v[1] for v in per.values())}
+        if key in alg:
+            entry["gbs"] = alg[key] / (tot / n * 1e-3) / 1e9
+        kernels[key] = entry
+    top = max(per.items(), key=lambda kv: kv[1][1])[0]
+    top_ms = per[top][1] / per[top][0]
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    if top == "conv_adjoint":
+        achieved = cb["flops_adjoint"] / (top_ms * 1e-3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+    else:
+        achieved = alg.get(top, 0.0) / (top_ms * 1e-3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
+    hbm_roofs = {}
+    for key in ("wt_synth.L1", "wt_adjoint_prox.L1", "blur_normal", "conv_adjoint"):
+        if key in per:
+            a = alg[key] / (per[key][1] / per[key][0] * 1e-3) / 1e9
+            hbm_roofs[key] = {"achieved_gbs": a, "frac_of_hbm": a / pk["hbm_gbs"]}
+
+    # end to end through the public API with host buffers
+    h2d = sum(pr["b_host"].numel() * 4 for pr in probs) + sum(ch[k + "_host"].numel() * 4 for k in ("s", "h", "x"))
+    out_host = {"gh": torch.empty(CH_B, CH_K).pin_memory(),
+                "ll": torch.empty(len(probs), max(p["wt"].band_rows[0] * p["wt"].band_pitch[0] for p in probs)).pin_memory()}
+    d2h = out_host["gh"].numel() * 4 + sum(p["wt"].band_rows[0] * p["wt"].band_pitch[0] * 4 for p in probs)
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        run_e2e_step(adj, torch, probs, ch, out_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = bytes_step * e2e_steps * world / (float(t.item()) * 1e-3) / 1e9
+
+    extra = {}
+    if rank == 0 and not args.no_solve:
+        extra["fista_sec_to_1e-4"] = fista_time_to_tol(adj, torch, probs[1])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded piecewise-smooth images, N(0,1) signals)",
+            "config": {"workload": WORKLOAD, "image": SIZE, "levels": LEVELS, "wavelet": WAVELET,
+                       "boundaries": list(BCS), "psf": [PSF_K, PSF_SIGMA], "channels": [CH_B, CH_N, CH_K],
+                       "parallelism": f"replicas x{world} (independent problems per rank)",
+                       "l2": "inputs larger than L2: ~540 MB touched per step vs 129 MB L2",
+                       "bytes_per_step": bytes_step},
+            "roofline": roof, "hbm_rooflines": hbm_roofs, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clocks,
+        }
+        line.update(extra)
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(max_seconds=20.0)
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+def oracle_sample(rng_seed=0, boundaries=BCS, rows_conv=8):
+    """One bounded sample of the step on the host with the float64 oracle:
+    one FISTA iteration per listed boundary at 2048^2, plus the channel
+    gradient of `rows_conv` of the 256 signals.  Returns (bytes, seconds)."""
+    from oracle import conv as oconv
+    from oracle import fista as ofista
+    from synthetic_inputs import channel_problem, gaussian_noise, piecewise_smooth_image
+    p = gaussian_taps(PSF_K, PSF_SIGMA)
+    secs, nbytes = 0.0, 0
+    for i, bc in enumerate(boundaries):
+        img = piecewise_smooth_image(SIZE, SIZE, 2000 + i)
+        b = img + gaussian_noise((SIZE, SIZE), 2001 + i, NOISE)
+        prob = ofista.Problem(SIZE, SIZE, LEVELS, WAVELET, bc, p, p, bc, b, LAM)
+        from oracle.layout import num_coeffs
+        C = num_coeffs(SIZE, SIZE, LEVELS, 10, bc)
+        x = np.zeros(C)
+        t0 = time.perf_counter()
+        ofista.fista_step(prob, x, x.copy(), 1.0, 1.0)
+        secs += time.perf_counter() - t0
+        nbytes += fista_bytes(bc)["total"]
+    cp = channel_problem(rows_conv, CH_N, CH_K, seed=3000)
+    x = oconv.conv_full(cp["h"], cp["s"]) + cp["noise"]
+    t0 = time.perf_counter()
+    r = oconv.conv_full(cp["h_est"], cp["s_est"]) - x
+    oconv.conv_adjoint(cp["s_est"], cp["h_est"], r)
+    secs += time.perf_counter() - t0
+    nbytes += channel_bytes()["total"] * rows_conv // CH_B
+    return nbytes, secs
+
+
+def cpu_baseline(max_seconds=20.0):
+    nbytes, secs = oracle_sample()
+    return {"value": nbytes / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "one float64 FISTA iteration at 2048^2 for each of PER/SYM/ZERO + channel gradient of "
+                      "8 of the 256 signals (numpy, single thread), bytes counted as on the GPU",
+            "seconds": secs, "host_cores_available": os.cpu_count()}
+
+
+def reference(args, budget_s=150.0):
+    """The oracle timed on the host: each step runs the next piece of the
+    workload in a fixed cycle (one FISTA iteration at 2048^2 for PER, SYM, ZERO,
+    each followed by the channel gradient of 4 signals); once the run has used
+    `budget_s`, the remaining steps run the channel gradient of one signal."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, total_bytes, spent = [], 0, 0.0
+    cycle = [("fista", bc) for bc in BCS]
+    for k in range(args.warmup + args.steps):
+        if spent < budget_s:
+            kind, bc = cycle[k % len(cycle)]
+            nbytes, secs = oracle_sample(boundaries=(bc,), rows_conv=4)
+        else:
+            nbytes, secs = oracle_sample(boundaries=(), rows_conv=1)
+        spent += secs
+        if k >= args.warmup:
+            times.append(secs)
+            total_bytes += nbytes
+    secs = sum(times)
+    value = total_bytes / secs / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "per step: one FISTA iteration at 2048^2 for one boundary "
+                   "(rotating PER/SYM/ZERO) + channel gradient of 4 of the 256 signals"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "float64 numpy oracle, single thread, bounded sample per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

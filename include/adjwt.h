@@ -1,0 +1,204 @@
+/*
+ * adjwt -- exact adjoints of multi-level 2D wavelet reconstruction and of
+ * Gaussian blur, the FISTA gradient W^* R^* (R W x - b) built from them, and
+ * the blind-channel convolution adjoint, on one GB300 (sm_103a).
+ *
+ * Paper: J. Folberth, S. Becker, "Efficient Adjoint Computation for Wavelet
+ * and Convolution Operators", IEEE Signal Processing Magazine (Lecture
+ * Notes), arXiv 1707.02018.
+ *
+ * Conventions for every entry point
+ *  - Tensors are caller-owned DEVICE buffers of float32 unless stated.
+ *    Pointers must be 16-byte aligned.  Calls are asynchronous on `stream`
+ *    except where a host result is returned (stated per call).
+ *  - Images are rows x cols, row-major, with a row pitch of image_pitch
+ *    floats (cols rounded up to a multiple of 4).  Pitch padding of an image
+ *    is ignored on input and left untouched on output.
+ *  - Coefficient vectors use the packed band order
+ *      [LL_J, LH_J, HL_J, HH_J, LH_{J-1}, ..., HH_1]
+ *    (LH = vertical highpass / horizontal lowpass, HL = vertical lowpass /
+ *    horizontal highpass).  Band b is band_rows[b] x band_cols[b] with row
+ *    pitch band_pitch[b] (multiple of 4 floats) starting at band_offsets[b]
+ *    floats; num_coeffs counts the padding.  Padding is ignored on input and
+ *    written as 0 on output.
+ *  - Plans are created once (they allocate a few KB of device tables), are
+ *    immutable, and may be used concurrently from several streams.  Hot calls
+ *    allocate nothing: scratch comes from a caller-provided workspace of at
+ *    least *_workspace_size bytes (256-byte aligned).
+ *  - Out-of-place only: an output that overlaps an input -> ADJWT_ERR_ALIAS.
+ *  - Return 0 on success or a negative ADJWT_ERR_* code; adjwt_last_error()
+ *    then holds a message for the calling thread.  Nothing throws or aborts
+ *    across this boundary.
+ */
+#ifndef ADJWT_H
+#define ADJWT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* adjwt_stream_t; /* same type as cudaStream_t */
+
+enum {
+  ADJWT_OK = 0,
+  ADJWT_ERR_INVALID_ARG = -1, /* null pointer, unknown enum, bad scalar     */
+  ADJWT_ERR_SHAPE = -2,       /* sizes unsupported for this mode            */
+  ADJWT_ERR_ALIGN = -3,       /* pointer not 16-byte aligned                */
+  ADJWT_ERR_ALIAS = -4,       /* output overlaps an input                   */
+  ADJWT_ERR_CUDA = -5,        /* CUDA runtime error (text in last_error)    */
+  ADJWT_ERR_NONFINITE = -6,   /* objective or step size not finite          */
+  ADJWT_ERR_WORKSPACE = -7,   /* workspace missing, small or misaligned     */
+  ADJWT_ERR_TIMEOUT = -8      /* a bounded device wait gave up              */
+};
+
+/* Boundary handling (Sec. I-A).  ZERO: zero-padded extension E_zpd.  SYM:
+ * half-point symmetric E_sym.  PPD: the periodic extension E_per of Sec. I-A
+ * (redundant).  PER: critically sampled circular transform (sizes divisible by
+ * 2^levels; for orthogonal filters W^* = W^-1).  Blur plans take ZERO, SYM or
+ * PER (PER = circular wrap). */
+typedef enum { ADJWT_BC_ZERO = 0, ADJWT_BC_SYM = 1, ADJWT_BC_PPD = 2, ADJWT_BC_PER = 3 } adjwt_bc;
+
+/* Filter banks (Sec. I-B orthogonal Haar / Daubechies, Sec. I-C CDF 9/7).
+ * DB2 = 4-tap Daubechies, DB4 = 8-tap, CDF97 = 9/7 biorthogonal in a length-10
+ * array.  L = 2, 4, 8, 10; extension length per side L' = L - 1. */
+typedef enum { ADJWT_HAAR = 0, ADJWT_DB2 = 1, ADJWT_DB4 = 2, ADJWT_CDF97 = 3 } adjwt_wavelet;
+
+typedef struct adjwt_wt_plan adjwt_wt_plan;
+typedef struct adjwt_blur_plan adjwt_blur_plan;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* adjwt_last_error(void);
+int adjwt_version(void);
+
+/* ------------------------------------------------------------------ wavelets
+ * Plan of a J-level 2D transform of a rows x cols image.  Band lengths per
+ * level and axis: n = floor((N + 3L')/2) for ZERO/SYM/PPD (the full
+ * zero-padded analysis of the length N + 2L' extended signal, odd samples),
+ * n = N/2 for PER.  rows, cols >= 1; 1 <= levels <= 16.
+ * Errors: INVALID_ARG (enum), SHAPE (PER sizes not divisible by 2^levels),
+ * CUDA (table allocation). */
+int adjwt_wt_plan_create(adjwt_wt_plan** out, int rows, int cols, int levels, int wavelet, int bc);
+void adjwt_wt_plan_destroy(adjwt_wt_plan* plan);
+
+/* Layout of the packed coefficient vector.  Arrays hold 3*levels+1 entries in
+ * packed band order; any output pointer may be NULL. */
+int adjwt_wt_layout(const adjwt_wt_plan* plan, int64_t* num_coeffs, int64_t* band_offsets,
+                    int* band_rows, int* band_cols, int* band_pitch, int* image_pitch);
+
+/* Workspace bytes needed by wt_synth / wt_synth_adjoint / wt_analysis. */
+size_t adjwt_wt_workspace_size(const adjwt_wt_plan* plan);
+
+/* The filter taps the plan derived (float64, length L each; NULL skips). */
+int adjwt_wt_filters(const adjwt_wt_plan* plan, double* dec_lo, double* dec_hi, double* rec_lo,
+                     double* rec_hi, int* L);
+
+/* W: multi-level reconstruction, W = E^dagger W_zpd per level (Sec. I-A,
+ * Eq. 2 with W^dagger = W^dagger_zpd E): coeffs (num_coeffs) -> image. */
+int wt_synth(const adjwt_wt_plan* plan, const float* coeffs, float* image, void* ws, size_t ws_bytes,
+             adjwt_stream_t stream);
+
+/* W^*: the exact adjoint of wt_synth, Eq. 4: dual-filter zero-padded analysis
+ * after the weighted extension (E^dagger)^*: image -> coeffs. */
+int wt_synth_adjoint(const adjwt_wt_plan* plan, const float* image, float* coeffs, void* ws,
+                     size_t ws_bytes, adjwt_stream_t stream);
+
+/* W^dagger: analysis W^dagger_zpd E (Sec. I-A); wt_synth(wt_analysis(u)) = u.
+ * The "pseudoinverse approximation" of W^* discussed in Sec. I-B. */
+int wt_analysis(const adjwt_wt_plan* plan, const float* image, float* coeffs, void* ws, size_t ws_bytes,
+                adjwt_stream_t stream);
+
+/* ---------------------------------------------------------------------- blur
+ * Separable PSF p = outer(taps_r, taps_c) (float64 taps, odd lengths
+ * kr, kc <= 65) applied as R u = C_valid(E_r u) under bc in {ZERO, SYM, PER}
+ * (Sec. I: Gaussian PSF under symmetric boundary conditions).  Images use
+ * image_pitch = cols rounded up to 4. */
+int adjwt_blur_plan_create(adjwt_blur_plan** out, int rows, int cols, const double* taps_r, int kr,
+                           const double* taps_c, int kc, int bc);
+void adjwt_blur_plan_destroy(adjwt_blur_plan* plan);
+int adjwt_blur_image_pitch(const adjwt_blur_plan* plan);
+size_t adjwt_blur_workspace_size(const adjwt_blur_plan* plan);
+
+/* out = R in. */
+int blur(const adjwt_blur_plan* plan, const float* in, float* out, adjwt_stream_t stream);
+/* out = R^* in = E_r^T C_valid^T in (correlation, then fold the extension). */
+int blur_adjoint(const adjwt_blur_plan* plan, const float* in, float* out, adjwt_stream_t stream);
+/* Fused image-space data gradient g = R^*(R u - b) in one pass; if
+ * half_sq_out (DEVICE double) is non-NULL it receives 1/2 ||R u - b||^2
+ * (float64 accumulation).  b may be NULL (taken as 0). */
+int blur_normal(const adjwt_blur_plan* plan, const float* u, const float* b, float* g, double* half_sq_out,
+                void* ws, size_t ws_bytes, adjwt_stream_t stream);
+
+/* ------------------------------------------------------- blind channel (Sec. II)
+ * Batched real signals, row-major with unit stride: s (batch x n),
+ * h (batch x k), r and x (batch x (n+k-1)).  Eq. 5 gradients:
+ *   grad_h[b][j] = sum_{i<n} s[b][i] r[b][i+j]   (j < k)   = S^T r
+ *   grad_s[b][m] = sum_{i<k} h[b][i] r[b][i+m]   (m < n)   = H^T r
+ * either output may be NULL.  batch >= 0, n >= 1, k >= 1. */
+size_t adjwt_conv_adjoint_workspace_size(int batch, int64_t n, int k);
+int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
+                 float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+/* Residual of the full convolution, r = h * s - x (x may be NULL: r = h * s). */
+int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
+                  adjwt_stream_t stream);
+
+/* --------------------------------------------------------------------- FISTA
+ * min_x 1/2 ||R W x - b||^2 + lambda ||x||_1 (Eq. 1) with constant step
+ * 1/lipschitz.  The wavelet and blur plans must describe the same image. */
+typedef struct {
+  const adjwt_wt_plan* wt;
+  const adjwt_blur_plan* blur;
+  const float* b;   /* device image (observed, blurred) */
+  double lambda;    /* > 0 */
+  double lipschitz; /* L_f > 0, e.g. from adjwt_fista_lipschitz */
+} adjwt_fista_problem;
+
+typedef struct {
+  float* x;  /* device coeffs: x_{k-1} on entry, x_k on return       */
+  float* y;  /* device coeffs: y_k on entry, y_{k+1} on return       */
+  double t;  /* t_k on entry (1 before the first step), t_{k+1} on return */
+  int64_t k; /* number of steps taken                                 */
+} adjwt_fista_state;
+
+size_t adjwt_fista_workspace_size(const adjwt_fista_problem* prob);
+
+/* One FISTA iteration (the method cited in Sec. I-B):
+ *   x_k = soft(y_k - grad f(y_k)/L_f, lambda/L_f),  grad f = W^* R^*(R W y_k - b)
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,  y_{k+1} = x_k + ((t_k-1)/t_{k+1})(x_k - x_{k-1}).
+ * If objective_out (HOST) is non-NULL the call also evaluates F(x_k) and
+ * synchronises the stream; a non-finite value returns ADJWT_ERR_NONFINITE. */
+int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* ws, size_t ws_bytes,
+               double* objective_out, adjwt_stream_t stream);
+
+/* F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1 into *objective_out (HOST);
+ * synchronises the stream. */
+int adjwt_fista_objective(const adjwt_fista_problem* prob, const float* x, void* ws, size_t ws_bytes,
+                          double* objective_out, adjwt_stream_t stream);
+
+/* Step size: power iteration on A^*A, A = R W.  v (device coeffs) holds the
+ * start vector and receives the last normalised iterate; after `iters` steps
+ * *lipschitz_out (HOST) = 1.01 * ||A^*A v_{iters-1}|| with ||v|| = 1.
+ * Synchronises the stream. */
+int adjwt_fista_lipschitz(const adjwt_fista_problem* prob, float* v, int iters, void* ws, size_t ws_bytes,
+                          double* lipschitz_out, adjwt_stream_t stream);
+
+/* ------------------------------------------------------------------- tracing
+ * Optional per-kernel device timing without a profiler (the paper has no
+ * counterpart; it serves the measurement harness).  adjwt_trace_enable(n)
+ * arms a pool of n CUDA event pairs: each kernel launched afterwards by this
+ * library (from one host thread) is bracketed by two events on its stream
+ * until the pool is full; adjwt_trace_enable(0) disarms and frees the pool.
+ * adjwt_trace_reset() reuses the pool from record 0.  adjwt_trace_get waits
+ * for record i and returns the kernel's name (static string), its tag (the
+ * wavelet level, else 0) and its duration in milliseconds. */
+int adjwt_trace_enable(int capacity);
+int adjwt_trace_reset(void);
+int adjwt_trace_count(void);
+int adjwt_trace_get(int i, const char** name, int* tag, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADJWT_H */

@@ -1,0 +1,300 @@
+"""Python binding of libadjwt (argument marshalling only).
+
+Every operator runs in the CUDA kernels of libadjwt.so behind the C-ABI of
+include/adjwt.h; this module only turns torch tensors into device pointers,
+sizes and the current CUDA stream, allocates outputs and workspaces with
+torch, and raises on a non-zero status.  Names follow the C-ABI.
+
+Layouts: images are (rows, image_pitch) float32 tensors (cols rounded up to a
+multiple of 4); coefficient vectors are flat (num_coeffs,) float32 tensors in
+the padded packed band order of the plan.  `WtPlan.pack` / `WtPlan.unpack`
+convert to and from the unpadded packed order.
+"""
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import AdjwtError, FistaProblem, FistaState  # noqa: F401
+
+BC = {"zero": 0, "sym": 1, "ppd": 2, "per": 3}
+WAVELET = {"haar": 0, "db2": 1, "db4": 2, "cdf97": 3}
+
+
+def lib():
+    return _lib.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, numel, name):
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"{name}: need a contiguous float32 CUDA tensor with >= {numel} elements")
+
+
+def workspace(nbytes, device=None):
+    """A 256-byte aligned scratch buffer (torch-allocated)."""
+    n = max(int(nbytes), 1) + 256
+    raw = torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+    off = (-raw.data_ptr()) % 256
+    return raw[off:off + max(int(nbytes), 1)]
+
+
+class WtPlan:
+    """Plan of a `levels`-level 2D transform of a rows x cols image."""
+
+    def __init__(self, rows, cols, levels, wavelet="cdf97", bc="sym"):
+        self.rows, self.cols, self.levels = rows, cols, levels
+        self.wavelet, self.bc = wavelet, bc
+        h = C.c_void_p()
+        _lib.check(lib().adjwt_wt_plan_create(C.byref(h), rows, cols, levels, WAVELET[wavelet], BC[bc]))
+        self._h = h
+        nb = 3 * levels + 1
+        nc = C.c_int64()
+        offs = (C.c_int64 * nb)()
+        br, bcol, bp = (C.c_int * nb)(), (C.c_int * nb)(), (C.c_int * nb)()
+        ip = C.c_int()
+        _lib.check(lib().adjwt_wt_layout(h, C.byref(nc), offs, br, bcol, bp, C.byref(ip)))
+        self.num_coeffs = nc.value
+        self.band_offsets = list(offs)
+        self.band_rows, self.band_cols, self.band_pitch = list(br), list(bcol), list(bp)
+        self.image_pitch = ip.value
+        self.workspace_bytes = lib().adjwt_wt_workspace_size(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.adjwt_wt_plan_destroy(h)
+            self._h = None
+
+    def filters(self):
+        arrs = [(C.c_double * 10)() for _ in range(4)]
+        L = C.c_int()
+        _lib.check(lib().adjwt_wt_filters(self._h, *arrs, C.byref(L)))
+        names = ("dec_lo", "dec_hi", "rec_lo", "rec_hi")
+        return {n: list(a)[:L.value] for n, a in zip(names, arrs)}
+
+    @property
+    def logical_size(self):
+        return sum(r * c for r, c in zip(self.band_rows, self.band_cols))
+
+    def pack(self, flat):
+        """Unpadded packed vector (any device) -> padded device vector."""
+        flat = torch.as_tensor(flat, dtype=torch.float32)
+        out = torch.zeros(self.num_coeffs, dtype=torch.float32, device="cuda")
+        pos = 0
+        for off, r, c, p in zip(self.band_offsets, self.band_rows, self.band_cols, self.band_pitch):
+            out[off:off + r * p].view(r, p)[:, :c] = flat[pos:pos + r * c].view(r, c).to(out.device)
+            pos += r * c
+        return out
+
+    def unpack(self, padded):
+        parts = []
+        for off, r, c, p in zip(self.band_offsets, self.band_rows, self.band_cols, self.band_pitch):
+            parts.append(padded[off:off + r * p].view(r, p)[:, :c].reshape(-1))
+        return torch.cat(parts)
+
+    def image(self, img=None):
+        """A (rows, image_pitch) device image, zero padded, optionally filled."""
+        out = torch.zeros(self.rows, self.image_pitch, dtype=torch.float32, device="cuda")
+        if img is not None:
+            out[:, :self.cols] = torch.as_tensor(img, dtype=torch.float32).to(out.device)
+        return out
+
+
+def _ws(plan_bytes, ws):
+    if ws is None:
+        ws = workspace(plan_bytes)
+    return ws, ws.numel()
+
+
+def wt_synth(plan, coeffs, image=None, ws=None, stream=None):
+    """W: coefficients -> image (rows, image_pitch)."""
+    _need(coeffs, plan.num_coeffs, "coeffs")
+    image = plan.image() if image is None else image
+    _need(image, plan.rows * plan.image_pitch, "image")
+    ws, nb = _ws(plan.workspace_bytes, ws)
+    _lib.check(lib().wt_synth(plan.handle, _ptr(coeffs), _ptr(image), _ptr(ws), nb, _stream(stream)))
+    return image
+
+
+def wt_synth_adjoint(plan, image, coeffs=None, ws=None, stream=None):
+    """W^*: image (rows, image_pitch) -> coefficients."""
+    _need(image, plan.rows * plan.image_pitch, "image")
+    coeffs = torch.empty(plan.num_coeffs, dtype=torch.float32, device=image.device) if coeffs is None else coeffs
+    _need(coeffs, plan.num_coeffs, "coeffs")
+    ws, nb = _ws(plan.workspace_bytes, ws)
+    _lib.check(lib().wt_synth_adjoint(plan.handle, _ptr(image), _ptr(coeffs), _ptr(ws), nb, _stream(stream)))
+    return coeffs
+
+
+def wt_analysis(plan, image, coeffs=None, ws=None, stream=None):
+    """W^dagger: image -> coefficients (wt_synth(wt_analysis(u)) = u)."""
+    _need(image, plan.rows * plan.image_pitch, "image")
+    coeffs = torch.empty(plan.num_coeffs, dtype=torch.float32, device=image.device) if coeffs is None else coeffs
+    _need(coeffs, plan.num_coeffs, "coeffs")
+    ws, nb = _ws(plan.workspace_bytes, ws)
+    _lib.check(lib().wt_analysis(plan.handle, _ptr(image), _ptr(coeffs), _ptr(ws), nb, _stream(stream)))
+    return coeffs
+
+
+class BlurPlan:
+    """Separable PSF outer(taps_r, taps_c) under bc in {zero, sym, per}."""
+
+    def __init__(self, rows, cols, taps_r, taps_c=None, bc="sym"):
+        taps_c = taps_r if taps_c is None else taps_c
+        tr = (C.c_double * len(taps_r))(*[float(v) for v in taps_r])
+        tc = (C.c_double * len(taps_c))(*[float(v) for v in taps_c])
+        h = C.c_void_p()
+        _lib.check(lib().adjwt_blur_plan_create(C.byref(h), rows, cols, tr, len(taps_r), tc, len(taps_c), BC[bc]))
+        self._h = h
+        self.rows, self.cols, self.bc = rows, cols, bc
+        self.image_pitch = lib().adjwt_blur_image_pitch(h)
+        self.workspace_bytes = lib().adjwt_blur_workspace_size(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.adjwt_blur_plan_destroy(h)
+            self._h = None
+
+    def image(self, img=None):
+        out = torch.zeros(self.rows, self.image_pitch, dtype=torch.float32, device="cuda")
+        if img is not None:
+            out[:, :self.cols] = torch.as_tensor(img, dtype=torch.float32).to(out.device)
+        return out
+
+
+def blur(plan, x, out=None, stream=None):
+    _need(x, plan.rows * plan.image_pitch, "in")
+    out = torch.zeros_like(x) if out is None else out
+    _lib.check(lib().blur(plan.handle, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def blur_adjoint(plan, x, out=None, stream=None):
+    _need(x, plan.rows * plan.image_pitch, "in")
+    out = torch.zeros_like(x) if out is None else out
+    _lib.check(lib().blur_adjoint(plan.handle, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def blur_normal(plan, u, b=None, g=None, want_norm=False, ws=None, stream=None):
+    """g = R^*(R u - b); with want_norm also returns 1/2 ||R u - b||^2 (float64 device scalar)."""
+    _need(u, plan.rows * plan.image_pitch, "u")
+    g = torch.zeros_like(u) if g is None else g
+    half = None
+    wsp, nb = (None, 0)
+    if want_norm:
+        half = torch.zeros(1, dtype=torch.float64, device=u.device)
+        wsp, nb = _ws(plan.workspace_bytes, ws)
+    _lib.check(lib().blur_normal(plan.handle, _ptr(u), _ptr(b), _ptr(g), _ptr(half), _ptr(wsp), nb, _stream(stream)))
+    return (g, half) if want_norm else g
+
+
+def conv_adjoint(s, h, r, grad_h=True, grad_s=True, ws=None, stream=None):
+    """(grad_h, grad_s) of Eq. 5 for batched rows s (B, n), h (B, k), r (B, n+k-1)."""
+    B, n = s.shape
+    k = h.shape[1]
+    assert r.shape == (B, n + k - 1)
+    gh = torch.empty(B, k, dtype=torch.float32, device=r.device) if grad_h is True else grad_h
+    gs = torch.empty(B, n, dtype=torch.float32, device=r.device) if grad_s is True else grad_s
+    gh = None if gh is False else gh
+    gs = None if gs is False else gs
+    nbytes = lib().adjwt_conv_adjoint_workspace_size(B, n, k)
+    wsp, nb = _ws(nbytes, ws)
+    _lib.check(lib().conv_adjoint(B, n, k, _ptr(s), _ptr(h), _ptr(r), _ptr(gh), _ptr(gs), _ptr(wsp), nb,
+                                  _stream(stream)))
+    return gh, gs
+
+
+def conv_residual(h, s, x=None, r=None, stream=None):
+    B, n = s.shape
+    k = h.shape[1]
+    r = torch.empty(B, n + k - 1, dtype=torch.float32, device=s.device) if r is None else r
+    _lib.check(lib().conv_residual(B, n, k, _ptr(h), _ptr(s), _ptr(x), _ptr(r), _stream(stream)))
+    return r
+
+
+class Fista:
+    """FISTA state and problem for min 1/2||R W x - b||^2 + lam ||x||_1 on one GPU."""
+
+    def __init__(self, wt_plan, blur_plan, b, lam, lipschitz=1.0):
+        self.wt, self.blur, self.b = wt_plan, blur_plan, b
+        self.problem = FistaProblem(wt_plan.handle, blur_plan.handle, b.data_ptr(), float(lam), float(lipschitz))
+        self.ws = workspace(lib().adjwt_fista_workspace_size(C.byref(self.problem)))
+        self.x = torch.zeros(wt_plan.num_coeffs, dtype=torch.float32, device="cuda")
+        self.y = torch.zeros_like(self.x)
+        self.state = FistaState(self.x.data_ptr(), self.y.data_ptr(), 1.0, 0)
+
+    def set_lipschitz(self, L):
+        self.problem.lipschitz = float(L)
+
+    def reset(self, x0=None):
+        self.x.zero_()
+        if x0 is not None:
+            self.x.copy_(x0)
+        self.y.copy_(self.x)
+        self.state.t = 1.0
+        self.state.k = 0
+
+    def step(self, objective=False, stream=None):
+        out = C.c_double()
+        _lib.check(lib().fista_step(C.byref(self.problem), C.byref(self.state), _ptr(self.ws), self.ws.numel(),
+                                    C.byref(out) if objective else None, _stream(stream)))
+        return out.value if objective else None
+
+    def objective(self, x=None, stream=None):
+        out = C.c_double()
+        x = self.x if x is None else x
+        _lib.check(lib().adjwt_fista_objective(C.byref(self.problem), _ptr(x), _ptr(self.ws), self.ws.numel(),
+                                               C.byref(out), _stream(stream)))
+        return out.value
+
+    def lipschitz(self, v, iters=50, stream=None):
+        out = C.c_double()
+        _lib.check(lib().adjwt_fista_lipschitz(C.byref(self.problem), _ptr(v), iters, _ptr(self.ws),
+                                               self.ws.numel(), C.byref(out), _stream(stream)))
+        return out.value
+
+
+def fista_step(fista, objective=False, stream=None):
+    return fista.step(objective, stream)
+
+
+def trace_enable(capacity):
+    """Arm (capacity > 0) or disarm (0) per-kernel event timing in libadjwt."""
+    _lib.check(lib().adjwt_trace_enable(int(capacity)))
+
+
+def trace_reset():
+    _lib.check(lib().adjwt_trace_reset())
+
+
+def trace_records():
+    """[(kernel name, tag, milliseconds)] of the armed trace (waits for each record)."""
+    out = []
+    name, tag, ms = C.c_char_p(), C.c_int(), C.c_float()
+    for i in range(lib().adjwt_trace_count()):
+        _lib.check(lib().adjwt_trace_get(i, C.byref(name), C.byref(tag), C.byref(ms)))
+        out.append((name.value.decode(), tag.value, ms.value))
+    return out

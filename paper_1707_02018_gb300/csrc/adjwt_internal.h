@@ -1,0 +1,128 @@
+// Internal types shared by the host plan code and the CUDA kernels of libadjwt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/adjwt.h"
+
+namespace adjwt {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxTaps = 10;     // longest filter array (CDF 9/7 in a length-10 array)
+constexpr int kMaxBlurRadius = 32;
+constexpr int kSynthTile = 32;   // output tile side of the tiled reconstruction kernel
+
+enum Mode : int { kZero = 0, kSym = 1, kPpd = 2, kPer = 3 };
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define ADJWT_CUDA_CHECK(call)                                  \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::adjwt::cuda_fail(e_, #call); \
+  } while (0)
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- tracing
+int trace_begin(const char* name, int tag, cudaStream_t s);
+void trace_end(int id, cudaStream_t s);
+#define ADJWT_TRACED(name, tag, stream, ...)                      \
+  do {                                                            \
+    const int tr_id_ = ::adjwt::trace_begin(name, tag, stream);   \
+    __VA_ARGS__;                                                  \
+    ::adjwt::trace_end(tr_id_, stream);                           \
+  } while (0)
+
+// ---------------------------------------------------------------- filters
+struct FilterBank {
+  int L = 0;
+  double dec_lo[kMaxTaps] = {}, dec_hi[kMaxTaps] = {}, rec_lo[kMaxTaps] = {}, rec_hi[kMaxTaps] = {};
+};
+bool make_filter_bank(int wavelet, FilterBank* fb);
+
+// ---------------------------------------------------------------- wavelet plan
+// One axis of one level.
+struct LevelAxis {
+  int N;          // length of LL_{j-1} along this axis (level input)
+  int n;          // band length along this axis
+  int pitch_in;   // unused for axis 1 / rows
+  const float* winv;  // device table of 1/c[j], j < N (null for PER / ZERO)
+};
+
+struct Level {
+  LevelAxis ax[2];  // 0 = rows (vertical), 1 = cols (horizontal)
+  int in_pitch;     // row pitch of LL_{j-1} (image pitch for j = 1)
+  int band_pitch;   // row pitch of the four bands of level j
+  int64_t off_band[4];  // offsets of LL(level J only) / LH / HL / HH in the packed vector (-1 = none)
+  bool generic_synth;   // synthesis of this level takes the per-pixel gather path
+};
+
+}  // namespace adjwt
+
+struct adjwt_wt_plan {
+  int rows, cols, levels, wavelet, bc;
+  adjwt::FilterBank fb;
+  int image_pitch;
+  int64_t num_coeffs;
+  std::vector<int64_t> band_offsets;  // 3J+1 packed order
+  std::vector<int> band_rows, band_cols, band_pitch;
+  std::vector<adjwt::Level> lv;       // lv[j-1] = level j
+  int64_t ll_buf_floats[2];           // ping-pong LL buffer sizes (odd / even levels)
+  float* d_tables = nullptr;          // device copy of all 1/c tables
+};
+
+struct adjwt_blur_plan {
+  int rows, cols, bc, kr, kc, image_pitch;
+  double taps_r[2 * adjwt::kMaxBlurRadius + 1], taps_c[2 * adjwt::kMaxBlurRadius + 1];
+};
+
+namespace adjwt {
+
+// ---------------------------------------------------------------- launchers (stream-ordered)
+struct ProxArgs {
+  float* x;          // packed coefficient buffers (state), null = plain W^* output
+  float* y;
+  float step;        // 1/L_f
+  float thresh;      // lambda/L_f
+  float beta;        // (t_k - 1)/t_{k+1}
+  double* l1_partials;  // per-CTA partial sums of |x_k| (null = skip)
+};
+
+// W (wt_synth): coeffs -> image.  ws holds the LL ping-pong buffers.
+int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, float* llbuf0, float* llbuf1,
+                    cudaStream_t s);
+// Analysis direction: W^* (adjoint = true) or W^dagger.  With prox.x != null
+// the final bands are not written to `coeffs` but fed to the FISTA prox step.
+int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs, bool adjoint,
+                       const ProxArgs& prox, float* llbuf0, float* llbuf1, cudaStream_t s, int* l1_slots_used);
+int wt_l1_partial_slots(const adjwt_wt_plan* p);
+
+// Blur family.
+int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s);
+int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b, float* g, double* partials,
+                       cudaStream_t s, int* nparts);
+int launch_blur_residual_norm(const adjwt_blur_plan* p, const float* u, const float* b, double* partials,
+                              cudaStream_t s, int* nparts);
+int blur_partial_slots(const adjwt_blur_plan* p);
+
+// Deterministic sum of float64 partials: out[0] = scale0 * sum(a[0..na)) + scale1 * sum(b[0..nb)).
+int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,
+                        double* out, cudaStream_t s);
+
+// Convolution family.
+int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                        float* grad_h, float* grad_s, float* partials, cudaStream_t st);
+int64_t conv_partial_floats(int batch, int64_t n, int k);
+int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
+                         cudaStream_t st);
+
+
+}  // namespace adjwt

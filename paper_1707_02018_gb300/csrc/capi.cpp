@@ -1,0 +1,263 @@
+// extern "C" entry points of libadjwt: argument validation, workspace
+// carving, and dispatch to the stream-ordered launchers.  Nothing here throws;
+// every failure returns an ADJWT_ERR_* code and records a message.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "adjwt_internal.h"
+
+namespace adjwt {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return ADJWT_ERR_CUDA;
+}
+
+size_t fista_workspace_bytes(const adjwt_fista_problem* pr);
+int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, double* objective_out,
+                    cudaStream_t s);
+int fista_objective_impl(const adjwt_fista_problem* pr, const float* x, void* ws, double* out, cudaStream_t s);
+int fista_lipschitz_impl(const adjwt_fista_problem* pr, float* v, int iters, void* ws, double* out,
+                         cudaStream_t s);
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+int check_ptr(const void* p, const char* name) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (!aligned16(p)) return fail(ADJWT_ERR_ALIGN, std::string(name) + " is not 16-byte aligned");
+  return ADJWT_OK;
+}
+
+int check_ws(const void* ws, size_t have, size_t need, const char* who) {
+  if (need == 0) return ADJWT_OK;
+  if (!ws) return fail(ADJWT_ERR_WORKSPACE, std::string(who) + ": workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return fail(ADJWT_ERR_WORKSPACE, std::string(who) + ": workspace not 256-byte aligned");
+  if (have < need)
+    return fail(ADJWT_ERR_WORKSPACE, std::string(who) + ": workspace of " + std::to_string(have) +
+                                         " bytes, need " + std::to_string(need));
+  return ADJWT_OK;
+}
+
+size_t image_bytes(int rows, int pitch) { return static_cast<size_t>(rows) * pitch * sizeof(float); }
+
+void split_wt_ws(const adjwt_wt_plan* p, void* ws, float** b0, float** b1) {
+  char* base = static_cast<char*>(ws);
+  *b0 = reinterpret_cast<float*>(base);
+  *b1 = reinterpret_cast<float*>(base + round_up(p->ll_buf_floats[0] * 4, 256));
+}
+
+int wt_common(const adjwt_wt_plan* p, const float* in, size_t in_bytes, const float* out, size_t out_bytes,
+              void* ws, size_t ws_bytes, const char* who) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, std::string(who) + ": plan is NULL");
+  int rc = check_ptr(in, "input");
+  if (!rc) rc = check_ptr(out, "output");
+  if (rc) return rc;
+  if (overlap(in, in_bytes, out, out_bytes)) return fail(ADJWT_ERR_ALIAS, std::string(who) + ": output overlaps input");
+  rc = check_ws(ws, ws_bytes, adjwt_wt_workspace_size(p), who);
+  if (rc) return rc;
+  if (ws && (overlap(ws, adjwt_wt_workspace_size(p), in, in_bytes) ||
+             overlap(ws, adjwt_wt_workspace_size(p), out, out_bytes)))
+    return fail(ADJWT_ERR_ALIAS, std::string(who) + ": workspace overlaps a tensor");
+  return ADJWT_OK;
+}
+
+int check_problem(const adjwt_fista_problem* pr) {
+  if (!pr || !pr->wt || !pr->blur) return fail(ADJWT_ERR_INVALID_ARG, "fista: problem or plan is NULL");
+  if (pr->wt->rows != pr->blur->rows || pr->wt->cols != pr->blur->cols)
+    return fail(ADJWT_ERR_SHAPE, "fista: wavelet and blur plans describe different images");
+  if (!(pr->lambda >= 0.0) || !std::isfinite(pr->lambda)) return fail(ADJWT_ERR_INVALID_ARG, "fista: bad lambda");
+  if (!(pr->lipschitz > 0.0) || !std::isfinite(pr->lipschitz))
+    return fail(ADJWT_ERR_INVALID_ARG, "fista: lipschitz must be finite and > 0");
+  return check_ptr(pr->b, "b");
+}
+
+}  // namespace
+}  // namespace adjwt
+
+using namespace adjwt;
+
+extern "C" const char* adjwt_last_error(void) { return g_last_error.c_str(); }
+extern "C" int adjwt_version(void) { return 1; }
+
+extern "C" int wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, void* ws, size_t ws_bytes,
+                        adjwt_stream_t stream) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, "wt_synth: plan is NULL");
+  int rc = wt_common(p, coeffs, p->num_coeffs * 4, image, image_bytes(p->rows, p->image_pitch), ws, ws_bytes,
+                     "wt_synth");
+  if (rc) return rc;
+  float *b0, *b1;
+  split_wt_ws(p, ws, &b0, &b1);
+  return launch_wt_synth(p, coeffs, image, b0, b1, stream);
+}
+
+static int analysis_entry(const adjwt_wt_plan* p, const float* image, float* coeffs, void* ws, size_t ws_bytes,
+                          adjwt_stream_t stream, bool adjoint, const char* who) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, std::string(who) + ": plan is NULL");
+  int rc = wt_common(p, image, image_bytes(p->rows, p->image_pitch), coeffs, p->num_coeffs * 4, ws, ws_bytes, who);
+  if (rc) return rc;
+  float *b0, *b1;
+  split_wt_ws(p, ws, &b0, &b1);
+  ProxArgs none{};
+  return launch_wt_analysis(p, image, coeffs, adjoint, none, b0, b1, stream, nullptr);
+}
+
+extern "C" int wt_synth_adjoint(const adjwt_wt_plan* p, const float* image, float* coeffs, void* ws,
+                                size_t ws_bytes, adjwt_stream_t stream) {
+  return analysis_entry(p, image, coeffs, ws, ws_bytes, stream, true, "wt_synth_adjoint");
+}
+
+extern "C" int wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs, void* ws, size_t ws_bytes,
+                           adjwt_stream_t stream) {
+  return analysis_entry(p, image, coeffs, ws, ws_bytes, stream, false, "wt_analysis");
+}
+
+static int blur_entry(const adjwt_blur_plan* p, const float* in, float* out, adjwt_stream_t stream, bool adjoint) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, "blur: plan is NULL");
+  int rc = check_ptr(in, "input");
+  if (!rc) rc = check_ptr(out, "output");
+  if (rc) return rc;
+  const size_t nb = image_bytes(p->rows, p->image_pitch);
+  if (overlap(in, nb, out, nb)) return fail(ADJWT_ERR_ALIAS, "blur: output overlaps input");
+  return launch_blur(p, in, out, adjoint, stream);
+}
+
+extern "C" int blur(const adjwt_blur_plan* p, const float* in, float* out, adjwt_stream_t stream) {
+  return blur_entry(p, in, out, stream, false);
+}
+
+extern "C" int blur_adjoint(const adjwt_blur_plan* p, const float* in, float* out, adjwt_stream_t stream) {
+  return blur_entry(p, in, out, stream, true);
+}
+
+extern "C" int blur_normal(const adjwt_blur_plan* p, const float* u, const float* b, float* g, double* half_sq_out,
+                           void* ws, size_t ws_bytes, adjwt_stream_t stream) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, "blur_normal: plan is NULL");
+  int rc = check_ptr(u, "u");
+  if (!rc) rc = check_ptr(g, "g");
+  if (!rc && b) rc = check_ptr(b, "b");
+  if (rc) return rc;
+  const size_t nb = image_bytes(p->rows, p->image_pitch);
+  if (overlap(u, nb, g, nb) || (b && overlap(b, nb, g, nb)))
+    return fail(ADJWT_ERR_ALIAS, "blur_normal: g overlaps an input");
+  double* parts = nullptr;
+  if (half_sq_out) {
+    rc = check_ws(ws, ws_bytes, adjwt_blur_workspace_size(p), "blur_normal");
+    if (rc) return rc;
+    parts = static_cast<double*>(ws);
+  }
+  int np = 0;
+  rc = launch_blur_normal(p, u, b, g, parts, stream, &np);
+  if (rc) return rc;
+  if (half_sq_out) return launch_sum_partials(parts, np, 1.0, nullptr, 0, 0.0, half_sq_out, stream);
+  return ADJWT_OK;
+}
+
+extern "C" size_t adjwt_conv_adjoint_workspace_size(int batch, int64_t n, int k) {
+  if (batch <= 0 || n <= 0 || k <= 0) return 0;
+  return static_cast<size_t>(round_up(conv_partial_floats(batch, n, k) * 4, 256));
+}
+
+extern "C" int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                            float* grad_h, float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream) {
+  if (batch < 0 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: need batch >= 0, n >= 1, k >= 1");
+  if (batch > 65535) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: batch above 65535");
+  if (batch == 0 || (!grad_h && !grad_s)) return ADJWT_OK;
+  int rc = check_ptr(r, "r");
+  if (!rc && grad_h) rc = check_ptr(s, "s");
+  if (!rc && grad_s) rc = check_ptr(h, "h");
+  if (!rc && grad_h) rc = check_ptr(grad_h, "grad_h");
+  if (!rc && grad_s) rc = check_ptr(grad_s, "grad_s");
+  if (rc) return rc;
+  const size_t sb = (size_t)batch * n * 4, hb = (size_t)batch * k * 4, rb = (size_t)batch * (n + k - 1) * 4;
+  if (grad_h && (overlap(grad_h, hb, s, sb) || overlap(grad_h, hb, r, rb) || (h && overlap(grad_h, hb, h, hb))))
+    return fail(ADJWT_ERR_ALIAS, "conv_adjoint: grad_h overlaps an input");
+  if (grad_s && (overlap(grad_s, sb, r, rb) || overlap(grad_s, sb, h, hb) || (s && overlap(grad_s, sb, s, sb))))
+    return fail(ADJWT_ERR_ALIAS, "conv_adjoint: grad_s overlaps an input");
+  if (grad_h) {
+    rc = check_ws(ws, ws_bytes, adjwt_conv_adjoint_workspace_size(batch, n, k), "conv_adjoint");
+    if (rc) return rc;
+  }
+  return launch_conv_adjoint(batch, n, k, s, h, r, grad_h, grad_s, static_cast<float*>(ws), stream);
+}
+
+extern "C" int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
+                             adjwt_stream_t stream) {
+  if (batch < 0 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "conv_residual: need batch >= 0, n >= 1, k >= 1");
+  if (batch > 65535) return fail(ADJWT_ERR_SHAPE, "conv_residual: batch above 65535");
+  if (batch == 0) return ADJWT_OK;
+  int rc = check_ptr(h, "h");
+  if (!rc) rc = check_ptr(s, "s");
+  if (!rc) rc = check_ptr(r, "r");
+  if (!rc && x) rc = check_ptr(x, "x");
+  if (rc) return rc;
+  const size_t rb = (size_t)batch * (n + k - 1) * 4;
+  if (overlap(r, rb, h, (size_t)batch * k * 4) || overlap(r, rb, s, (size_t)batch * n * 4))
+    return fail(ADJWT_ERR_ALIAS, "conv_residual: r overlaps an input");
+  return launch_conv_residual(batch, n, k, h, s, x, r, stream);
+}
+
+extern "C" size_t adjwt_fista_workspace_size(const adjwt_fista_problem* pr) {
+  if (!pr || !pr->wt || !pr->blur) return 0;
+  return fista_workspace_bytes(pr);
+}
+
+extern "C" int fista_step(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, size_t ws_bytes,
+                          double* objective_out, adjwt_stream_t stream) {
+  int rc = check_problem(pr);
+  if (rc) return rc;
+  if (!st) return fail(ADJWT_ERR_INVALID_ARG, "fista_step: state is NULL");
+  rc = check_ptr(st->x, "x");
+  if (!rc) rc = check_ptr(st->y, "y");
+  if (rc) return rc;
+  if (!(st->t >= 1.0) || !std::isfinite(st->t)) return fail(ADJWT_ERR_INVALID_ARG, "fista_step: t must be >= 1");
+  const size_t cb = pr->wt->num_coeffs * 4;
+  if (overlap(st->x, cb, st->y, cb)) return fail(ADJWT_ERR_ALIAS, "fista_step: x and y overlap");
+  rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "fista_step");
+  if (rc) return rc;
+  return fista_step_impl(pr, st, ws, objective_out, stream);
+}
+
+extern "C" int adjwt_fista_objective(const adjwt_fista_problem* pr, const float* x, void* ws, size_t ws_bytes,
+                                     double* objective_out, adjwt_stream_t stream) {
+  int rc = check_problem(pr);
+  if (rc) return rc;
+  rc = check_ptr(x, "x");
+  if (rc) return rc;
+  if (!objective_out) return fail(ADJWT_ERR_INVALID_ARG, "objective_out is NULL");
+  rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "fista_objective");
+  if (rc) return rc;
+  return fista_objective_impl(pr, x, ws, objective_out, stream);
+}
+
+extern "C" int adjwt_fista_lipschitz(const adjwt_fista_problem* pr, float* v, int iters, void* ws, size_t ws_bytes,
+                                     double* lipschitz_out, adjwt_stream_t stream) {
+  if (!pr || !pr->wt || !pr->blur) return fail(ADJWT_ERR_INVALID_ARG, "fista_lipschitz: problem or plan is NULL");
+  if (pr->wt->rows != pr->blur->rows || pr->wt->cols != pr->blur->cols)
+    return fail(ADJWT_ERR_SHAPE, "fista_lipschitz: plans describe different images");
+  int rc = check_ptr(v, "v");
+  if (rc) return rc;
+  if (iters < 1) return fail(ADJWT_ERR_INVALID_ARG, "fista_lipschitz: iters must be >= 1");
+  if (!lipschitz_out) return fail(ADJWT_ERR_INVALID_ARG, "lipschitz_out is NULL");
+  rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "fista_lipschitz");
+  if (rc) return rc;
+  return fista_lipschitz_impl(pr, v, iters, ws, lipschitz_out, stream);
+}

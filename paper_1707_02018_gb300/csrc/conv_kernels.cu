@@ -1,0 +1,177 @@
+// Blind-channel gradients of Sec. II (Eq. 5), batched over independent rows.
+//
+//   grad_s[m] = sum_{i<K} h[i] r[i+m]   (m < N)   -- H^T r, valid correlation
+//   grad_h[j] = sum_{i<N} s[i] r[i+j]   (j < K)   -- S^T r, valid correlation
+//   r = h * s - x                                  -- the residual (full conv)
+//
+// One CTA owns a chunk of kChunk samples of one row: it stages r (with the
+// K-1 tail), s and h in shared memory, writes grad_s for its chunk and a
+// partial grad_h over its chunk to workspace; a second pass sums the partials
+// of each row in a fixed order (deterministic, no atomics).
+#include <algorithm>
+
+#include "adjwt_internal.h"
+#include "device_common.cuh"
+
+namespace adjwt {
+namespace {
+
+constexpr int kChunk = 1024;
+constexpr int kThreads = 256;
+constexpr int kMaxK = 4096;
+
+__global__ void __launch_bounds__(kThreads) k_conv_adjoint(int64_t n, int K, const float* __restrict__ s,
+                                                           const float* __restrict__ h, const float* __restrict__ r,
+                                                           float* __restrict__ grad_s, float* __restrict__ part_h,
+                                                           int nchunks) {
+  extern __shared__ float sm[];
+  float* rs = sm;                    // kChunk + K - 1
+  float* ss = rs + kChunk + K - 1;   // kChunk
+  float* hs = ss + kChunk;           // K
+  float* red = hs + K;               // kThreads
+  const int b = blockIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t nr = n + K - 1;
+  const float* rrow = r + (size_t)b * nr;
+  const float* srow = s + (size_t)b * n;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kChunk + K - 1; i += kThreads) {
+    const int64_t g = m0 + i;
+    rs[i] = g < nr ? __ldg(rrow + g) : 0.0f;
+  }
+  for (int i = tid; i < kChunk; i += kThreads) {
+    const int64_t g = m0 + i;
+    ss[i] = g < n ? __ldg(srow + g) : 0.0f;
+  }
+  if (h)
+    for (int i = tid; i < K; i += kThreads) hs[i] = __ldg(h + (size_t)b * K + i);
+  __syncthreads();
+
+  if (grad_s) {
+    float acc[kChunk / kThreads];
+#pragma unroll
+    for (int q = 0; q < kChunk / kThreads; ++q) acc[q] = 0.0f;
+    for (int i = 0; i < K; ++i) {
+      const float hv = hs[i];
+#pragma unroll
+      for (int q = 0; q < kChunk / kThreads; ++q) acc[q] = fmaf(hv, rs[tid + q * kThreads + i], acc[q]);
+    }
+    float* out = grad_s + (size_t)b * n;
+#pragma unroll
+    for (int q = 0; q < kChunk / kThreads; ++q) {
+      const int64_t m = m0 + tid + q * kThreads;
+      if (m < n) out[m] = acc[q];
+    }
+  }
+
+  if (part_h) {
+    // lags are spread over the threads; each lag's sample range is split in P parts
+    const int P = K >= kThreads ? 1 : kThreads / K;
+    const int span = (kChunk + P - 1) / P;
+    float* dst = part_h + ((size_t)b * nchunks + blockIdx.x) * K;
+    for (int j0 = 0; j0 < K; j0 += kThreads / P) {
+      const int j = j0 + tid % (kThreads / P);
+      const int part = tid / (kThreads / P);
+      float acc = 0.0f;
+      if (j < K && part < P) {
+        const int i0 = part * span, i1 = min(kChunk, i0 + span);
+        for (int i = i0; i < i1; ++i) acc = fmaf(ss[i], rs[i + j], acc);
+      }
+      red[tid] = acc;
+      __syncthreads();
+      if (tid < kThreads / P && j0 + tid < K) {
+        float t = 0.0f;
+        for (int p = 0; p < P; ++p) t += red[p * (kThreads / P) + tid];
+        dst[j0 + tid] = t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_conv_reduce(int K, int nchunks, const float* __restrict__ part_h, float* __restrict__ grad_h,
+                              int64_t total) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t b = idx / K;
+  const int j = static_cast<int>(idx - b * K);
+  const float* p = part_h + (size_t)b * nchunks * K + j;
+  float acc = 0.0f;
+  for (int c = 0; c < nchunks; ++c) acc += p[(size_t)c * K];
+  grad_h[idx] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_conv_residual(int64_t n, int K, const float* __restrict__ h,
+                                                            const float* __restrict__ s, const float* __restrict__ x,
+                                                            float* __restrict__ r) {
+  extern __shared__ float sm[];
+  float* seg = sm;                  // s[m0 - K + 1 .. m0 + kChunk)
+  float* hs = seg + kChunk + K - 1;
+  const int b = blockIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t nr = n + K - 1;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kChunk + K - 1; i += kThreads) {
+    const int64_t g = m0 - (K - 1) + i;
+    seg[i] = (g >= 0 && g < n) ? __ldg(s + (size_t)b * n + g) : 0.0f;
+  }
+  for (int i = tid; i < K; i += kThreads) hs[i] = __ldg(h + (size_t)b * K + i);
+  __syncthreads();
+  for (int q = 0; q < kChunk / kThreads; ++q) {
+    const int mm = tid + q * kThreads;
+    const int64_t m = m0 + mm;
+    if (m >= nr) break;
+    float acc = 0.0f;
+    for (int i = 0; i < K; ++i) acc = fmaf(hs[i], seg[mm + K - 1 - i], acc);
+    if (x) acc -= __ldg(x + (size_t)b * nr + m);
+    r[(size_t)b * nr + m] = acc;
+  }
+}
+
+int64_t nchunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
+
+}  // namespace
+
+int64_t conv_partial_floats(int batch, int64_t n, int k) { return (int64_t)batch * nchunks_of(n) * k; }
+
+int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
+                        float* grad_s, float* partials, cudaStream_t st) {
+  if (k > kMaxK) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: k above 4096");
+  if (batch == 0) return ADJWT_OK;
+  const int64_t nch = nchunks_of(n);
+  if (nch > 65535 * 1024LL) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: n too large");
+  const size_t smem = (size_t)(kChunk + k - 1 + kChunk + k + kThreads) * sizeof(float);
+  if (smem > 48 * 1024)
+    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_conv_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem)));
+  dim3 grid(static_cast<unsigned>(nch), static_cast<unsigned>(batch));
+  ADJWT_TRACED("conv_adjoint", 0, st,
+               k_conv_adjoint<<<grid, kThreads, smem, st>>>(n, k, s, h, r, grad_s, grad_h ? partials : nullptr,
+                                                            static_cast<int>(nch)));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  if (grad_h) {
+    const int64_t total = (int64_t)batch * k;
+    const unsigned nb = static_cast<unsigned>((total + 255) / 256);
+    ADJWT_TRACED("conv_reduce", 0, st,
+                 k_conv_reduce<<<nb, 256, 0, st>>>(k, static_cast<int>(nch), partials, grad_h, total));
+    ADJWT_CUDA_CHECK(cudaGetLastError());
+  }
+  return ADJWT_OK;
+}
+
+int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
+                         cudaStream_t st) {
+  if (k > kMaxK) return fail(ADJWT_ERR_SHAPE, "conv_residual: k above 4096");
+  if (batch == 0) return ADJWT_OK;
+  const int64_t nr = n + k - 1;
+  const size_t smem = (size_t)(kChunk + k - 1 + k) * sizeof(float);
+  if (smem > 48 * 1024)
+    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_conv_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem)));
+  dim3 grid(static_cast<unsigned>(nchunks_of(nr)), static_cast<unsigned>(batch));
+  ADJWT_TRACED("conv_residual", 0, st, k_conv_residual<<<grid, kThreads, smem, st>>>(n, k, h, s, x, r));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+}  // namespace adjwt

@@ -1,0 +1,47 @@
+// Device helpers shared by the libadjwt kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace adjwt {
+
+__device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
+  int q = a / b;
+  return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+__device__ __forceinline__ int pos_mod(int a, int b) {  // b > 0
+  int m = a % b;
+  return m < 0 ? m + b : m;
+}
+
+// Source index of virtual position x (image coordinates) under the extension
+// `mode` (0 zero, 1 half-point symmetric, 2/3 periodic); -1 means a zero.
+__device__ __forceinline__ int ext_src(int x, int N, int mode) {
+  if (mode == 0) return (x >= 0 && x < N) ? x : -1;
+  if (mode == 1) {
+    int m = pos_mod(x, 2 * N);
+    return m < N ? m : 2 * N - 1 - m;
+  }
+  return pos_mod(x, N);
+}
+
+// Block-wide float64 sum; every thread passes its value, thread 0 gets the total.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* scratch /* NT/32 doubles */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) t += scratch[w];
+  }
+  return t;
+}
+
+}  // namespace adjwt

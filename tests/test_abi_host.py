@@ -1,0 +1,145 @@
+"""Host-side checks of the C-ABI library (no GPU needed, no kernel launched).
+
+* libadjwt.so loads and exports every function include/adjwt.h declares;
+* plan layouts (sizes, offsets, pitches) match the oracle's band sizes;
+* the device path's own filter derivation matches the oracle's taps;
+* argument validation rejects bad calls before anything reaches the device.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filters as ofilters
+from oracle import layout as olayout
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "adjwt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1707_02018_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1707_02018_gb300 import build_ext
+        build_ext.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|size_t|char)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in ["wt_synth", "wt_synth_adjoint", "blur", "blur_adjoint", "conv_adjoint", "fista_step"]:
+        assert n in names
+    for n in names:
+        assert hasattr(lib, n), f"libadjwt.so does not export {n}"
+    from paper_1707_02018_gb300._lib import PROTOTYPES
+    assert set(PROTOTYPES) == set(names)
+
+
+def _plan(lib, rows, cols, levels, w, bc):
+    h = C.c_void_p()
+    rc = lib.adjwt_wt_plan_create(C.byref(h), rows, cols, levels, w, bc)
+    return rc, h
+
+
+WAV = {"haar": 0, "db2": 1, "db4": 2, "cdf97": 3}
+
+
+@pytest.mark.parametrize("w", list(WAV))
+@pytest.mark.parametrize("bc,mode", [(0, "zero"), (3, "per")])
+@pytest.mark.parametrize("rows,cols,J", [(2048, 2048, 5), (256, 256, 3), (37, 53, 2), (64, 32, 4), (1, 1, 1)])
+def test_layout_matches_oracle(lib, w, bc, mode, rows, cols, J):
+    if mode == "per" and (rows % 2 ** J or cols % 2 ** J):
+        rc, _ = _plan(lib, rows, cols, J, WAV[w], bc)
+        assert rc == -2                                     # ADJWT_ERR_SHAPE
+        return
+    rc, h = _plan(lib, rows, cols, J, WAV[w], bc)
+    assert rc == 0, lib.adjwt_last_error()
+    nb = 3 * J + 1
+    nc = C.c_int64()
+    offs = (C.c_int64 * nb)()
+    br, bcl, bp = (C.c_int * nb)(), (C.c_int * nb)(), (C.c_int * nb)()
+    ip = C.c_int()
+    assert lib.adjwt_wt_layout(h, C.byref(nc), offs, br, bcl, bp, C.byref(ip)) == 0
+    L = ofilters.filter_bank(w).L
+    sizes = olayout.level_sizes(rows, cols, J, L, mode)
+    want = [sizes[-1][1]] + [sizes[j - 1][1] for j in range(J, 0, -1) for _ in range(3)]
+    assert [(br[i], bcl[i]) for i in range(nb)] == want
+    pos = 0
+    for i in range(nb):
+        assert offs[i] == pos and bp[i] % 4 == 0 and bp[i] >= bcl[i] and bp[i] - bcl[i] < 4
+        pos += br[i] * bp[i]
+    assert nc.value == pos
+    assert ip.value % 4 == 0 and ip.value - cols < 4
+    assert sum(r * c for r, c in want) == olayout.num_coeffs(rows, cols, J, L, mode)
+    lib.adjwt_wt_plan_destroy(h)
+
+
+@pytest.mark.parametrize("w", list(WAV))
+def test_device_path_filters_match_oracle(lib, w):
+    rc, h = _plan(lib, 64, 64, 1, WAV[w], 0)
+    assert rc == 0
+    arrs = [(C.c_double * 10)() for _ in range(4)]
+    L = C.c_int()
+    assert lib.adjwt_wt_filters(h, *arrs, C.byref(L)) == 0
+    fb = ofilters.filter_bank(w)
+    assert L.value == fb.L
+    for got, want in zip(arrs, (fb.dec_lo, fb.dec_hi, fb.rec_lo, fb.rec_hi)):
+        assert np.abs(np.array(list(got)[:fb.L]) - want).max() < 1e-13
+    lib.adjwt_wt_plan_destroy(h)
+
+
+def test_plan_argument_errors(lib):
+    h = C.c_void_p()
+    assert lib.adjwt_wt_plan_create(C.byref(h), 8, 8, 1, 7, 0) == -1       # unknown wavelet
+    assert lib.adjwt_wt_plan_create(C.byref(h), 8, 8, 1, 0, 9) == -1       # unknown bc
+    assert lib.adjwt_wt_plan_create(C.byref(h), 0, 8, 1, 0, 0) == -2       # empty image
+    assert lib.adjwt_wt_plan_create(C.byref(h), 8, 8, 0, 0, 0) == -2       # no level
+    assert lib.adjwt_wt_plan_create(C.byref(h), 12, 8, 3, 0, 3) == -2      # PER needs 2^J | size
+    assert lib.adjwt_wt_plan_create(None, 8, 8, 1, 0, 0) == -1
+    taps = (C.c_double * 4)(0.25, 0.25, 0.25, 0.25)
+    assert lib.adjwt_blur_plan_create(C.byref(h), 8, 8, taps, 4, taps, 3, 1) == -1   # even length
+    assert lib.adjwt_blur_plan_create(C.byref(h), 8, 8, taps, 3, taps, 3, 2) == -1   # PPD not a blur bc
+    assert b"odd" in lib.adjwt_last_error() or len(lib.adjwt_last_error()) > 0
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="fake-pointer validation runs on the host only")
+def test_call_validation_before_launch(lib):
+    """Calls that must fail in validation (fake addresses are never dereferenced)."""
+    rc, h = _plan(lib, 16, 16, 1, 1, 0)
+    assert rc == 0
+    ws_need = lib.adjwt_wt_workspace_size(h)
+    assert ws_need > 0
+    a, b, ws = 0x10000000, 0x20000000, 0x30000000
+    assert lib.wt_synth(h, None, b, ws, ws_need, None) == -1
+    assert lib.wt_synth(h, a + 4, b, ws, ws_need, None) == -3              # misaligned
+    assert lib.wt_synth(h, a, a + 16, ws, ws_need, None) == -4             # aliasing
+    assert lib.wt_synth(h, a, b, None, ws_need, None) == -7                # no workspace
+    assert lib.wt_synth(h, a, b, ws + 16, ws_need, None) == -7             # misaligned workspace
+    assert lib.wt_synth(h, a, b, ws, ws_need - 1, None) == -7              # small workspace
+    assert lib.wt_synth(None, a, b, ws, ws_need, None) == -1
+    assert lib.conv_adjoint(-1, 5, 3, a, b, ws, None, None, None, 0, None) == -2
+    assert lib.conv_adjoint(4, 0, 3, a, b, ws, None, None, None, 0, None) == -2
+    assert lib.conv_adjoint(0, 5, 3, None, None, None, None, None, None, 0, None) == 0   # empty batch
+    assert lib.conv_adjoint(2, 5, 3, a, b, ws, a, None, None, 0, None) == -4  # grad_h over s
+    lib.adjwt_wt_plan_destroy(h)
+
+
+def test_workspace_sizes(lib):
+    assert lib.adjwt_conv_adjoint_workspace_size(256, 65536, 64) >= 256 * 64 * 64 * 4
+    assert lib.adjwt_conv_adjoint_workspace_size(0, 10, 3) == 0
+    rc, h = _plan(lib, 2048, 2048, 5, 3, 3)
+    assert rc == 0
+    assert lib.adjwt_wt_workspace_size(h) >= (1024 * 1024 + 512 * 512) * 4
+    lib.adjwt_wt_plan_destroy(h)

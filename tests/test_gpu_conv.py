@@ -1,0 +1,71 @@
+"""Parity of the CUDA blind-channel gradients with the float64 oracle (Sec. II, Eq. 5)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import conv as oconv
+from synthetic_inputs import channel_problem, random_vector
+from tests.gpu_util import assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def adj():
+    import paper_1707_02018_gb300 as adj
+    adj.lib()
+    return adj
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous()
+
+
+def test_paper_k3_n5_exact(adj):
+    """Integer data of the K = 3, N = 5 example: float32 sums are exact."""
+    h = np.array([[2.0, -1.0, 3.0]])
+    s = np.array([[1.0, 4.0, -2.0, 5.0, 3.0]])
+    r = np.array([[1.0, -2.0, 0.0, 7.0, 2.0, -1.0, 4.0]])
+    gh, gs = adj.conv_adjoint(dev(s), dev(h), dev(r))
+    wh, ws = oconv.conv_adjoint(s, h, r)
+    assert np.array_equal(gh.cpu().numpy(), wh) and np.array_equal(gs.cpu().numpy(), ws)
+    x = np.array([[0.0, 1.0, 0.0, 0.0, 2.0, 0.0, 1.0]])
+    res = adj.conv_residual(dev(h), dev(s), dev(x))
+    assert np.array_equal(res.cpu().numpy(), oconv.conv_full(h, s) - x)
+
+
+@pytest.mark.parametrize("B,n,k", [(3, 5, 3), (2, 1, 1), (4, 1000, 64), (2, 1025, 7), (1, 3, 9), (5, 3000, 300),
+                                   (2, 2048, 257), (1, 4097, 1)])
+def test_conv_parity(adj, B, n, k):
+    p = channel_problem(B, n, k, seed=B * 1000 + n + k)
+    x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
+    r = oconv.conv_full(p["h_est"], p["s_est"]) - x
+    gh, gs = adj.conv_adjoint(dev(p["s_est"]), dev(p["h_est"]), dev(r))
+    wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r)
+    assert_close(gh.cpu().numpy(), wh, what=f"grad_h {B}x{n}x{k}")
+    assert_close(gs.cpu().numpy(), ws, what=f"grad_s {B}x{n}x{k}")
+    rr = adj.conv_residual(dev(p["h_est"]), dev(p["s_est"]), dev(x))
+    assert_close(rr.cpu().numpy(), r, what=f"residual {B}x{n}x{k}")
+
+
+def test_one_gradient_only_and_empty(adj):
+    s, h = dev(random_vector((2, 50), 1)), dev(random_vector((2, 4), 2))
+    r = dev(random_vector((2, 53), 3))
+    gh, gs = adj.conv_adjoint(s, h, r, grad_s=False)
+    assert gs is None and gh.shape == (2, 4)
+    gh2, gs2 = adj.conv_adjoint(s, h, r, grad_h=False)
+    assert gh2 is None and gs2.shape == (2, 50)
+    e = torch.empty(0, 50, device="cuda")
+    gh, gs = adj.conv_adjoint(e, torch.empty(0, 4, device="cuda"), torch.empty(0, 53, device="cuda"))
+    assert gh.numel() == 0 and gs.numel() == 0
+
+
+def test_full_size_256x65536x64(adj):
+    """The bench workload (256 signals of 65,536 samples, 64-tap channels), in full."""
+    p = channel_problem(256, 65536, 64, seed=2)
+    x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
+    r = oconv.conv_full(p["h_est"], p["s_est"]) - x
+    gh, gs = adj.conv_adjoint(dev(p["s_est"]), dev(p["h_est"]), dev(r))
+    wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r)
+    assert_close(gh.cpu().numpy(), wh, what="grad_h full")
+    assert_close(gs.cpu().numpy(), ws, what="grad_s full")

@@ -1,0 +1,111 @@
+"""Parity of the CUDA W, W^* and W^dagger with the float64 oracle (Sec. I-A, Eq. 2-4)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import wavelet as owt
+from synthetic_inputs import piecewise_smooth_image, random_vector
+from tests.gpu_util import assert_close, image_dev, to_host_image
+
+pytestmark = pytest.mark.gpu
+
+WAVELETS = ["haar", "db2", "db4", "cdf97"]
+MODES = ["zero", "sym", "ppd", "per"]
+# several tiles with ragged tails, thin images, tiny images (N <= 2L': gather path)
+SHAPES = [(64, 48, 2), (70, 45, 3), (33, 97, 2), (5, 7, 2), (1, 1, 1), (2, 3, 1), (19, 130, 1)]
+
+
+@pytest.fixture(scope="module")
+def adj():
+    import paper_1707_02018_gb300 as adj
+    adj.lib()
+    return adj
+
+
+def _shapes(mode):
+    out = []
+    for r, c, J in SHAPES:
+        if mode == "per":
+            r, c = r + (-r) % 2 ** J, c + (-c) % 2 ** J
+        out.append((r, c, J))
+    return out
+
+
+@pytest.mark.parametrize("w", WAVELETS)
+@pytest.mark.parametrize("mode", MODES)
+def test_adjoint_analysis_synthesis_parity(adj, w, mode):
+    for rows, cols, J in _shapes(mode):
+        plan = adj.WtPlan(rows, cols, J, w, mode)
+        img = random_vector((rows, cols), rows * 1000 + cols)
+        dimg = image_dev(plan, img)
+        got = adj.wt_synth_adjoint(plan, dimg)
+        torch.cuda.synchronize()
+        want = owt.wt_adjoint(img, J, w, mode)
+        assert_close(plan.unpack(got).cpu().numpy(), want, what=f"W^* {w} {mode} {rows}x{cols} J{J}")
+        # padding of every band is written as zero
+        assert float((got.abs().sum() - plan.unpack(got).abs().sum()).abs()) < 1e-3 * float(got.abs().sum() + 1)
+        got = adj.wt_analysis(plan, dimg)
+        want = owt.wt_pinv(img, J, w, mode)
+        assert_close(plan.unpack(got).cpu().numpy(), want, what=f"W^dagger {w} {mode} {rows}x{cols}")
+        x = random_vector(plan.logical_size, rows + cols)
+        out = adj.wt_synth(plan, plan.pack(x))
+        want = owt.wt_synth(x, rows, cols, J, w, mode)
+        assert_close(to_host_image(out, rows, cols), want, what=f"W {w} {mode} {rows}x{cols}")
+
+
+@pytest.mark.parametrize("mode", ["sym", "per", "zero"])
+def test_full_size_cdf97_five_levels(adj, mode):
+    """The 2048 x 2048, 5-level CDF 9/7 operators of the bench, compared in full."""
+    rows = cols = 2048
+    plan = adj.WtPlan(rows, cols, 5, "cdf97", mode)
+    img = piecewise_smooth_image(rows, cols, 11)
+    got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
+    want = owt.wt_adjoint(img, 5, "cdf97", mode)
+    assert_close(plan.unpack(got).cpu().numpy(), want, what=f"W^* 2048 {mode}")
+    x = random_vector(plan.logical_size, 5)
+    out = adj.wt_synth(plan, plan.pack(x))
+    want = owt.wt_synth(x, rows, cols, 5, "cdf97", mode)
+    assert_close(to_host_image(out, rows, cols), want, what=f"W 2048 {mode}")
+
+
+@pytest.mark.parametrize("w", WAVELETS)
+@pytest.mark.parametrize("mode", MODES)
+def test_gpu_dot_product_and_reconstruction(adj, w, mode):
+    rows, cols, J = (96, 64, 3)
+    plan = adj.WtPlan(rows, cols, J, w, mode)
+    x = plan.pack(random_vector(plan.logical_size, 1))
+    yimg = image_dev(plan, random_vector((rows, cols), 2))
+    Wx = adj.wt_synth(plan, x)
+    Wty = adj.wt_synth_adjoint(plan, yimg)
+    lhs = float((Wx[:, :cols].double() * yimg[:, :cols].double()).sum())
+    rhs = float((x.double() * Wty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    u = image_dev(plan, piecewise_smooth_image(rows, cols, 3))
+    rec = adj.wt_synth(plan, adj.wt_analysis(plan, u))
+    assert float((rec - u)[:, :cols].abs().max()) < 1e-5
+
+
+def test_repeated_calls_and_streams(adj):
+    """Plans are reusable and stream-ordered: two streams, same plan, same result."""
+    plan = adj.WtPlan(130, 70, 3, "db4", "sym")
+    img = image_dev(plan, random_vector((130, 70), 9))
+    ref = adj.wt_synth_adjoint(plan, img).clone()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        a = adj.wt_synth_adjoint(plan, img)
+    with torch.cuda.stream(s2):
+        b = adj.wt_synth_adjoint(plan, img)
+    torch.cuda.synchronize()
+    assert torch.equal(a, ref) and torch.equal(b, ref)
+
+
+def test_errors_reach_python(adj):
+    plan = adj.WtPlan(16, 16, 1, "db2", "sym")
+    buf = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    img = buf[:256].view(16, 16)
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.wt_synth_adjoint(plan, img, coeffs=buf[64:64 + plan.num_coeffs])   # output aliases input
+    assert e.value.code == -4
+    with pytest.raises(adj.AdjwtError):
+        adj.WtPlan(12, 16, 3, "db2", "per")
