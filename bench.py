@@ -235,12 +235,14 @@ def ours(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for k in range(args.steps):
         if k == args.steps - traced:
             adj.trace_enable(traced * 64)
         run_step(adj, probs, ch)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     ms_local = e0.elapsed_time(e1)

@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   const int tid = threadIdx.x;
   const int t0r = blockIdx.y * kTile, t0c = blockIdx.x * kTile;
   const bool sym = a.mode == 1;
+  // filter index m = x + off - 2k - 1: the extended modes carry the L' shift of
+  // the extension on top of the bank's delay L'; the circular mode has none
+  const int off = a.mode == 3 ? Lp : 2 * Lp;
   int xa[2], xb[2], ka[2], nk[2];
   {
     const int t0[2] = {t0r, t0c};
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
     for (int ax = 0; ax < 2; ++ax) {
       xa[ax] = (sym && t0[ax] < Lp) ? -Lp : t0[ax];
       xb[ax] = (sym && t0[ax] + kTile > N[ax] - Lp) ? N[ax] + Lp : t0[ax] + kTile;
-      ka[ax] = floor_div(xa[ax] + Lp, 2);
-      nk[ax] = floor_div(xb[ax] + 2 * Lp - 2, 2) - ka[ax] + 1;
+      ka[ax] = floor_div(xa[ax] + off - Lp, 2);
+      nk[ax] = floor_div(xb[ax] + off - 2, 2) - ka[ax] + 1;
     }
   }
   const int nx_r = xb[0] - xa[0], nx_c = xb[1] - xa[1];
@@ -210,12 +213,12 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
     const int rem = i - hb * nx_r * nk[1];
     const int xx = rem / nk[1], ll = rem - xx * nk[1];
     const int x = xa[0] + xx;
-    const int m0 = (x + 1) & 1;
+    const int m0 = (x + off - 1) & 1;
     float acc = 0.0f;
 #pragma unroll
     for (int q = 0; q < L / 2; ++q) {
       const int m = m0 + 2 * q;
-      const int kk = ((x + 2 * Lp - 1 - m) >> 1) - ka[0];
+      const int kk = ((x + off - 1 - m) >> 1) - ka[0];
       acc = fmaf(C[2 * hb][kk][ll], a.g[0][m], acc);
       acc = fmaf(C[2 * hb + 1][kk][ll], a.g[1][m], acc);
     }
@@ -246,12 +249,12 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   for (int i = tid; i < kTile * nx_c; i += kThreads) {
     const int tt = i / nx_c, xx = i - tt * nx_c;
     const int x = xa[1] + xx;
-    const int m0 = (x + 1) & 1;
+    const int m0 = (x + off - 1) & 1;
     float acc = 0.0f;
 #pragma unroll
     for (int q = 0; q < L / 2; ++q) {
       const int m = m0 + 2 * q;
-      const int ll = ((x + 2 * Lp - 1 - m) >> 1) - ka[1];
+      const int ll = ((x + off - 1 - m) >> 1) - ka[1];
       acc = fmaf(G[0][tt][ll], a.g[0][m], acc);
       acc = fmaf(G[1][tt][ll], a.g[1][m], acc);
     }
