@@ -140,6 +140,24 @@ int blur_normal(const adjwt_blur_plan* plan, const float* u, const float* b, flo
 size_t adjwt_conv_adjoint_workspace_size(int batch, int64_t n, int k);
 int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
                  float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+/* conv_adjoint without a workspace argument (the paper has no counterpart;
+ * this is a deployment variant).  It is for callers that must not allocate
+ * device memory on their call path: processes whose device memory is owned by
+ * another allocator (a framework's pool, a fixed budget), loops in which the
+ * device-wide synchronisation of cudaMalloc/cudaFree is not acceptable, and
+ * deployments that forbid allocation after start-up.  The grad_h partial sums
+ * go to a fixed 4 MiB array (2^20 floats) in the library's device memory,
+ * which every GPU that loads the library holds until the process exits; the
+ * call itself allocates nothing.  Limit: when grad_h is requested,
+ * batch * ceil(n/1024) * k <= 2^20, else ADJWT_ERR_WORKSPACE and nothing runs.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Results equal conv_adjoint's; arguments, layouts and errors as there. */
+int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                         float* grad_h, float* grad_s, adjwt_stream_t stream);
+
 /* Residual of the full convolution, r = h * s - x (x may be NULL: r = h * s). */
 int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                   adjwt_stream_t stream);

@@ -121,6 +121,9 @@ int launch_sum_partials(const double* a, int na, double scale_a, const double* b
 int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
                         float* grad_h, float* grad_s, float* partials, cudaStream_t st);
 int64_t conv_partial_floats(int batch, int64_t n, int k);
+int64_t conv_static_scratch_floats();
+int launch_conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                                float* grad_h, float* grad_s, cudaStream_t st);
 int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                          cudaStream_t st);
 

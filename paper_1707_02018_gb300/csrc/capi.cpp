@@ -199,6 +199,31 @@ extern "C" int conv_adjoint(int batch, int64_t n, int k, const float* s, const f
   return launch_conv_adjoint(batch, n, k, s, h, r, grad_h, grad_s, static_cast<float*>(ws), stream);
 }
 
+extern "C" int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                                    float* grad_h, float* grad_s, adjwt_stream_t stream) {
+  if (batch < 0 || n < 1 || k < 1)
+    return fail(ADJWT_ERR_SHAPE, "conv_adjoint_noalloc: need batch >= 0, n >= 1, k >= 1");
+  if (batch > 65535) return fail(ADJWT_ERR_SHAPE, "conv_adjoint_noalloc: batch above 65535");
+  if (batch == 0 || (!grad_h && !grad_s)) return ADJWT_OK;
+  if (grad_h && conv_partial_floats(batch, n, k) > conv_static_scratch_floats())
+    return fail(ADJWT_ERR_WORKSPACE,
+                "conv_adjoint_noalloc: batch * ceil(n/1024) * k = " + std::to_string(conv_partial_floats(batch, n, k)) +
+                    " exceeds the fixed scratch of " + std::to_string(conv_static_scratch_floats()) +
+                    " floats; use conv_adjoint with a workspace");
+  int rc = check_ptr(r, "r");
+  if (!rc && grad_h) rc = check_ptr(s, "s");
+  if (!rc && grad_s) rc = check_ptr(h, "h");
+  if (!rc && grad_h) rc = check_ptr(grad_h, "grad_h");
+  if (!rc && grad_s) rc = check_ptr(grad_s, "grad_s");
+  if (rc) return rc;
+  const size_t sb = (size_t)batch * n * 4, hb = (size_t)batch * k * 4, rb = (size_t)batch * (n + k - 1) * 4;
+  if (grad_h && (overlap(grad_h, hb, s, sb) || overlap(grad_h, hb, r, rb) || (h && overlap(grad_h, hb, h, hb))))
+    return fail(ADJWT_ERR_ALIAS, "conv_adjoint_noalloc: grad_h overlaps an input");
+  if (grad_s && (overlap(grad_s, sb, r, rb) || overlap(grad_s, sb, h, hb) || (s && overlap(grad_s, sb, s, sb))))
+    return fail(ADJWT_ERR_ALIAS, "conv_adjoint_noalloc: grad_s overlaps an input");
+  return launch_conv_adjoint_noalloc(batch, n, k, s, h, r, grad_h, grad_s, stream);
+}
+
 extern "C" int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                              adjwt_stream_t stream) {
   if (batch < 0 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "conv_residual: need batch >= 0, n >= 1, k >= 1");

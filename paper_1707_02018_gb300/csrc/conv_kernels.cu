@@ -9,6 +9,7 @@
 // partial grad_h over its chunk to workspace; a second pass sums the partials
 // of each row in a fixed order (deterministic, no atomics).
 #include <algorithm>
+#include <mutex>
 
 #include "adjwt_internal.h"
 #include "device_common.cuh"
@@ -157,6 +158,57 @@ int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float
     ADJWT_CUDA_CHECK(cudaGetLastError());
   }
   return ADJWT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of conv_adjoint.  Some callers must not allocate
+// device memory on their call path: processes whose device memory belongs to
+// another allocator (a framework's pool or a fixed budget), loops where the
+// device-wide synchronisation of cudaMalloc / cudaFree is not acceptable, and
+// deployments that forbid allocation after start-up.  For them the grad_h
+// partial sums live in a fixed array in this library's device memory instead
+// of a caller workspace.  The array is loaded with the library's module, so
+// every GPU that loads the library holds it until the process exits.
+namespace {
+
+constexpr int64_t kStaticScratchFloats = int64_t(1) << 20;  // 4 MiB
+__device__ __align__(256) float g_conv_static_scratch[kStaticScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+int static_scratch(float** out) {
+  int dev = 0;
+  ADJWT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(ADJWT_ERR_INVALID_ARG, "conv_adjoint_noalloc: device index above 63");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    ADJWT_CUDA_CHECK(cudaGetSymbolAddress(&p, g_conv_static_scratch));
+    g_static_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return ADJWT_OK;
+}
+
+}  // namespace
+
+int64_t conv_static_scratch_floats() { return kStaticScratchFloats; }
+
+int launch_conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
+                                float* grad_h, float* grad_s, cudaStream_t st) {
+  float* scratch = nullptr;
+  if (grad_h) {
+    int rc = static_scratch(&scratch);
+    if (rc) return rc;
+  }
+  // Every (row, chunk, lag) slot the reduction reads is written by exactly one
+  // CTA of the same call, so nothing has to be cleared between calls.
+  return launch_conv_adjoint(batch, n, k, s, h, r, grad_h, grad_s, scratch, st);
 }
 
 int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
