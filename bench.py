@@ -65,11 +65,11 @@ def fista_bytes(bc):
 
 
 def channel_bytes():
+    """Fused channel gradient: reads s, h, x; writes grad_s, grad_h (r stays on chip)."""
     B, n, k = CH_B, CH_N, CH_K
-    res = 4 * (B * k + B * n + 2 * B * (n + k - 1))
-    adj = 4 * (B * n + B * k + B * (n + k - 1) + B * n + B * k)
-    return {"conv_residual": res, "conv_adjoint": adj, "total": res + adj,
-            "flops_adjoint": 4 * B * n * k, "flops_residual": 2 * B * (n + k - 1) * k}
+    total = 4 * (B * n + B * k + B * (n + k - 1) + B * n + B * k)
+    return {"conv_gradient": total, "total": total,
+            "flops": 2 * B * (n + k - 1) * k + 4 * B * n * k}
 
 
 def step_bytes():
@@ -148,9 +148,8 @@ def build_workload(adj, torch, rank):
     h, s = dev(cp["h"]), dev(cp["s"])
     x = adj.conv_residual(h, s) + dev(cp["noise"])
     ch = {"s": dev(cp["s_est"]), "h": dev(cp["h_est"]), "x": x,
-          "r": torch.empty(CH_B, CH_N + CH_K - 1, device="cuda"),
           "gh": torch.empty(CH_B, CH_K, device="cuda"), "gs": torch.empty(CH_B, CH_N, device="cuda")}
-    ch["ws"] = adj.workspace(adj.lib().adjwt_conv_adjoint_workspace_size(CH_B, CH_N, CH_K))
+    ch["ws"] = adj.workspace(adj.lib().adjwt_conv_gradient_workspace_size(CH_B, CH_N, CH_K))
     for key in ("s", "h", "x"):
         ch[key + "_host"] = ch[key].cpu().pin_memory()
     return probs, ch
@@ -159,8 +158,7 @@ def build_workload(adj, torch, rank):
 def run_step(adj, probs, ch):
     for pr in probs:
         pr["fista"].step()
-    adj.conv_residual(ch["h"], ch["s"], ch["x"], r=ch["r"])
-    adj.conv_adjoint(ch["s"], ch["h"], ch["r"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
+    adj.conv_gradient(ch["s"], ch["h"], ch["x"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
 
 
 def run_e2e_step(adj, torch, probs, ch, out_host):
@@ -170,8 +168,7 @@ def run_e2e_step(adj, torch, probs, ch, out_host):
         pr["fista"].step()
     for key in ("s", "h", "x"):
         ch[key].copy_(ch[key + "_host"], non_blocking=True)
-    adj.conv_residual(ch["h"], ch["s"], ch["x"], r=ch["r"])
-    adj.conv_adjoint(ch["s"], ch["h"], ch["r"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
+    adj.conv_gradient(ch["s"], ch["h"], ch["x"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
     out_host["gh"].copy_(ch["gh"], non_blocking=True)
     for i, pr in enumerate(probs):
         ll = pr["wt"].band_rows[0] * pr["wt"].band_pitch[0]
@@ -270,8 +267,7 @@ def ours(args):
     cb = channel_bytes()
     alg = {"wt_synth.L1": sum(fb[bc]["level1"]["wt_synth"] for bc in BCS) / 3,
            "wt_adjoint_prox.L1": sum(fb[bc]["level1"]["wt_adjoint_prox"] for bc in BCS) / 3,
-           "blur_normal": fb["sym"]["blur_normal"], "conv_adjoint": cb["conv_adjoint"],
-           "conv_residual": cb["conv_residual"]}
+           "blur_normal": fb["sym"]["blur_normal"], "conv_gradient": cb["conv_gradient"]}
     kernels = {}
     for key, (n, tot) in sorted(per.items(), key=lambda kv: -kv[1][1]):
         entry = {"launches_per_step": n / traced, "ms_per_launch": tot / n, "share": tot / sum(v[1] for v in per.values())}
@@ -281,8 +277,8 @@ def ours(args):
     top = max(per.items(), key=lambda kv: kv[1][1])[0]
     top_ms = per[top][1] / per[top][0]
     fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    if top == "conv_adjoint":
-        achieved = cb["flops_adjoint"] / (top_ms * 1e-3) / 1e12
+    if top == "conv_gradient":
+        achieved = cb["flops"] / (top_ms * 1e-3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
@@ -291,7 +287,7 @@ def ours(args):
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
     hbm_roofs = {}
-    for key in ("wt_synth.L1", "wt_adjoint_prox.L1", "blur_normal", "conv_adjoint"):
+    for key in ("wt_synth.L1", "wt_adjoint_prox.L1", "blur_normal", "conv_gradient"):
         if key in per:
             a = alg[key] / (per[key][1] / per[key][0] * 1e-3) / 1e9
             hbm_roofs[key] = {"achieved_gbs": a, "frac_of_hbm": a / pk["hbm_gbs"]}

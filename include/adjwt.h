@@ -140,6 +140,15 @@ int blur_normal(const adjwt_blur_plan* plan, const float* u, const float* b, flo
 size_t adjwt_conv_adjoint_workspace_size(int batch, int64_t n, int k);
 int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
                  float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+/* Both gradients of Eq. 5 at (h, s) in one pass: r = h * s - x (full
+ * convolution, x of length n+k-1, NULL = 0) is formed on chip and fed to
+ * grad_h = S^T r and grad_s = H^T r; r is also written out when r != NULL.
+ * Any of r, grad_h, grad_s may be NULL.  Workspace:
+ * adjwt_conv_gradient_workspace_size (it holds r too when k > 1024). */
+size_t adjwt_conv_gradient_workspace_size(int batch, int64_t n, int k);
+int conv_gradient(int batch, int64_t n, int k, const float* s, const float* h, const float* x, float* r,
+                  float* grad_h, float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+
 /* conv_adjoint without a workspace argument (the paper has no counterpart;
  * this is a deployment variant).  It is for callers that must not allocate
  * device memory on their call path: processes whose device memory is owned by
@@ -149,7 +158,9 @@ int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, co
  * go to a fixed 4 MiB array (2^20 floats) in the library's device memory,
  * which every GPU that loads the library holds until the process exits; the
  * call itself allocates nothing.  Limit: when grad_h is requested,
- * batch * ceil(n/1024) * k <= 2^20, else ADJWT_ERR_WORKSPACE and nothing runs.
+ * batch * ceil(n / c) * k <= 2^20 with the chunk c = 32 * floor((4097 - k) / 32)
+ * for k <= 1024 (c = 4032 at k = 64) and c = 1024 above, else
+ * ADJWT_ERR_WORKSPACE and nothing runs.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU (other

@@ -227,6 +227,22 @@ def conv_adjoint(s, h, r, grad_h=True, grad_s=True, ws=None, stream=None):
     return gh, gs
 
 
+def conv_gradient(s, h, x=None, r=None, grad_h=True, grad_s=True, ws=None, stream=None):
+    """(grad_h, grad_s) of Eq. 5 at (h, s) with r = h * s - x formed in the same pass.
+    Pass a (B, n+k-1) tensor as r to also receive the residual."""
+    B, n = s.shape
+    k = h.shape[1]
+    gh = torch.empty(B, k, dtype=torch.float32, device=s.device) if grad_h is True else grad_h
+    gs = torch.empty(B, n, dtype=torch.float32, device=s.device) if grad_s is True else grad_s
+    gh = None if gh is False else gh
+    gs = None if gs is False else gs
+    nbytes = lib().adjwt_conv_gradient_workspace_size(B, n, k)
+    wsp, nb = _ws(nbytes, ws)
+    _lib.check(lib().conv_gradient(B, n, k, _ptr(s), _ptr(h), _ptr(x), _ptr(r), _ptr(gh), _ptr(gs), _ptr(wsp), nb,
+                                   _stream(stream)))
+    return gh, gs
+
+
 def conv_residual(h, s, x=None, r=None, stream=None):
     B, n = s.shape
     k = h.shape[1]

@@ -47,6 +47,8 @@ PROTOTYPES = {
     "conv_adjoint": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "conv_residual": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP]),
     "conv_adjoint_noalloc": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP, VP]),
+    "adjwt_conv_gradient_workspace_size": (SZ, [C.c_int, I64, C.c_int]),
+    "conv_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "adjwt_fista_workspace_size": (SZ, [C.POINTER(FistaProblem)]),
     "fista_step": (C.c_int, [C.POINTER(FistaProblem), C.POINTER(FistaState), VP, SZ, DP, VP]),
     "adjwt_fista_objective": (C.c_int, [C.POINTER(FistaProblem), VP, VP, SZ, DP, VP]),

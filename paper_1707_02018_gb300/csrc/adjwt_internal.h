@@ -112,6 +112,12 @@ int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b,
 int launch_blur_residual_norm(const adjwt_blur_plan* p, const float* u, const float* b, double* partials,
                               cudaStream_t s, int* nparts);
 int blur_partial_slots(const adjwt_blur_plan* p);
+// Register-blocked tiles for radii <= 12 (which: 0 fused normal, 1 forward /
+// residual norm when out is null, 2 adjoint).
+bool tiled_blur_supported(const adjwt_blur_plan* p);
+int tiled_blur_grid_slots(const adjwt_blur_plan* p);
+int launch_tiled_blur(const adjwt_blur_plan* p, int which, const float* in, const float* b, float* out,
+                      double* partials, cudaStream_t s);
 
 // Deterministic sum of float64 partials: out[0] = scale0 * sum(a[0..na)) + scale1 * sum(b[0..nb)).
 int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,
@@ -122,6 +128,14 @@ int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float
                         float* grad_h, float* grad_s, float* partials, cudaStream_t st);
 int64_t conv_partial_floats(int batch, int64_t n, int k);
 int64_t conv_static_scratch_floats();
+void conv_reduce(unsigned nblocks, int k, int nchunks, const float* partials, float* grad_h, int64_t total,
+                 cudaStream_t st);
+// Register-blocked channel-gradient kernel (k <= 1024): r given (r_in) or
+// computed as h * s - x in the same pass.
+bool conv_fused_supported(int k);
+int64_t conv_fused_nchunks(int64_t n, int k);
+int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
+                      float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st);
 int launch_conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
                                 float* grad_h, float* grad_s, cudaStream_t st);
 int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,

@@ -258,11 +258,13 @@ int launch(const char* name, K kernel, const adjwt_blur_plan* p, const BlurArgs&
 }  // namespace
 
 int blur_partial_slots(const adjwt_blur_plan* p) {
+  if (tiled_blur_supported(p)) return tiled_blur_grid_slots(p);
   dim3 g = grid_of(p);
   return static_cast<int>(g.x * g.y);
 }
 
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s) {
+  if (tiled_blur_supported(p)) return launch_tiled_blur(p, adjoint ? 2 : 1, in, nullptr, out, nullptr, s);
   BlurArgs a;
   fill_args(p, &a);
   a.in = in;
@@ -273,25 +275,27 @@ int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjo
 
 int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b, float* g, double* partials,
                        cudaStream_t s, int* nparts) {
+  if (nparts) *nparts = blur_partial_slots(p);
+  if (tiled_blur_supported(p)) return launch_tiled_blur(p, 0, u, b, g, partials, s);
   BlurArgs a;
   fill_args(p, &a);
   a.in = u;
   a.b = b;
   a.out = g;
   a.partials = partials;
-  if (nparts) *nparts = blur_partial_slots(p);
   return launch("blur_normal", k_blur_normal, p, a, smem_normal(a.rr, a.rc), s);
 }
 
 int launch_blur_residual_norm(const adjwt_blur_plan* p, const float* u, const float* b, double* partials,
                               cudaStream_t s, int* nparts) {
+  if (nparts) *nparts = blur_partial_slots(p);
+  if (tiled_blur_supported(p)) return launch_tiled_blur(p, 1, u, b, nullptr, partials, s);
   BlurArgs a;
   fill_args(p, &a);
   a.in = u;
   a.b = b;
   a.out = nullptr;
   a.partials = partials;
-  if (nparts) *nparts = blur_partial_slots(p);
   return launch("blur_residual", k_blur_fwd, p, a, smem_fwd(a.rr, a.rc), s);
 }
 

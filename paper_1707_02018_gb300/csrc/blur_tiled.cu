@@ -1,0 +1,416 @@
+// Register-blocked tile kernels for R, R^* and the fused R^*(R u - b), for
+// PSF radii up to kTiledMaxRadius (compile-time radius; the shorter axis is
+// zero-padded to the same radius, which leaves the operator unchanged).
+//
+// Same operator definitions as blur_kernels.cu.  A CTA owns a 64 x 64 output
+// tile and runs the separable passes in shared memory.  Every pass is a 1D
+// correlation executed by threads that each produce kRB consecutive outputs
+// along the filter direction from one sliding window held in registers
+// (kRB + 2R shared-memory loads for kRB * (2R + 1) FMAs):
+//   vertical passes:   lanes take consecutive columns (conflict-free rows),
+//   horizontal passes: lanes take consecutive rows (odd row pitches keep the
+//                      32 lanes on 32 banks).
+// The boundary extension is applied when the tile is gathered from global
+// memory; tiles that touch the border of a symmetric image switch to the
+// orientation-aware taps of R^* (see blur_kernels.cu) and refill the off-image
+// samples of R u - b from their mirror.
+#include <algorithm>
+
+#include "adjwt_internal.h"
+#include "device_common.cuh"
+
+namespace adjwt {
+
+constexpr int kTiledMaxRadius = 12;
+
+namespace {
+
+constexpr int kT = 64;        // output tile side
+constexpr int kRB = 8;        // outputs per thread per pass
+constexpr int kNT = 256;      // threads per CTA
+
+__host__ __device__ constexpr int odd_up(int v) { return v | 1; }
+__host__ __device__ constexpr int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
+
+template <int R>
+struct Geo {
+  // fused kernel
+  static constexpr int VR = kT + 2 * R;                    // rows of R u - b
+  static constexpr int VC = kT + 2 * R;
+  static constexpr int UR = ceil_to(VR, kRB) + 2 * R;      // rows read by pass 1
+  static constexpr int UC = kT + 4 * R;
+  static constexpr int UP = odd_up(UC);
+  static constexpr int T1R = VR;
+  static constexpr int T1P = odd_up(ceil_to(VC, kRB) + 2 * R);  // cols read by pass 2
+  static constexpr int VP = odd_up(ceil_to(VC, kRB));
+  static constexpr int VROWS = ceil_to(kT, kRB) + 2 * R;   // rows read by pass 3
+  static constexpr int T2P = odd_up(ceil_to(kT, kRB) + 2 * R);
+  static constexpr int A_FLOATS = (UR * UP > VROWS * VP) ? UR * UP : VROWS * VP;
+  static constexpr int B_FLOATS = (T1R * T1P > kT * T2P) ? T1R * T1P : kT * T2P;
+  // single-operator kernels (forward / adjoint): one halo of R
+  static constexpr int SR = ceil_to(kT, kRB) + 2 * R;
+  static constexpr int SC = kT + 2 * R;
+  static constexpr int SP = odd_up(ceil_to(kT, kRB) + 2 * R);
+  static constexpr int S_FLOATS = SR * SP;
+  static constexpr int S2_FLOATS = kT * odd_up(SC);
+};
+
+struct TiledArgs {
+  const float* in;
+  const float* b;
+  float* out;
+  double* partials;
+  int rows, cols, pitch, bc;  // bc: 0 zero, 1 sym, 3 per
+  float pr[2 * kTiledMaxRadius + 1], pc[2 * kTiledMaxRadius + 1];  // padded to 2R+1
+};
+
+__device__ __forceinline__ bool odd_period(int x, int N) { return (floor_div(x, N) & 1) != 0; }
+
+// out[i][c] = sum_t w[t] in[i + t][c], i in [0, nrows), c in [0, ncols)
+template <int R, bool FLIP>
+__device__ __forceinline__ void vpass(const float* __restrict__ in, int in_p, float* __restrict__ out, int out_p,
+                                      int nrows, int ncols, const float (&w)[2 * R + 1],
+                                      const unsigned char* __restrict__ flip) {
+  constexpr int K = 2 * R + 1;
+  const int nblk = (nrows + kRB - 1) / kRB;
+  for (int item = threadIdx.x; item < nblk * ncols; item += kNT) {
+    const int blk = item / ncols, c = item - blk * ncols;
+    const int i0 = blk * kRB;
+    float acc[kRB];
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) acc[o] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kRB + 2 * R; ++j) {
+      const float v = in[(i0 + j) * in_p + c];
+      bool f = false;
+      if (FLIP) f = flip[i0 + j];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        const int t = j - o;
+        if (t >= 0 && t < K) acc[o] = fmaf(FLIP ? (f ? w[K - 1 - t] : w[t]) : w[t], v, acc[o]);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kRB; ++o)
+      if (i0 + o < nrows) out[(i0 + o) * out_p + c] = acc[o];
+  }
+}
+
+// out[r][i] = sum_t w[t] in[r][i + t] (- bsub[r][i]); r in [0, nrows), i in [0, ncols)
+template <int R, bool FLIP>
+__device__ __forceinline__ void hpass(const float* __restrict__ in, int in_p, float* __restrict__ out, int out_p,
+                                      int nrows, int ncols, const float (&w)[2 * R + 1],
+                                      const unsigned char* __restrict__ flip) {
+  constexpr int K = 2 * R + 1;
+  const int nblk = (ncols + kRB - 1) / kRB;
+  for (int item = threadIdx.x; item < nblk * nrows; item += kNT) {
+    const int blk = item / nrows, r = item - blk * nrows;
+    const int i0 = blk * kRB;
+    float acc[kRB];
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) acc[o] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kRB + 2 * R; ++j) {
+      const float v = in[r * in_p + i0 + j];
+      bool f = false;
+      if (FLIP) f = flip[i0 + j];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        const int t = j - o;
+        if (t >= 0 && t < K) acc[o] = fmaf(FLIP ? (f ? w[K - 1 - t] : w[t]) : w[t], v, acc[o]);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kRB; ++o)
+      if (i0 + o < ncols) out[r * out_p + i0 + o] = acc[o];
+  }
+}
+
+// Final horizontal pass straight to global memory (kRB outputs -> two float4).
+template <int R, bool FLIP>
+__device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in_p, const TiledArgs& a, int y0,
+                                            int x0, const float (&w)[2 * R + 1],
+                                            const unsigned char* __restrict__ flip, const float* __restrict__ bsub,
+                                            double* sq) {
+  constexpr int K = 2 * R + 1;
+  constexpr int nblk = kT / kRB;
+  for (int item = threadIdx.x; item < nblk * kT; item += kNT) {
+    const int blk = item / kT, r = item - blk * kT;
+    const int i0 = blk * kRB;
+    const int y = y0 + r;
+    if (y >= a.rows) continue;
+    float acc[kRB];
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) acc[o] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kRB + 2 * R; ++j) {
+      const float v = in[r * in_p + i0 + j];
+      bool f = false;
+      if (FLIP) f = flip[i0 + j];
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        const int t = j - o;
+        if (t >= 0 && t < K) acc[o] = fmaf(FLIP ? (f ? w[K - 1 - t] : w[t]) : w[t], v, acc[o]);
+      }
+    }
+    const int x = x0 + i0;
+    float* dst = a.out ? a.out + (size_t)y * a.pitch + x : nullptr;
+    const float* bb = bsub ? bsub + (size_t)y * a.pitch + x : nullptr;
+    if (x + kRB <= a.cols) {
+      if (bb) {
+        const float4 b0 = __ldg(reinterpret_cast<const float4*>(bb));
+        const float4 b1 = __ldg(reinterpret_cast<const float4*>(bb) + 1);
+        acc[0] -= b0.x; acc[1] -= b0.y; acc[2] -= b0.z; acc[3] -= b0.w;
+        acc[4] -= b1.x; acc[5] -= b1.y; acc[6] -= b1.z; acc[7] -= b1.w;
+      }
+      if (sq) {
+#pragma unroll
+        for (int o = 0; o < kRB; ++o) *sq += (double)acc[o] * (double)acc[o];
+      }
+      if (dst) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        if (x + o < a.cols) {
+          float v = acc[o];
+          if (bb) v -= __ldg(bb + o);
+          if (sq) *sq += (double)v * (double)v;
+          if (dst) dst[o] = v;
+        }
+      }
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_taps(const TiledArgs& a, float (&pr)[2 * R + 1], float (&pc)[2 * R + 1],
+                                          bool reversed) {
+#pragma unroll
+  for (int t = 0; t < 2 * R + 1; ++t) {
+    pr[t] = reversed ? a.pr[2 * R - t] : a.pr[t];
+    pc[t] = reversed ? a.pc[2 * R - t] : a.pc[t];
+  }
+}
+
+// Gather rows [oy, oy + nr) x cols [ox, ox + nc) of the boundary-extended
+// image into smem (pitch sp); 8 independent loads in flight per thread.
+__device__ __forceinline__ void gather(const float* __restrict__ img, int rows, int cols, int pitch, int mode,
+                                       int oy, int ox, int nr, int nc, float* __restrict__ dst, int sp,
+                                       const int* __restrict__ src_c) {
+  const int total = nr * nc;
+  for (int base = threadIdx.x; base < total; base += 8 * kNT) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * kNT;
+      v[u] = 0.0f;
+      if (i < total) {
+        const int rr = i / nc, cc = i - rr * nc;
+        const int sr = ext_src(oy + rr, rows, mode), sc = src_c[cc];
+        if (sr >= 0 && sc >= 0) v[u] = __ldg(img + (size_t)sr * pitch + sc);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * kNT;
+      if (i < total) {
+        const int rr = i / nc, cc = i - rr * nc;
+        dst[rr * sp + cc] = v[u];
+      }
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
+  using G = Geo<R>;
+  extern __shared__ float sm[];
+  float* A = sm;
+  float* B = A + G::A_FLOATS;
+  int* src_c = reinterpret_cast<int*>(B + G::B_FLOATS);
+  unsigned char* flip_r = reinterpret_cast<unsigned char*>(src_c + G::UC);
+  unsigned char* flip_c = flip_r + G::VROWS;
+  __shared__ double red[kNT / 32];
+  __shared__ int s_border;
+  const int y0 = blockIdx.y * kT, x0 = blockIdx.x * kT;
+  const int tid = threadIdx.x;
+  const int mode = a.bc == 3 ? 2 : a.bc;
+  const bool sym = a.bc == 1, per = a.bc == 3;
+  // does the R u - b window leave the image?  (then SYM flips / ZERO zeros apply)
+  const bool border = (y0 - R < 0) || (x0 - R < 0) || (y0 + kT + R > a.rows) || (x0 + kT + R > a.cols);
+  if (tid == 0) s_border = border;
+  for (int c = tid; c < G::UC; c += kNT) src_c[c] = ext_src(x0 - 2 * R + c, a.cols, mode);
+  for (int u = tid; u < G::VROWS; u += kNT) flip_r[u] = sym && odd_period(y0 - R + u, a.rows);
+  for (int c = tid; c < G::VP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
+  __syncthreads();
+  gather(a.in, a.rows, a.cols, a.pitch, mode, y0 - 2 * R, x0 - 2 * R, G::UR, G::UC, A, G::UP, src_c);
+  __syncthreads();
+  float pr[2 * R + 1], pc[2 * R + 1];
+  load_taps<R>(a, pr, pc, true);  // convolution = correlation with reversed taps
+  vpass<R, false>(A, G::UP, B, G::T1P, G::VR, G::UC, pr, nullptr);
+  __syncthreads();
+  hpass<R, false>(B, G::T1P, A, G::VP, G::VR, G::VC, pc, nullptr);
+  __syncthreads();
+  // subtract b and fix the off-image samples
+  double sq = 0.0;
+  for (int i = tid; i < G::VR * G::VC; i += kNT) {
+    const int v = i / G::VC, w = i - v * G::VC;
+    const int y = y0 - R + v, x = x0 - R + w;
+    const bool real = y >= 0 && y < a.rows && x >= 0 && x < a.cols;
+    float val = A[v * G::VP + w];
+    if (real || per) {
+      if (a.b) val -= __ldg(a.b + (size_t)pos_mod(y, a.rows) * a.pitch + pos_mod(x, a.cols));
+      if (real && v >= R && v < R + kT && w >= R && w < R + kT) sq += (double)val * (double)val;
+    } else {
+      val = 0.0f;
+    }
+    A[v * G::VP + w] = val;
+  }
+  __syncthreads();
+  if (sym && s_border) {
+    for (int i = tid; i < G::VR * G::VC; i += kNT) {
+      const int v = i / G::VC, w = i - v * G::VC;
+      const int y = y0 - R + v, x = x0 - R + w;
+      if (y >= 0 && y < a.rows && x >= 0 && x < a.cols) continue;
+      const int sv = ext_src(y, a.rows, 1) - (y0 - R), sw = ext_src(x, a.cols, 1) - (x0 - R);
+      float val = 0.0f;
+      if (sv >= 0 && sv < G::VR && sw >= 0 && sw < G::VC) val = A[sv * G::VP + sw];
+      A[v * G::VP + w] = val;
+    }
+    __syncthreads();
+  }
+  load_taps<R>(a, pr, pc, false);  // adjoint = correlation with the taps as given
+  if (sym && s_border) {
+    vpass<R, true>(A, G::VP, B, G::T2P, kT, G::VC, pr, flip_r);
+    __syncthreads();
+    hpass_store<R, true>(B, G::T2P, a, y0, x0, pc, flip_c, nullptr, nullptr);
+  } else {
+    vpass<R, false>(A, G::VP, B, G::T2P, kT, G::VC, pr, nullptr);
+    __syncthreads();
+    hpass_store<R, false>(B, G::T2P, a, y0, x0, pc, nullptr, nullptr, nullptr);
+  }
+  if (a.partials) {
+    const double tot = block_sum<kNT>(sq, red);
+    if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
+  }
+}
+
+// Forward R (optionally - b, optionally only the norm) or adjoint R^*.
+template <int R, bool ADJ>
+__global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
+  using G = Geo<R>;
+  extern __shared__ float sm[];
+  float* S = sm;                       // gathered input, SR x SP
+  float* T = S + G::S_FLOATS;          // after the vertical pass, kT x odd(SC)
+  int* src_c = reinterpret_cast<int*>(T + G::S2_FLOATS);
+  unsigned char* flip_r = reinterpret_cast<unsigned char*>(src_c + G::SC);
+  unsigned char* flip_c = flip_r + G::SR;
+  __shared__ double red[kNT / 32];
+  const int y0 = blockIdx.y * kT, x0 = blockIdx.x * kT;
+  const int tid = threadIdx.x;
+  const int mode = a.bc == 3 ? 2 : a.bc;
+  const bool sym = a.bc == 1;
+  const bool border = (y0 - R < 0) || (x0 - R < 0) || (y0 + kT + R > a.rows) || (x0 + kT + R > a.cols);
+  for (int c = tid; c < G::SC; c += kNT) src_c[c] = ext_src(x0 - R + c, a.cols, mode);
+  if (ADJ) {
+    for (int u = tid; u < G::SR; u += kNT) flip_r[u] = sym && odd_period(y0 - R + u, a.rows);
+    for (int c = tid; c < G::SP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
+  }
+  __syncthreads();
+  gather(a.in, a.rows, a.cols, a.pitch, mode, y0 - R, x0 - R, G::SR, G::SC, S, G::SP, src_c);
+  __syncthreads();
+  float pr[2 * R + 1], pc[2 * R + 1];
+  load_taps<R>(a, pr, pc, !ADJ);
+  double sq = 0.0;
+  const int TP = odd_up(G::SC);
+  if (ADJ && sym && border) {
+    vpass<R, true>(S, G::SP, T, TP, kT, G::SC, pr, flip_r);
+    __syncthreads();
+    hpass_store<R, true>(T, TP, a, y0, x0, pc, flip_c, nullptr, nullptr);
+  } else {
+    vpass<R, false>(S, G::SP, T, TP, kT, G::SC, pr, nullptr);
+    __syncthreads();
+    hpass_store<R, false>(T, TP, a, y0, x0, pc, nullptr, ADJ ? nullptr : a.b, a.partials ? &sq : nullptr);
+  }
+  if (!ADJ && a.partials) {
+    const double tot = block_sum<kNT>(sq, red);
+    if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
+  }
+}
+
+template <int R>
+size_t smem_normal_t() {
+  using G = Geo<R>;
+  return (size_t)(G::A_FLOATS + G::B_FLOATS) * 4 + G::UC * 4 + G::VROWS + G::VP + 16;
+}
+template <int R>
+size_t smem_single_t() {
+  using G = Geo<R>;
+  return (size_t)(G::S_FLOATS + G::S2_FLOATS) * 4 + G::SC * 4 + G::SR + G::SP + 16;
+}
+
+template <int R>
+int launch_r(int which, const TiledArgs& a, cudaStream_t s) {
+  dim3 grid((a.cols + kT - 1) / kT, (a.rows + kT - 1) / kT);
+  if (which == 0) {
+    const size_t sm = smem_normal_t<R>();
+    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_blur_normal_t<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ADJWT_TRACED("blur_normal", 0, s, k_blur_normal_t<R><<<grid, kNT, sm, s>>>(a));
+  } else {
+    const size_t sm = smem_single_t<R>();
+    if (which == 1) {
+      ADJWT_CUDA_CHECK(
+          cudaFuncSetAttribute(k_blur_single_t<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      ADJWT_TRACED(a.out ? "blur" : "blur_residual", 0, s, k_blur_single_t<R, false><<<grid, kNT, sm, s>>>(a));
+    } else {
+      ADJWT_CUDA_CHECK(
+          cudaFuncSetAttribute(k_blur_single_t<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      ADJWT_TRACED("blur_adjoint", 0, s, k_blur_single_t<R, true><<<grid, kNT, sm, s>>>(a));
+    }
+  }
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+}  // namespace
+
+int tiled_blur_grid_slots(const adjwt_blur_plan* p) {
+  return ((p->cols + kT - 1) / kT) * ((p->rows + kT - 1) / kT);
+}
+
+bool tiled_blur_supported(const adjwt_blur_plan* p) {
+  return (p->kr / 2) <= kTiledMaxRadius && (p->kc / 2) <= kTiledMaxRadius;
+}
+
+// which: 0 = fused normal, 1 = forward (residual if out == null), 2 = adjoint
+int launch_tiled_blur(const adjwt_blur_plan* p, int which, const float* in, const float* b, float* out,
+                      double* partials, cudaStream_t s) {
+  const int R = std::max(p->kr / 2, p->kc / 2);
+  TiledArgs a{};
+  a.in = in;
+  a.b = b;
+  a.out = out;
+  a.partials = partials;
+  a.rows = p->rows;
+  a.cols = p->cols;
+  a.pitch = p->image_pitch;
+  a.bc = p->bc;
+  const int or_ = R - p->kr / 2, oc = R - p->kc / 2;
+  for (int t = 0; t < p->kr; ++t) a.pr[or_ + t] = static_cast<float>(p->taps_r[t]);
+  for (int t = 0; t < p->kc; ++t) a.pc[oc + t] = static_cast<float>(p->taps_c[t]);
+  switch (R) {
+#define ADJWT_R(r) \
+  case r:          \
+    return launch_r<r>(which, a, s);
+    ADJWT_R(0) ADJWT_R(1) ADJWT_R(2) ADJWT_R(3) ADJWT_R(4) ADJWT_R(5) ADJWT_R(6)
+    ADJWT_R(7) ADJWT_R(8) ADJWT_R(9) ADJWT_R(10) ADJWT_R(11) ADJWT_R(12)
+#undef ADJWT_R
+    default:
+      return fail(ADJWT_ERR_INVALID_ARG, "tiled blur: radius above 12");
+  }
+}
+
+}  // namespace adjwt

@@ -224,6 +224,54 @@ extern "C" int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s,
   return launch_conv_adjoint_noalloc(batch, n, k, s, h, r, grad_h, grad_s, stream);
 }
 
+extern "C" size_t adjwt_conv_gradient_workspace_size(int batch, int64_t n, int k) {
+  if (batch <= 0 || n <= 0 || k <= 0) return 0;
+  size_t bytes = adjwt_conv_adjoint_workspace_size(batch, n, k);
+  if (!conv_fused_supported(k)) bytes += static_cast<size_t>(round_up((int64_t)batch * (n + k - 1) * 4, 256));
+  return bytes;
+}
+
+extern "C" int conv_gradient(int batch, int64_t n, int k, const float* s, const float* h, const float* x, float* r,
+                             float* grad_h, float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream) {
+  if (batch < 0 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "conv_gradient: need batch >= 0, n >= 1, k >= 1");
+  if (batch > 65535) return fail(ADJWT_ERR_SHAPE, "conv_gradient: batch above 65535");
+  if (k > 4096) return fail(ADJWT_ERR_SHAPE, "conv_gradient: k above 4096");
+  if (batch == 0) return ADJWT_OK;
+  int rc = check_ptr(s, "s");
+  if (!rc) rc = check_ptr(h, "h");
+  if (!rc && x) rc = check_ptr(x, "x");
+  if (!rc && r) rc = check_ptr(r, "r");
+  if (!rc && grad_h) rc = check_ptr(grad_h, "grad_h");
+  if (!rc && grad_s) rc = check_ptr(grad_s, "grad_s");
+  if (rc) return rc;
+  const size_t sb = (size_t)batch * n * 4, hb = (size_t)batch * k * 4, rb = (size_t)batch * (n + k - 1) * 4;
+  const void* ins[3] = {s, h, x};
+  const size_t inb[3] = {sb, hb, rb};
+  void* outs[3] = {r, grad_h, grad_s};
+  const size_t outb[3] = {rb, hb, sb};
+  for (int o = 0; o < 3; ++o) {
+    if (!outs[o]) continue;
+    for (int i = 0; i < 3; ++i)
+      if (ins[i] && overlap(outs[o], outb[o], ins[i], inb[i]))
+        return fail(ADJWT_ERR_ALIAS, "conv_gradient: an output overlaps an input");
+    for (int p = o + 1; p < 3; ++p)
+      if (outs[p] && overlap(outs[o], outb[o], outs[p], outb[p]))
+        return fail(ADJWT_ERR_ALIAS, "conv_gradient: outputs overlap");
+  }
+  const size_t need = adjwt_conv_gradient_workspace_size(batch, n, k);
+  rc = check_ws(ws, ws_bytes, need, "conv_gradient");
+  if (rc) return rc;
+  float* partials = static_cast<float*>(ws);
+  if (conv_fused_supported(k))
+    return launch_conv_fused(batch, n, k, s, h, x, nullptr, r, grad_h, grad_s, partials, stream);
+  // long channels: residual into r (or the workspace), then the adjoint
+  float* rbuf = r ? r : reinterpret_cast<float*>(static_cast<char*>(ws) + adjwt_conv_adjoint_workspace_size(batch, n, k));
+  rc = launch_conv_residual(batch, n, k, h, s, x, rbuf, stream);
+  if (rc) return rc;
+  if (!grad_h && !grad_s) return ADJWT_OK;
+  return launch_conv_adjoint(batch, n, k, s, h, rbuf, grad_h, grad_s, partials, stream);
+}
+
 extern "C" int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                              adjwt_stream_t stream) {
   if (batch < 0 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "conv_residual: need batch >= 0, n >= 1, k >= 1");

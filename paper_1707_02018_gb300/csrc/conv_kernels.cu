@@ -133,12 +133,22 @@ int64_t nchunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 }  // namespace
 
-int64_t conv_partial_floats(int batch, int64_t n, int k) { return (int64_t)batch * nchunks_of(n) * k; }
+void conv_reduce(unsigned nblocks, int k, int nchunks, const float* partials, float* grad_h, int64_t total,
+                 cudaStream_t st) {
+  k_conv_reduce<<<nblocks, 256, 0, st>>>(k, nchunks, partials, grad_h, total);
+}
+
+int64_t conv_partial_floats(int batch, int64_t n, int k) {
+  if (conv_fused_supported(k)) return (int64_t)batch * conv_fused_nchunks(n, k) * k;
+  return (int64_t)batch * nchunks_of(n) * k;
+}
 
 int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
                         float* grad_s, float* partials, cudaStream_t st) {
   if (k > kMaxK) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: k above 4096");
   if (batch == 0) return ADJWT_OK;
+  if (conv_fused_supported(k))
+    return launch_conv_fused(batch, n, k, s, h, nullptr, r, nullptr, grad_h, grad_s, partials, st);
   const int64_t nch = nchunks_of(n);
   if (nch > 65535 * 1024LL) return fail(ADJWT_ERR_SHAPE, "conv_adjoint: n too large");
   const size_t smem = (size_t)(kChunk + k - 1 + kChunk + k + kThreads) * sizeof(float);

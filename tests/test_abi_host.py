@@ -137,7 +137,10 @@ def test_call_validation_before_launch(lib):
 
 
 def test_workspace_sizes(lib):
-    assert lib.adjwt_conv_adjoint_workspace_size(256, 65536, 64) >= 256 * 64 * 64 * 4
+    # one partial grad_h per (row, chunk) with chunks of 32*floor((4097-k)/32) = 4032 samples at k = 64
+    assert lib.adjwt_conv_adjoint_workspace_size(256, 65536, 64) >= 256 * 17 * 64 * 4
+    assert lib.adjwt_conv_adjoint_workspace_size(2, 10000, 2000) >= 2 * 10 * 2000 * 4
+    assert lib.adjwt_conv_gradient_workspace_size(2, 10000, 2000) >= 2 * 10 * 2000 * 4 + 2 * 11999 * 4
     assert lib.adjwt_conv_adjoint_workspace_size(0, 10, 3) == 0
     rc, h = _plan(lib, 2048, 2048, 5, 3, 3)
     assert rc == 0

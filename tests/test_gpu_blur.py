@@ -60,11 +60,14 @@ def test_full_size_15x15(adj, bc):
     assert abs(float(half) - hw) <= 1e-5 * hw
 
 
-def test_largest_radius_and_identity(adj):
-    pr = random_taps(65, 3)
-    pc = np.array([1.0])
+@pytest.mark.parametrize("kr,kc", [(65, 1), (27, 5), (25, 25), (1, 1)])
+def test_large_radius_paths_and_identity(adj, kr, kc):
+    """Radii above 12 take the runtime-radius kernels, radii up to 12 the
+    register-blocked tiles; k = 1 is the identity."""
+    pr = random_taps(kr, 3) if kr > 1 else np.array([1.0])
+    pc = random_taps(kc, 4) if kc > 1 else np.array([1.0])
     for bc in BCS:
-        for rows, cols in [(40, 9), (100, 70)]:
+        for rows, cols in [(40, 9), (100, 70), (130, 200)]:
             plan = adj.BlurPlan(rows, cols, pr, pc, bc)
             u = random_vector((rows, cols), 4)
             du = image_dev(plan, u)

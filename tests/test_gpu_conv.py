@@ -48,6 +48,24 @@ def test_conv_parity(adj, B, n, k):
     assert_close(rr.cpu().numpy(), r, what=f"residual {B}x{n}x{k}")
 
 
+@pytest.mark.parametrize("B,n,k", [(3, 5, 3), (2, 1, 1), (4, 1000, 64), (2, 4033, 64), (2, 8065, 64),
+                                   (1, 3, 9), (3, 3000, 300), (2, 5000, 1024), (2, 3000, 1025), (1, 7000, 17)])
+def test_conv_gradient_fused_parity(adj, B, n, k):
+    """r = h * s - x and both gradients in one call (chunk edges at 4032 / 8064 for k = 64;
+    k = 1025 takes the two-kernel path with r in the workspace)."""
+    p = channel_problem(B, n, k, seed=B * 7 + n + k)
+    x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
+    r_want = oconv.conv_full(p["h_est"], p["s_est"]) - x
+    wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r_want)
+    r = torch.full((B, n + k - 1), float("nan"), device="cuda")
+    gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x), r=r)
+    assert_close(r.cpu().numpy(), r_want, what=f"residual {B}x{n}x{k}")
+    assert_close(gh.cpu().numpy(), wh, what=f"grad_h {B}x{n}x{k}")
+    assert_close(gs.cpu().numpy(), ws, what=f"grad_s {B}x{n}x{k}")
+    gh2, gs2 = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x))     # without r out
+    assert torch.equal(gh2, gh) and torch.equal(gs2, gs)
+
+
 def test_one_gradient_only_and_empty(adj):
     s, h = dev(random_vector((2, 50), 1)), dev(random_vector((2, 4), 2))
     r = dev(random_vector((2, 53), 3))
@@ -69,3 +87,6 @@ def test_full_size_256x65536x64(adj):
     wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r)
     assert_close(gh.cpu().numpy(), wh, what="grad_h full")
     assert_close(gs.cpu().numpy(), ws, what="grad_s full")
+    gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x))
+    assert_close(gh.cpu().numpy(), wh, what="fused grad_h full")
+    assert_close(gs.cpu().numpy(), ws, what="fused grad_s full")

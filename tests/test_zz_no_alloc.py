@@ -63,10 +63,11 @@ def _no_alloc(lib, s, h, r):
 def test_no_alloc_matches_workspace_entry_point_twice():
     from paper_1707_02018_gb300 import _lib
     lib = _lib.load()
-    # the first call fills the whole fixed scratch (256 x 64 chunks x 64 lags);
-    # the second is smaller, so a partial sum left over from the first call in a
-    # slot the second call failed to write would show up in its grad_h
-    cases = [(256, 65536, 64, 11), (7, 3000, 33, 12)]
+    # the first call fills the whole fixed scratch (1024 rows x 1 chunk x 1024
+    # lags = 2^20 partial sums); the second is smaller, so a partial sum left over
+    # from the first call in a slot the second call failed to write would show
+    # up in its grad_h
+    cases = [(1024, 3072, 1024, 11), (7, 3000, 33, 12)]
     for B, n, k, seed in cases:
         s, h, r = _inputs(B, n, k, seed)
         want_h, want_s = _with_workspace(lib, s, h, r)
@@ -79,9 +80,9 @@ def test_no_alloc_matches_workspace_entry_point_twice():
 def test_no_alloc_rejects_sizes_beyond_its_scratch():
     from paper_1707_02018_gb300 import _lib
     lib = _lib.load()
-    # 300 rows x 64 chunks x 64 lags = 1,228,800 partial sums > 2^20: rejected
+    # 1025 rows x 1 chunk x 1024 lags = 1,049,600 partial sums > 2^20: rejected
     # before any pointer is looked at or any kernel is launched
-    gh = torch.empty(300, 64, device="cuda")
-    rc = lib.conv_adjoint_noalloc(300, 65536, 64, None, None, None, _ptr(gh), None, None)
+    gh = torch.empty(1025, 1024, device="cuda")
+    rc = lib.conv_adjoint_noalloc(1025, 3072, 1024, None, None, None, _ptr(gh), None, None)
     assert rc == -7
     assert b"exceeds the fixed scratch" in lib.adjwt_last_error()
