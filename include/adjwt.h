@@ -158,8 +158,9 @@ int conv_gradient(int batch, int64_t n, int k, const float* s, const float* h, c
  * go to a fixed 4 MiB array (2^20 floats) in the library's device memory,
  * which every GPU that loads the library holds until the process exits; the
  * call itself allocates nothing.  Limit: when grad_h is requested,
- * batch * ceil(n / c) * k <= 2^20 with the chunk c = 32 * floor((4097 - k) / 32)
- * for k <= 1024 (c = 4032 at k = 64) and c = 1024 above, else
+ * batch * ceil(n / c) * k <= 2^20 with the chunk
+ * c = 16 * floor((4097 - 16 * ceil(k / 16)) / 16) for k <= 1024 (c = 4032 at
+ * k = 64, 3072 at k = 1024) and c = 1024 above, else
  * ADJWT_ERR_WORKSPACE and nothing runs.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream

@@ -195,29 +195,38 @@ __device__ __forceinline__ void load_taps(const TiledArgs& a, float (&pr)[2 * R 
   }
 }
 
-// Gather rows [oy, oy + nr) x cols [ox, ox + nc) of the boundary-extended
-// image into smem (pitch sp); 8 independent loads in flight per thread.
+// Gather rows [oy, oy + NR) x cols [ox, ox + NC) of the boundary-extended
+// image into smem (pitch sp).  Each thread keeps 16 independent loads in
+// flight; a window that lies inside the image skips the extension map.
+template <int NR, int NC>
 __device__ __forceinline__ void gather(const float* __restrict__ img, int rows, int cols, int pitch, int mode,
-                                       int oy, int ox, int nr, int nc, float* __restrict__ dst, int sp,
+                                       int oy, int ox, float* __restrict__ dst, int sp,
                                        const int* __restrict__ src_c) {
-  const int total = nr * nc;
-  for (int base = threadIdx.x; base < total; base += 8 * kNT) {
-    float v[8];
+  constexpr int total = NR * NC;
+  constexpr int U = 16;
+  const bool inside = oy >= 0 && ox >= 0 && oy + NR <= rows && ox + NC <= cols;
+  const float* base = img + (size_t)(inside ? oy : 0) * pitch + (inside ? ox : 0);
+  for (int b0 = threadIdx.x; b0 < total; b0 += U * kNT) {
+    float v[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = base + u * kNT;
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * kNT;
       v[u] = 0.0f;
       if (i < total) {
-        const int rr = i / nc, cc = i - rr * nc;
-        const int sr = ext_src(oy + rr, rows, mode), sc = src_c[cc];
-        if (sr >= 0 && sc >= 0) v[u] = __ldg(img + (size_t)sr * pitch + sc);
+        const int rr = i / NC, cc = i - rr * NC;
+        if (inside) {
+          v[u] = __ldg(base + (size_t)rr * pitch + cc);
+        } else {
+          const int sr = ext_src(oy + rr, rows, mode), sc = src_c[cc];
+          if (sr >= 0 && sc >= 0) v[u] = __ldg(img + (size_t)sr * pitch + sc);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = base + u * kNT;
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * kNT;
       if (i < total) {
-        const int rr = i / nc, cc = i - rr * nc;
+        const int rr = i / NC, cc = i - rr * NC;
         dst[rr * sp + cc] = v[u];
       }
     }
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
   for (int u = tid; u < G::VROWS; u += kNT) flip_r[u] = sym && odd_period(y0 - R + u, a.rows);
   for (int c = tid; c < G::VP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
   __syncthreads();
-  gather(a.in, a.rows, a.cols, a.pitch, mode, y0 - 2 * R, x0 - 2 * R, G::UR, G::UC, A, G::UP, src_c);
+  gather<G::UR, G::UC>(a.in, a.rows, a.cols, a.pitch, mode, y0 - 2 * R, x0 - 2 * R, A, G::UP, src_c);
   __syncthreads();
   float pr[2 * R + 1], pc[2 * R + 1];
   load_taps<R>(a, pr, pc, true);  // convolution = correlation with reversed taps
@@ -256,18 +265,42 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
   __syncthreads();
   // subtract b and fix the off-image samples
   double sq = 0.0;
-  for (int i = tid; i < G::VR * G::VC; i += kNT) {
-    const int v = i / G::VC, w = i - v * G::VC;
-    const int y = y0 - R + v, x = x0 - R + w;
-    const bool real = y >= 0 && y < a.rows && x >= 0 && x < a.cols;
-    float val = A[v * G::VP + w];
-    if (real || per) {
-      if (a.b) val -= __ldg(a.b + (size_t)pos_mod(y, a.rows) * a.pitch + pos_mod(x, a.cols));
-      if (real && v >= R && v < R + kT && w >= R && w < R + kT) sq += (double)val * (double)val;
-    } else {
-      val = 0.0f;
+  {
+    constexpr int total = G::VR * G::VC, U = 16;
+    for (int b0 = tid; b0 < total; b0 += U * kNT) {
+      float bv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {  // all b loads of this round in flight first
+        const int i = b0 + u * kNT;
+        bv[u] = 0.0f;
+        if (i < total && a.b) {
+          const int v = i / G::VC, w = i - v * G::VC;
+          const int y = y0 - R + v, x = x0 - R + w;
+          const bool real = y >= 0 && y < a.rows && x >= 0 && x < a.cols;
+          if (real) {
+            bv[u] = __ldg(a.b + (size_t)y * a.pitch + x);
+          } else if (per) {
+            bv[u] = __ldg(a.b + (size_t)pos_mod(y, a.rows) * a.pitch + pos_mod(x, a.cols));
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = b0 + u * kNT;
+        if (i >= total) break;
+        const int v = i / G::VC, w = i - v * G::VC;
+        const int y = y0 - R + v, x = x0 - R + w;
+        const bool real = y >= 0 && y < a.rows && x >= 0 && x < a.cols;
+        float val = A[v * G::VP + w];
+        if (real || per) {
+          val -= bv[u];
+          if (real && v >= R && v < R + kT && w >= R && w < R + kT) sq += (double)val * (double)val;
+        } else {
+          val = 0.0f;
+        }
+        A[v * G::VP + w] = val;
+      }
     }
-    A[v * G::VP + w] = val;
   }
   __syncthreads();
   if (sym && s_border) {
@@ -320,7 +353,7 @@ __global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
     for (int c = tid; c < G::SP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
   }
   __syncthreads();
-  gather(a.in, a.rows, a.cols, a.pitch, mode, y0 - R, x0 - R, G::SR, G::SC, S, G::SP, src_c);
+  gather<G::SR, G::SC>(a.in, a.rows, a.cols, a.pitch, mode, y0 - R, x0 - R, S, G::SP, src_c);
   __syncthreads();
   float pr[2 * R + 1], pc[2 * R + 1];
   load_taps<R>(a, pr, pc, !ADJ);

@@ -46,11 +46,40 @@ struct AnaArgs {
   float flo[kMaxTaps], fhi[kMaxTaps];
 };
 
+
+// Issue up to 8 independent gathers per thread before storing them, so the
+// staging of a tile keeps several loads in flight.
+// MAXN bounds `total` at compile time, so every load of a tile is issued
+// before the first shared-memory store: one memory round trip per tile.
+template <int MAXN, typename Src, typename Dst>
+__device__ __forceinline__ void staged_copy(int total, Src src, Dst dst) {
+  constexpr int U = (MAXN + kThreads - 1) / kThreads;
+  float v[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    v[u] = i < total ? src(i) : 0.0f;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    if (i < total) dst(i, v[u]);
+  }
+}
+
+// ---------------------------------------------------------------- analysis
+// One CTA: kTile x kTile outputs of each of the four bands.  Column pass:
+// each thread filters kAP consecutive outputs of one column from 2*kAP + L - 2
+// values held in registers; row pass likewise along a row (lanes on rows, odd
+// row pitch).  Both filters of a pass share the loaded window.
+constexpr int kAP = 8;
+
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_analysis(const AnaArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
   constexpr int Lp = L - 1;
   constexpr int E = 2 * kTile + L - 2;  // extended samples feeding one tile
-  constexpr int EP = E + 1;
+  constexpr int EP = E | 1;
+  constexpr int NW = 2 * kAP + L - 2;   // window of one thread
   __shared__ float T[E][EP];
   __shared__ float V[2][kTile][EP];
   __shared__ int s_src[2][E];
@@ -58,85 +87,179 @@ __global__ void __launch_bounds__(kThreads) k_analysis(const AnaArgs a) {
   __shared__ double red[kThreads / 32];
 
   const int k0 = blockIdx.y * kTile, l0 = blockIdx.x * kTile;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int i = tid; i < 2 * E; i += kThreads) {
-    const int axis = i / E, el = i - axis * E;
-    const int e = (axis == 0 ? 2 * k0 : 2 * l0) + 1 - Lp + el;
-    const int N = axis == 0 ? a.Nr : a.Nc;
-    int s;
-    if (a.mode == 3) {
-      s = pos_mod(e, N);
-    } else {
-      s = (e >= 0 && e < N + 2 * Lp) ? ext_src(e - Lp, N, a.mode) : -1;
+  // first extended coordinate of each axis and whether the tile reads only
+  // plain interior samples (no zero, mirror, wrap or weight)
+  const int e0r = 2 * k0 + 1 - Lp, e0c = 2 * l0 + 1 - Lp;
+  const int sh = a.mode == 3 ? 0 : Lp;   // extended coordinate -> image index
+  auto interior = [&](int e0, int N, const float* winv) {
+    const int lo = e0 - sh, hi = e0 - sh + E - 1;
+    const int guard = winv ? Lp : 0;
+    return lo >= guard && hi < N - guard;
+  };
+  const bool fast = interior(e0r, a.Nr, a.winv_r) && interior(e0c, a.Nc, a.winv_c);
+
+  if (fast) {
+    const float* src = a.in + (size_t)(e0r - sh) * a.in_pitch + (e0c - sh);
+    staged_copy<E * E>(
+        E * E,
+        [&](int i) {
+          const int er = i / E;
+          return __ldg(src + (size_t)er * a.in_pitch + (i - er * E));
+        },
+        [&](int i, float v) {
+          const int er = i / E;
+          T[er][i - er * E] = v;
+        });
+  } else {
+    for (int i = tid; i < 2 * E; i += kThreads) {
+      const int axis = i / E, el = i - axis * E;
+      const int e = (axis == 0 ? e0r : e0c) + el;
+      const int N = axis == 0 ? a.Nr : a.Nc;
+      int s;
+      if (a.mode == 3) {
+        s = pos_mod(e, N);
+      } else {
+        s = (e >= 0 && e < N + 2 * Lp) ? ext_src(e - Lp, N, a.mode) : -1;
+      }
+      const float* winv = axis == 0 ? a.winv_r : a.winv_c;
+      s_src[axis][el] = s;
+      s_w[axis][el] = (s >= 0 && winv) ? __ldg(winv + s) : 1.0f;
     }
-    const float* winv = axis == 0 ? a.winv_r : a.winv_c;
-    s_src[axis][el] = s;
-    s_w[axis][el] = (s >= 0 && winv) ? __ldg(winv + s) : 1.0f;
+    __syncthreads();
+    staged_copy<E * E>(
+        E * E,
+        [&](int i) {
+          const int er = i / E, ec = i - er * E;
+          const int sr = s_src[0][er], sc = s_src[1][ec];
+          return (sr >= 0 && sc >= 0) ? s_w[0][er] * s_w[1][ec] * __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+        },
+        [&](int i, float v) {
+          const int er = i / E;
+          T[er][i - er * E] = v;
+        });
   }
   __syncthreads();
 
-  for (int i = tid; i < E * E; i += kThreads) {
-    const int er = i / E, ec = i - er * E;
-    const int sr = s_src[0][er], sc = s_src[1][ec];
-    float v = 0.0f;
-    if (sr >= 0 && sc >= 0) v = s_w[0][er] * s_w[1][ec] * __ldg(a.in + (size_t)sr * a.in_pitch + sc);
-    T[er][ec] = v;
-  }
-  __syncthreads();
-
-  // column pass (filter along rows, keep odd samples)
-  for (int i = tid; i < kTile * E; i += kThreads) {
-    const int kk = i / E, ec = i - kk * E;
-    float lo = 0.0f, hi = 0.0f;
+  // column pass: V[f][kk][ec] = sum_t f[t] T[2 kk + L' - t][ec]
+  for (int item = tid; item < E * (kTile / kAP); item += kThreads) {
+    const int kb = item / E, ec = item - kb * E;
+    float w[NW];
 #pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const float v = T[2 * kk + Lp - t][ec];
-      lo = fmaf(a.flo[t], v, lo);
-      hi = fmaf(a.fhi[t], v, hi);
-    }
-    V[0][kk][ec] = lo;
-    V[1][kk][ec] = hi;
-  }
-  __syncthreads();
-
-  // row pass + store / prox epilogue
-  double l1 = 0.0;
-  for (int i = tid; i < kTile * kTile; i += kThreads) {
-    const int kk = i / kTile, ll = i - kk * kTile;
-    const int k = k0 + kk, l = l0 + ll;
-    if (k >= a.nr || l >= a.out_pitch) continue;
-    const bool inside = l < a.nc;
-    float res[4];
+    for (int j = 0; j < NW; ++j) w[j] = T[2 * kAP * kb + j][ec];
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
+    for (int p = 0; p < kAP; ++p) {
       float lo = 0.0f, hi = 0.0f;
 #pragma unroll
       for (int t = 0; t < L; ++t) {
-        const float v = V[f][kk][2 * ll + Lp - t];
-        lo = fmaf(a.flo[t], v, lo);
-        hi = fmaf(a.fhi[t], v, hi);
+        lo = fmaf(a.flo[t], w[2 * p + Lp - t], lo);
+        hi = fmaf(a.fhi[t], w[2 * p + Lp - t], hi);
       }
-      res[f] = lo;      // band (f, lo): f = 0 -> LL, f = 1 -> LH
-      res[2 + f] = hi;  // band (f, hi): f = 0 -> HL, f = 1 -> HH
+      V[0][kAP * kb + p][ec] = lo;
+      V[1][kAP * kb + p][ec] = hi;
     }
-    const size_t idx = (size_t)k * a.out_pitch + l;
+  }
+  __syncthreads();
+
+  // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
+  double l1 = 0.0;
+  {
+    const int kk = lane, f = warp & 1, lb = warp >> 1;
+    const int k = k0 + kk;
+    float w[NW];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      if (a.px[b]) {
-        float xn = 0.0f, yn = 0.0f;
-        if (inside) {
-          const float v = a.py[b][idx] - a.step * res[b];
-          const float mag = fabsf(v) - a.thresh;
-          xn = mag > 0.0f ? copysignf(mag, v) : 0.0f;
-          const float xo = a.px[b][idx];
-          yn = fmaf(a.beta, xn - xo, xn);
-          l1 += fabs((double)xn);
+    for (int j = 0; j < NW; ++j) w[j] = V[f][kk][2 * kAP * lb + j];
+    float res[2][kAP];
+#pragma unroll
+    for (int p = 0; p < kAP; ++p) {
+      float lo = 0.0f, hi = 0.0f;
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        lo = fmaf(a.flo[t], w[2 * p + Lp - t], lo);
+        hi = fmaf(a.fhi[t], w[2 * p + Lp - t], hi);
+      }
+      res[0][p] = lo;
+      res[1][p] = hi;
+    }
+    const int lbase = l0 + kAP * lb;
+    if (k < a.nr && lbase < a.out_pitch) {
+      const size_t row = (size_t)k * a.out_pitch + lbase;
+      const bool full = lbase + kAP <= a.nc;   // all eight inside the band (16-byte aligned)
+      // band pointers by compile-time index (avoids dynamic indexing of the parameter block)
+      auto pick = [&](float* const (&arr)[4], int b) -> float* {
+        return b == 0 ? arr[0] : (b == 1 ? arr[1] : (b == 2 ? arr[2] : arr[3]));
+      };
+      float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
+      float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
+      float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
+      // prox bands: gather y and x first (all loads in flight), then compute and store
+      float yv[2][kAP], xv[2][kAP];
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        if (!pxs[hb]) continue;
+        const float* __restrict__ ys = pys[hb] + row;
+        const float* __restrict__ xs = pxs[hb] + row;
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < kAP / 4; ++q) {
+            const float4 y4 = reinterpret_cast<const float4*>(ys)[q];
+            const float4 x4 = reinterpret_cast<const float4*>(xs)[q];
+            yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
+            xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < kAP; ++p) {
+            const bool in = lbase + p < a.nc;
+            yv[hb][p] = in ? ys[p] : 0.0f;
+            xv[hb][p] = in ? xs[p] : 0.0f;
+          }
         }
-        a.px[b][idx] = xn;
-        a.py[b][idx] = yn;
-      } else if (a.dst[b]) {
-        a.dst[b][idx] = inside ? res[b] : 0.0f;
+      }
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        if (pxs[hb]) {
+          float* __restrict__ ys = pys[hb] + row;
+          float* __restrict__ xs = pxs[hb] + row;
+          float xn[kAP], yn[kAP];
+#pragma unroll
+          for (int p = 0; p < kAP; ++p) {
+            const float v = yv[hb][p] - a.step * res[hb][p];
+            const float mag = fabsf(v) - a.thresh;
+            float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
+            float y = fmaf(a.beta, x - xv[hb][p], x);
+            if (!full && lbase + p >= a.nc) x = y = 0.0f;
+            xn[p] = x;
+            yn[p] = y;
+            l1 += fabs((double)x);
+          }
+          if (full) {
+#pragma unroll
+            for (int q = 0; q < kAP / 4; ++q) {
+              reinterpret_cast<float4*>(xs)[q] = make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
+              reinterpret_cast<float4*>(ys)[q] = make_float4(yn[4 * q], yn[4 * q + 1], yn[4 * q + 2], yn[4 * q + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int p = 0; p < kAP; ++p) {
+              if (lbase + p < a.out_pitch) {
+                xs[p] = xn[p];
+                ys[p] = yn[p];
+              }
+            }
+          }
+        } else if (dst[hb]) {
+          float* d = dst[hb] + row;
+          if (full) {
+            reinterpret_cast<float4*>(d)[0] = make_float4(res[hb][0], res[hb][1], res[hb][2], res[hb][3]);
+            reinterpret_cast<float4*>(d)[1] = make_float4(res[hb][4], res[hb][5], res[hb][6], res[hb][7]);
+          } else {
+#pragma unroll
+            for (int p = 0; p < kAP; ++p)
+              if (lbase + p < a.out_pitch) d[p] = lbase + p < a.nc ? res[hb][p] : 0.0f;
+          }
+        }
       }
     }
   }
@@ -157,72 +280,208 @@ struct SynArgs {
   float g[2][kMaxTaps];  // synthesis filters lo / hi
 };
 
+// ---------------------------------------------------------------- synthesis
+// One CTA: kTile x kTile output pixels.  Along an axis the outputs x of the
+// tile's virtual range [xa, xb) come in pairs (xa + 2p, xa + 2p + 1); with
+// phi = (xa + off - 1) mod 2 and Kb = floor((xa + off - 1) / 2) the pair p
+// reads the coefficients Kb + p - q (+ e when phi = 1) with filter taps
+// m = (e xor phi) + 2q, q < L/2.  A thread produces kSP pairs of one column
+// (column pass) or one row (row pass) from kSP + L/2 coefficients per band
+// held in registers.
+constexpr int kSP = 4;
+
+template <int L>
+struct SynGeo {
+  static constexpr int Lp = L - 1;
+  static constexpr int XM = kTile + 2 * Lp;                   // virtual outputs per axis (max)
+  static constexpr int NPAIR = (XM + 1) / 2;
+  static constexpr int NBLK = (NPAIR + kSP - 1) / kSP;
+  static constexpr int KM = NBLK * kSP + L / 2;               // coefficients per axis (max)
+  static constexpr int KP = KM | 1;
+  static constexpr int NC = kSP + L / 2;                      // coefficients per thread window
+  static constexpr int YP = XM | 1;
+};
+
+template <int L, int PHI>
+__device__ __forceinline__ void pair_block(const float (&c0)[SynGeo<L>::NC], const float (&c1)[SynGeo<L>::NC],
+                                           const float (&g0)[L], const float (&g1)[L], float (&out)[2 * kSP]) {
+#pragma unroll
+  for (int p = 0; p < kSP; ++p) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < L / 2; ++q) {
+        const int j = p - q + L / 2 - 1 + (PHI ? e : 0);
+        const int m = (PHI ? 1 - e : e) + 2 * q;
+        acc = fmaf(c0[j], g0[m], acc);
+        acc = fmaf(c1[j], g1[m], acc);
+      }
+      out[2 * p + e] = acc;
+    }
+  }
+}
+
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
+  using G = SynGeo<L>;
   constexpr int Lp = L - 1;
-  constexpr int XM = kTile + 2 * Lp;       // virtual rows a tile may need
-  constexpr int KM = (XM + L) / 2 + 2;     // coefficient rows feeding them
-  constexpr int KP = KM + 1;
-  __shared__ float C[4][KM][KP];
-  __shared__ float H[2][XM][KP];           // reused as Y[kTile][XM + 1]
-  __shared__ float G[2][kTile][KP];
-  float(*Y)[XM + 1] = reinterpret_cast<float(*)[XM + 1]>(&H[0][0][0]);
-  static_assert(kTile * (XM + 1) <= 2 * XM * KP, "Y must fit in H");
+  __shared__ float C[4][G::KM][G::KP];
+  __shared__ float H[2][G::XM][G::KP];     // reused as Y[kTile][YP]
+  __shared__ float Gf[2][kTile][G::KP];
+  float(*Y)[G::YP] = reinterpret_cast<float(*)[G::YP]>(&H[0][0][0]);
+  static_assert(kTile * G::YP <= 2 * G::XM * G::KP, "Y must fit in H");
 
   const int tid = threadIdx.x;
   const int t0r = blockIdx.y * kTile, t0c = blockIdx.x * kTile;
   const bool sym = a.mode == 1;
+  float g0[L], g1[L];
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    g0[t] = a.g[0][t];
+    g1[t] = a.g[1][t];
+  }
   // filter index m = x + off - 2k - 1: the extended modes carry the L' shift of
   // the extension on top of the bank's delay L'; the circular mode has none
   const int off = a.mode == 3 ? Lp : 2 * Lp;
-  int xa[2], xb[2], ka[2], nk[2];
+  int xa[2], nx[2], phi[2], ka[2], nk[2], nblk[2];
   {
     const int t0[2] = {t0r, t0c};
     const int N[2] = {a.Nr, a.Nc};
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
       xa[ax] = (sym && t0[ax] < Lp) ? -Lp : t0[ax];
-      xb[ax] = (sym && t0[ax] + kTile > N[ax] - Lp) ? N[ax] + Lp : t0[ax] + kTile;
-      ka[ax] = floor_div(xa[ax] + off - Lp, 2);
-      nk[ax] = floor_div(xb[ax] + off - 2, 2) - ka[ax] + 1;
+      const int xb = (sym && t0[ax] + kTile > N[ax] - Lp) ? N[ax] + Lp : t0[ax] + kTile;
+      nx[ax] = xb - xa[ax];
+      phi[ax] = (xa[ax] + off - 1) & 1;
+      const int Kb = floor_div(xa[ax] + off - 1, 2);
+      nblk[ax] = ((nx[ax] + 1) / 2 + kSP - 1) / kSP;
+      ka[ax] = Kb - (L / 2 - 1);
+      nk[ax] = nblk[ax] * kSP + L / 2 - 1 + phi[ax];
     }
   }
-  const int nx_r = xb[0] - xa[0], nx_c = xb[1] - xa[1];
+
+  // Interior tiles (no mirror copy, weight 1, coefficients inside the bands,
+  // no wrap) skip the fold buffers: the column pass writes the folded rows
+  // directly and the row pass stores straight to global memory.
+  bool fast = true;
+  {
+    const int t0[2] = {t0r, t0c};
+    const int N[2] = {a.Nr, a.Nc};
+    const int n[2] = {a.nr, a.nc};
+    const bool weighted = a.winv_r != nullptr || a.mode == 2;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+      const int guard = (weighted || sym) ? Lp : 0;
+      fast = fast && xa[ax] == t0[ax] && nx[ax] == kTile && t0[ax] >= guard && t0[ax] + kTile <= N[ax] - guard &&
+             ka[ax] >= 0 && ka[ax] + nk[ax] <= n[ax];
+    }
+  }
+  if (fast) {
+    // coefficients: warp w stages band w%4, rows of parity w/4; every load of
+    // the thread is issued before its first shared-memory store
+    constexpr int FK = 4 * kSP + L / 2;  // nk of an interior tile is at most this
+    constexpr int RPW = (FK + 1) / 2;    // rows per warp
+    const int lane = tid & 31, warp = tid >> 5;
+    {
+      const int b = warp & 3, half = warp >> 2;
+      const float* src = a.band[b] + (size_t)(ka[0] + half) * a.band_pitch + ka[1] + lane;
+      float v[RPW];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int kk = half + 2 * r;
+        v[r] = (kk < nk[0] && lane < nk[1]) ? __ldg(src + (size_t)(2 * r) * a.band_pitch) : 0.0f;
+      }
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int kk = half + 2 * r;
+        if (kk < nk[0] && lane < nk[1]) C[b][kk][lane] = v[r];
+      }
+    }
+    __syncthreads();
+    // column pass into the folded rows (identity fold, weight 1): warp = (hb, block), lane = column
+    if (lane < nk[1]) {
+      const int hb = warp & 1, blk = warp >> 1, ll = lane;
+      float c0[G::NC], c1[G::NC], out[2 * kSP];
+#pragma unroll
+      for (int j = 0; j < G::NC; ++j) {
+        const int kk = blk * kSP + j;
+        c0[j] = kk < nk[0] ? C[2 * hb][kk][ll] : 0.0f;
+        c1[j] = kk < nk[0] ? C[2 * hb + 1][kk][ll] : 0.0f;
+      }
+      if (phi[0])
+        pair_block<L, 1>(c0, c1, g0, g1, out);
+      else
+        pair_block<L, 0>(c0, c1, g0, g1, out);
+#pragma unroll
+      for (int o = 0; o < 2 * kSP; ++o) Gf[hb][2 * kSP * blk + o][ll] = out[o];
+    }
+    __syncthreads();
+    // row pass straight to global memory: eight consecutive pixels per thread
+    for (int item = tid; item < kTile * nblk[1]; item += kThreads) {
+      const int tt = item & (kTile - 1), blk = item / kTile;
+      float c0[G::NC], c1[G::NC], out[2 * kSP];
+#pragma unroll
+      for (int j = 0; j < G::NC; ++j) {
+        const int kk = blk * kSP + j;
+        c0[j] = kk < nk[1] ? Gf[0][tt][kk] : 0.0f;
+        c1[j] = kk < nk[1] ? Gf[1][tt][kk] : 0.0f;
+      }
+      if (phi[1])
+        pair_block<L, 1>(c0, c1, g0, g1, out);
+      else
+        pair_block<L, 0>(c0, c1, g0, g1, out);
+      float4* dst = reinterpret_cast<float4*>(a.out + (size_t)(t0r + tt) * a.out_pitch + t0c + 2 * kSP * blk);
+      dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+      dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+    return;
+  }
 
   // coefficient tiles of the four bands (periodic wrap for PER, zeros outside otherwise)
-  for (int i = tid; i < 4 * nk[0] * nk[1]; i += kThreads) {
-    const int b = i / (nk[0] * nk[1]);
-    const int rem = i - b * nk[0] * nk[1];
-    const int kk = rem / nk[1], ll = rem - kk * nk[1];
-    int k = ka[0] + kk, l = ka[1] + ll;
-    float v = 0.0f;
-    if (a.mode == 3) {
-      k = pos_mod(k, a.nr);
-      l = pos_mod(l, a.nc);
-      v = __ldg(a.band[b] + (size_t)k * a.band_pitch + l);
-    } else if (k >= 0 && k < a.nr && l >= 0 && l < a.nc) {
-      v = __ldg(a.band[b] + (size_t)k * a.band_pitch + l);
-    }
-    C[b][kk][ll] = v;
-  }
+  const int nkk = nk[0] * nk[1];
+  staged_copy<4 * G::KM * G::KM>(
+      4 * nkk,
+      [&](int i) {
+        const int b = i / nkk, rem = i - b * nkk;
+        const int kk = rem / nk[1], ll = rem - kk * nk[1];
+        int k = ka[0] + kk, l = ka[1] + ll;
+        if (a.mode == 3) {
+          k = pos_mod(k, a.nr);
+          l = pos_mod(l, a.nc);
+        } else if (k < 0 || k >= a.nr || l < 0 || l >= a.nc) {
+          return 0.0f;
+        }
+        return __ldg(a.band[b] + (size_t)k * a.band_pitch + l);
+      },
+      [&](int i, float v) {
+        const int b = i / nkk, rem = i - b * nkk;
+        const int kk = rem / nk[1];
+        C[b][kk][rem - kk * nk[1]] = v;
+      });
   __syncthreads();
 
-  // column pass: H[hb][x][l] = sum_va sum_q C[va + 2 hb][k][l] g_va[m]
-  for (int i = tid; i < 2 * nx_r * nk[1]; i += kThreads) {
-    const int hb = i / (nx_r * nk[1]);
-    const int rem = i - hb * nx_r * nk[1];
-    const int xx = rem / nk[1], ll = rem - xx * nk[1];
-    const int x = xa[0] + xx;
-    const int m0 = (x + off - 1) & 1;
-    float acc = 0.0f;
+  // column pass: H[hb][x][l] over the virtual rows, both vertical bands summed
+  for (int item = tid; item < 2 * nk[1] * nblk[0]; item += kThreads) {
+    const int blk = item / (2 * nk[1]);
+    const int rem = item - blk * 2 * nk[1];
+    const int hb = rem / nk[1], ll = rem - hb * nk[1];
+    float c0[G::NC], c1[G::NC], out[2 * kSP];
 #pragma unroll
-    for (int q = 0; q < L / 2; ++q) {
-      const int m = m0 + 2 * q;
-      const int kk = ((x + off - 1 - m) >> 1) - ka[0];
-      acc = fmaf(C[2 * hb][kk][ll], a.g[0][m], acc);
-      acc = fmaf(C[2 * hb + 1][kk][ll], a.g[1][m], acc);
+    for (int j = 0; j < G::NC; ++j) {
+      const int kk = blk * kSP + j;
+      c0[j] = kk < nk[0] ? C[2 * hb][kk][ll] : 0.0f;
+      c1[j] = kk < nk[0] ? C[2 * hb + 1][kk][ll] : 0.0f;
     }
-    H[hb][xx][ll] = acc;
+    if (phi[0])
+      pair_block<L, 1>(c0, c1, g0, g1, out);
+    else
+      pair_block<L, 0>(c0, c1, g0, g1, out);
+#pragma unroll
+    for (int o = 0; o < 2 * kSP; ++o) {
+      const int xx = 2 * kSP * blk + o;
+      if (xx < nx[0]) H[hb][xx][ll] = out[o];
+    }
   }
   __syncthreads();
 
@@ -241,43 +500,67 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
       }
       if (a.winv_r) v *= __ldg(a.winv_r + t);
     }
-    G[hb][tt][ll] = v;
+    Gf[hb][tt][ll] = v;
   }
   __syncthreads();
 
-  // row pass: Y[t][x] = sum_hb sum_q G[hb][t][l] g_hb[m]
-  for (int i = tid; i < kTile * nx_c; i += kThreads) {
-    const int tt = i / nx_c, xx = i - tt * nx_c;
-    const int x = xa[1] + xx;
-    const int m0 = (x + off - 1) & 1;
-    float acc = 0.0f;
+  // row pass: Y[t][x] over the virtual columns; lanes on rows
+  for (int item = tid; item < kTile * nblk[1]; item += kThreads) {
+    const int tt = item & (kTile - 1), blk = item / kTile;
+    float c0[G::NC], c1[G::NC], out[2 * kSP];
 #pragma unroll
-    for (int q = 0; q < L / 2; ++q) {
-      const int m = m0 + 2 * q;
-      const int ll = ((x + off - 1 - m) >> 1) - ka[1];
-      acc = fmaf(G[0][tt][ll], a.g[0][m], acc);
-      acc = fmaf(G[1][tt][ll], a.g[1][m], acc);
+    for (int j = 0; j < G::NC; ++j) {
+      const int kk = blk * kSP + j;
+      c0[j] = kk < nk[1] ? Gf[0][tt][kk] : 0.0f;
+      c1[j] = kk < nk[1] ? Gf[1][tt][kk] : 0.0f;
     }
-    Y[tt][xx] = acc;
+    if (phi[1])
+      pair_block<L, 1>(c0, c1, g0, g1, out);
+    else
+      pair_block<L, 0>(c0, c1, g0, g1, out);
+#pragma unroll
+    for (int o = 0; o < 2 * kSP; ++o) {
+      const int xx = 2 * kSP * blk + o;
+      if (xx < nx[1]) Y[tt][xx] = out[o];
+    }
   }
   __syncthreads();
 
-  // fold columns and store
+  // fold columns and store (four consecutive pixels per thread)
   const bool ppd = a.mode == 2;
-  for (int i = tid; i < kTile * kTile; i += kThreads) {
-    const int tt = i / kTile, cc = i - tt * kTile;
-    const int tr = t0r + tt, tc = t0c + cc;
-    if (tr >= a.Nr || tc >= a.Nc) continue;
-    float v = Y[tt][tc - xa[1]];
-    if (sym) {
-      if (tc < Lp) v += Y[tt][-1 - tc - xa[1]];
-      if (tc >= a.Nc - Lp) v += Y[tt][2 * a.Nc - 1 - tc - xa[1]];
+  for (int i = tid; i < kTile * (kTile / 4); i += kThreads) {
+    const int tt = i / (kTile / 4), c4 = (i - tt * (kTile / 4)) * 4;
+    const int tr = t0r + tt;
+    if (tr >= a.Nr) continue;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tc = t0c + c4 + u;
+      float s = 0.0f;
+      if (tc < a.Nc) {
+        s = Y[tt][tc - xa[1]];
+        if (sym) {
+          if (tc < Lp) s += Y[tt][-1 - tc - xa[1]];
+          if (tc >= a.Nc - Lp) s += Y[tt][2 * a.Nc - 1 - tc - xa[1]];
+        }
+        if (a.winv_c) s *= __ldg(a.winv_c + tc);
+      }
+      v[u] = s;
     }
-    if (ppd) {  // pixels with periodic far copies belong to the border kernel
-      if (tr < Lp || tr >= a.Nr - Lp || tc < Lp || tc >= a.Nc - Lp) continue;
+    const bool ppd_row = ppd && (tr < Lp || tr >= a.Nr - Lp);
+    float* dst = a.out + (size_t)tr * a.out_pitch + t0c + c4;
+    if (!ppd && t0c + c4 + 4 <= a.Nc) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int tc = t0c + c4 + u;
+        if (tc >= a.Nc) break;
+        // pixels with periodic far copies belong to the border kernel
+        if (ppd && (ppd_row || tc < Lp || tc >= a.Nc - Lp)) continue;
+        dst[u] = v[u];
+      }
     }
-    if (a.winv_c) v *= __ldg(a.winv_c + tc);
-    a.out[(size_t)tr * a.out_pitch + tc] = v;
   }
 }
 
