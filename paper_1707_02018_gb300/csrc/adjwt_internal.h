@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/adjwt.h"
@@ -30,6 +31,44 @@ int cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Programmatic dependent launch.  Every kernel of this library is launched
+// with programmatic stream serialisation and starts with pdl_entry(): it lets
+// the next kernel in the stream begin launching once all of its own CTAs are
+// resident, then waits until the preceding kernel has completed and its
+// writes are visible.  Chains of small dependent kernels (the deep wavelet
+// levels) thereby hide their launch latency.  Nothing is read or written
+// before the wait.
+#if defined(__CUDACC__)
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
+
+// Opt a kernel into `bytes` of dynamic shared memory and the largest shared
+// carveout, so that several such CTAs can be resident on one SM.
+template <typename Kernel>
+inline cudaError_t set_smem(Kernel kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
 
 // ---------------------------------------------------------------- tracing
 int trace_begin(const char* name, int tag, cudaStream_t s);

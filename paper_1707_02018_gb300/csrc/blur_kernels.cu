@@ -40,6 +40,7 @@ __device__ __forceinline__ bool odd_period(int x, int N) { return (floor_div(x, 
 
 // Forward R (optionally minus b, optionally only the norm).
 __global__ void __launch_bounds__(kThreads) k_blur_fwd(const BlurArgs a) {
+  pdl_entry();
   extern __shared__ float sm[];
   const int rr = a.rr, rc = a.rc;
   const int UR = kTile + 2 * rr, UC = kTile + 2 * rc;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_fwd(const BlurArgs a) {
     T1[i] = acc;
   }
   __syncthreads();
-  double sq = 0.0;
+  float sq = 0.0f;  // per-thread float32 partial, float64 across the block
   for (int i = tid; i < kTile * kTile; i += kThreads) {
     const int ii = i / kTile, jj = i - ii * kTile;
     const int y = y0 + ii, x = x0 + jj;
@@ -74,16 +75,17 @@ __global__ void __launch_bounds__(kThreads) k_blur_fwd(const BlurArgs a) {
     const size_t o = (size_t)y * a.pitch + x;
     if (a.b) acc -= __ldg(a.b + o);
     if (a.out) a.out[o] = acc;
-    sq += (double)acc * (double)acc;
+    if (a.partials) sq = fmaf(acc, acc, sq);
   }
   if (a.partials) {
-    const double tot = block_sum<kThreads>(sq, red);
+    const double tot = block_sum<kThreads>((double)sq, red);
     if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
   }
 }
 
 // Adjoint R^* as a gather with per-sample tap orientation.
 __global__ void __launch_bounds__(kThreads) k_blur_adj(const BlurArgs a) {
+  pdl_entry();
   extern __shared__ float sm[];
   const int rr = a.rr, rc = a.rc;
   const int UR = kTile + 2 * rr, UC = kTile + 2 * rc;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_adj(const BlurArgs a) {
 
 // Fused g = R^*(R u - b) (+ per-CTA 1/2 ||R u - b||^2 over the CTA's own pixels).
 __global__ void __launch_bounds__(kThreads) k_blur_normal(const BlurArgs a) {
+  pdl_entry();
   extern __shared__ float sm[];
   const int rr = a.rr, rc = a.rc;
   const int UR = kTile + 4 * rr, UC = kTile + 4 * rc;  // u with a 2r halo
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_normal(const BlurArgs a) {
   }
   __syncthreads();
   // V = R along columns - b, on the virtual window with an r halo
-  double sq = 0.0;
+  float sq = 0.0f;  // per-thread float32 partial, float64 across the block
   for (int i = tid; i < VR * VC; i += kThreads) {
     const int v = i / VC, w = i - v * VC;
     const int y = y0 - rr + v, x = x0 - rc + w;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_normal(const BlurArgs a) {
       for (int t = 0; t <= 2 * rc; ++t) acc = fmaf(a.pc[t], B[v * UC + w + 2 * rc - t], acc);
       if (a.b) acc -= __ldg(a.b + (size_t)pos_mod(y, a.rows) * a.pitch + pos_mod(x, a.cols));
       val = acc;
-      if (real && v >= rr && v < rr + kTile && w >= rc && w < rc + kTile) sq += (double)val * (double)val;
+      if (a.partials && real && v >= rr && v < rr + kTile && w >= rc && w < rc + kTile) sq = fmaf(val, val, sq);
     }
     A[i] = val;
   }
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_normal(const BlurArgs a) {
     a.out[(size_t)y * a.pitch + x] = acc;
   }
   if (a.partials) {
-    const double tot = block_sum<kThreads>(sq, red);
+    const double tot = block_sum<kThreads>((double)sq, red);
     if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
   }
 }
@@ -250,7 +253,7 @@ template <typename K>
 int launch(const char* name, K kernel, const adjwt_blur_plan* p, const BlurArgs& a, size_t smem, cudaStream_t s) {
   if (smem > 48 * 1024) ADJWT_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                              static_cast<int>(smem)));
-  ADJWT_TRACED(name, 0, s, kernel<<<grid_of(p), kThreads, smem, s>>>(a));
+  ADJWT_TRACED(name, 0, s, pdl_launch(kernel, grid_of(p), kThreads, smem, s, a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }

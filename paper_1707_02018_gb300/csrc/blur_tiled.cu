@@ -131,7 +131,7 @@ template <int R, bool FLIP>
 __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in_p, const TiledArgs& a, int y0,
                                             int x0, const float (&w)[2 * R + 1],
                                             const unsigned char* __restrict__ flip, const float* __restrict__ bsub,
-                                            double* sq) {
+                                            float* sq) {
   constexpr int K = 2 * R + 1;
   constexpr int nblk = kT / kRB;
   for (int item = threadIdx.x; item < nblk * kT; item += kNT) {
@@ -165,7 +165,7 @@ __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in
       }
       if (sq) {
 #pragma unroll
-        for (int o = 0; o < kRB; ++o) *sq += (double)acc[o] * (double)acc[o];
+        for (int o = 0; o < kRB; ++o) *sq = fmaf(acc[o], acc[o], *sq);
       }
       if (dst) {
         reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -177,7 +177,7 @@ __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in
         if (x + o < a.cols) {
           float v = acc[o];
           if (bb) v -= __ldg(bb + o);
-          if (sq) *sq += (double)v * (double)v;
+          if (sq) *sq = fmaf(v, v, *sq);
           if (dst) dst[o] = v;
         }
       }
@@ -235,6 +235,7 @@ __device__ __forceinline__ void gather(const float* __restrict__ img, int rows, 
 
 template <int R>
 __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
+  pdl_entry();
   using G = Geo<R>;
   extern __shared__ float sm[];
   float* A = sm;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
   hpass<R, false>(B, G::T1P, A, G::VP, G::VR, G::VC, pc, nullptr);
   __syncthreads();
   // subtract b and fix the off-image samples
-  double sq = 0.0;
+  float sq = 0.0f;  // per-thread float32 partial, float64 across the block
   {
     constexpr int total = G::VR * G::VC, U = 16;
     for (int b0 = tid; b0 < total; b0 += U * kNT) {
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
         float val = A[v * G::VP + w];
         if (real || per) {
           val -= bv[u];
-          if (real && v >= R && v < R + kT && w >= R && w < R + kT) sq += (double)val * (double)val;
+          if (a.partials && real && v >= R && v < R + kT && w >= R && w < R + kT) sq = fmaf(val, val, sq);
         } else {
           val = 0.0f;
         }
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
     hpass_store<R, false>(B, G::T2P, a, y0, x0, pc, nullptr, nullptr, nullptr);
   }
   if (a.partials) {
-    const double tot = block_sum<kNT>(sq, red);
+    const double tot = block_sum<kNT>((double)sq, red);
     if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
   }
 }
@@ -334,6 +335,7 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
 // Forward R (optionally - b, optionally only the norm) or adjoint R^*.
 template <int R, bool ADJ>
 __global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
+  pdl_entry();
   using G = Geo<R>;
   extern __shared__ float sm[];
   float* S = sm;                       // gathered input, SR x SP
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
   __syncthreads();
   float pr[2 * R + 1], pc[2 * R + 1];
   load_taps<R>(a, pr, pc, !ADJ);
-  double sq = 0.0;
+  float sq = 0.0f;
   const int TP = odd_up(G::SC);
   if (ADJ && sym && border) {
     vpass<R, true>(S, G::SP, T, TP, kT, G::SC, pr, flip_r);
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
     hpass_store<R, false>(T, TP, a, y0, x0, pc, nullptr, ADJ ? nullptr : a.b, a.partials ? &sq : nullptr);
   }
   if (!ADJ && a.partials) {
-    const double tot = block_sum<kNT>(sq, red);
+    const double tot = block_sum<kNT>((double)sq, red);
     if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
   }
 }
@@ -390,18 +392,18 @@ int launch_r(int which, const TiledArgs& a, cudaStream_t s) {
   dim3 grid((a.cols + kT - 1) / kT, (a.rows + kT - 1) / kT);
   if (which == 0) {
     const size_t sm = smem_normal_t<R>();
-    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_blur_normal_t<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ADJWT_TRACED("blur_normal", 0, s, k_blur_normal_t<R><<<grid, kNT, sm, s>>>(a));
+    ADJWT_CUDA_CHECK(set_smem(k_blur_normal_t<R>, sm));
+    ADJWT_TRACED("blur_normal", 0, s, pdl_launch(k_blur_normal_t<R>, grid, kNT, sm, s, a));
   } else {
     const size_t sm = smem_single_t<R>();
     if (which == 1) {
       ADJWT_CUDA_CHECK(
           cudaFuncSetAttribute(k_blur_single_t<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      ADJWT_TRACED(a.out ? "blur" : "blur_residual", 0, s, k_blur_single_t<R, false><<<grid, kNT, sm, s>>>(a));
+      ADJWT_TRACED(a.out ? "blur" : "blur_residual", 0, s, pdl_launch(k_blur_single_t<R, false>, grid, kNT, sm, s, a));
     } else {
       ADJWT_CUDA_CHECK(
           cudaFuncSetAttribute(k_blur_single_t<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      ADJWT_TRACED("blur_adjoint", 0, s, k_blur_single_t<R, true><<<grid, kNT, sm, s>>>(a));
+      ADJWT_TRACED("blur_adjoint", 0, s, pdl_launch(k_blur_single_t<R, true>, grid, kNT, sm, s, a));
     }
   }
   ADJWT_CUDA_CHECK(cudaGetLastError());

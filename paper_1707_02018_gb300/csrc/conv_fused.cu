@@ -64,11 +64,12 @@ __device__ __forceinline__ void load_taps16(const float* h_sm, int i0, float (&h
 }
 
 template <bool FUSED>
-__global__ void __launch_bounds__(kNT) k_conv_grad(int64_t n, int K, const float* __restrict__ s,
+__global__ void __launch_bounds__(kNT, 4) k_conv_grad(int64_t n, int K, const float* __restrict__ s,
                                                     const float* __restrict__ h, const float* __restrict__ x,
                                                     const float* __restrict__ r_in, float* __restrict__ r_out,
                                                     float* __restrict__ grad_s, float* __restrict__ part_h,
                                                     int nchunks) {
+  pdl_entry();
   extern __shared__ __align__(16) float sm[];
   const FusedGeo g(K);
   const int kp = g.kp;
@@ -82,24 +83,55 @@ __global__ void __launch_bounds__(kNT) k_conv_grad(int64_t n, int K, const float
   const int tid = threadIdx.x;
   const float* srow = s + (size_t)b * n;
 
-  // ---- stage h (zero-padded), s, and r (adjoint only) -----------------------
+  const int base = tid * kW;  // this thread's 16-aligned window start
+  // x for this thread's 16 residuals, requested before the staging below so
+  // that its latency overlaps the staging
+  float xv[kW];
+  if (FUSED) {
+    const float* xrow = x ? x + (size_t)b * nr : nullptr;
+#pragma unroll
+    for (int o = 0; o < kW; ++o) {
+      const int64_t q = m0 + base + o;
+      xv[o] = (xrow && q < nr) ? __ldg(xrow + q) : 0.0f;
+    }
+  }
+
+  // ---- stage h (zero-padded), s, and r (adjoint only); 16 loads in flight per thread
   for (int i = tid; i < kp; i += kNT) h_sm[i] = (h && i < K) ? __ldg(h + (size_t)b * K + i) : 0.0f;
-  for (int u = tid; u < g.s_len; u += kNT) {
-    const int64_t q = m0 - (kp - 1) + u;
-    s_loc[padx(u)] = (q >= 0 && q < n) ? __ldg(srow + q) : 0.0f;
+  for (int u0 = tid; u0 < g.s_len; u0 += kW * kNT) {
+    float v[kW];
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+      const int u = u0 + j * kNT;
+      const int64_t q = m0 - (kp - 1) + u;
+      v[j] = (u < g.s_len && q >= 0 && q < n) ? __ldg(srow + q) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+      const int u = u0 + j * kNT;
+      if (u < g.s_len) s_loc[padx(u)] = v[j];
+    }
   }
   if (!FUSED) {
     const float* rrow = r_in + (size_t)b * nr;
-    for (int v = tid; v < g.r_len; v += kNT) {
-      const int64_t q = m0 + v;
-      r_loc[padx(v)] = (v < g.ch + kp - 1 && q < nr) ? __ldg(rrow + q) : 0.0f;
+    for (int v0 = tid; v0 < g.r_len; v0 += kW * kNT) {
+      float v[kW];
+#pragma unroll
+      for (int j = 0; j < kW; ++j) {
+        const int vv = v0 + j * kNT;
+        const int64_t q = m0 + vv;
+        v[j] = (vv < g.r_len && vv < g.ch + kp - 1 && q < nr) ? __ldg(rrow + q) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < kW; ++j) {
+        const int vv = v0 + j * kNT;
+        if (vv < g.r_len) r_loc[padx(vv)] = v[j];
+      }
     }
   } else {
     for (int v = kSpan + tid; v < g.r_len; v += kNT) r_loc[padx(v)] = 0.0f;
   }
   __syncthreads();
-
-  const int base = tid * kW;  // this thread's 16-aligned window start
 
   // ---- r = h * s - x on [m0, m0 + 4096) ------------------------------------
   if (FUSED) {
@@ -130,7 +162,6 @@ __global__ void __launch_bounds__(kNT) k_conv_grad(int64_t n, int K, const float
         for (int o = 0; o < kW; ++o) acc[o] = fmaf(hv[ii], buf[(o - ii) & (kW - 1)], acc[o]);
       }
     }
-    const float* xrow = x ? x + (size_t)b * nr : nullptr;
     float* rrow = r_out ? r_out + (size_t)b * nr : nullptr;
     const int own = g.ch + (blockIdx.x == nchunks - 1 ? K - 1 : 0);
 #pragma unroll
@@ -138,8 +169,7 @@ __global__ void __launch_bounds__(kNT) k_conv_grad(int64_t n, int K, const float
       const int64_t q = m0 + base + o;
       float v = 0.0f;
       if (q < nr) {
-        v = acc[o];
-        if (xrow) v -= __ldg(xrow + q);
+        v = acc[o] - xv[o];
         if (rrow && base + o < own) rrow[q] = v;
       }
       r_loc[padx(base + o)] = v;
@@ -245,14 +275,14 @@ int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* 
   dim3 grid(static_cast<unsigned>(nch), static_cast<unsigned>(batch));
   float* part = grad_h ? partials : nullptr;
   if (r_in) {
-    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_conv_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ADJWT_CUDA_CHECK(set_smem(k_conv_grad<false>, smem));
     ADJWT_TRACED("conv_adjoint", 0, st,
-                 k_conv_grad<false><<<grid, kNT, smem, st>>>(n, k, s, h, nullptr, r_in, nullptr, grad_s, part,
+                 pdl_launch(k_conv_grad<false>, grid, kNT, smem, st, n, k, s, h, nullptr, r_in, nullptr, grad_s, part,
                                                              static_cast<int>(nch)));
   } else {
-    ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_conv_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ADJWT_CUDA_CHECK(set_smem(k_conv_grad<true>, smem));
     ADJWT_TRACED("conv_gradient", 0, st,
-                 k_conv_grad<true><<<grid, kNT, smem, st>>>(n, k, s, h, x, nullptr, r_out, grad_s, part,
+                 pdl_launch(k_conv_grad<true>, grid, kNT, smem, st, n, k, s, h, x, nullptr, r_out, grad_s, part,
                                                             static_cast<int>(nch)));
   }
   ADJWT_CUDA_CHECK(cudaGetLastError());

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_adjoint(int64_t n, int K, con
                                                            const float* __restrict__ h, const float* __restrict__ r,
                                                            float* __restrict__ grad_s, float* __restrict__ part_h,
                                                            int nchunks) {
+  pdl_entry();
   extern __shared__ float sm[];
   float* rs = sm;                    // kChunk + K - 1
   float* ss = rs + kChunk + K - 1;   // kChunk
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_adjoint(int64_t n, int K, con
 
 __global__ void k_conv_reduce(int K, int nchunks, const float* __restrict__ part_h, float* __restrict__ grad_h,
                               int64_t total) {
+  pdl_entry();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int64_t b = idx / K;
@@ -105,6 +107,7 @@ __global__ void k_conv_reduce(int K, int nchunks, const float* __restrict__ part
 __global__ void __launch_bounds__(kThreads) k_conv_residual(int64_t n, int K, const float* __restrict__ h,
                                                             const float* __restrict__ s, const float* __restrict__ x,
                                                             float* __restrict__ r) {
+  pdl_entry();
   extern __shared__ float sm[];
   float* seg = sm;                  // s[m0 - K + 1 .. m0 + kChunk)
   float* hs = seg + kChunk + K - 1;
@@ -135,7 +138,7 @@ int64_t nchunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 void conv_reduce(unsigned nblocks, int k, int nchunks, const float* partials, float* grad_h, int64_t total,
                  cudaStream_t st) {
-  k_conv_reduce<<<nblocks, 256, 0, st>>>(k, nchunks, partials, grad_h, total);
+  pdl_launch(k_conv_reduce, nblocks, 256, 0, st, k, nchunks, partials, grad_h, total);
 }
 
 int64_t conv_partial_floats(int batch, int64_t n, int k) {
@@ -157,14 +160,14 @@ int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float
                                           static_cast<int>(smem)));
   dim3 grid(static_cast<unsigned>(nch), static_cast<unsigned>(batch));
   ADJWT_TRACED("conv_adjoint", 0, st,
-               k_conv_adjoint<<<grid, kThreads, smem, st>>>(n, k, s, h, r, grad_s, grad_h ? partials : nullptr,
+               pdl_launch(k_conv_adjoint, grid, kThreads, smem, st, n, k, s, h, r, grad_s, grad_h ? partials : nullptr,
                                                             static_cast<int>(nch)));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   if (grad_h) {
     const int64_t total = (int64_t)batch * k;
     const unsigned nb = static_cast<unsigned>((total + 255) / 256);
     ADJWT_TRACED("conv_reduce", 0, st,
-                 k_conv_reduce<<<nb, 256, 0, st>>>(k, static_cast<int>(nch), partials, grad_h, total));
+                 pdl_launch(k_conv_reduce, nb, 256, 0, st, k, static_cast<int>(nch), partials, grad_h, total));
     ADJWT_CUDA_CHECK(cudaGetLastError());
   }
   return ADJWT_OK;
@@ -231,7 +234,7 @@ int launch_conv_residual(int batch, int64_t n, int k, const float* h, const floa
     ADJWT_CUDA_CHECK(cudaFuncSetAttribute(k_conv_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           static_cast<int>(smem)));
   dim3 grid(static_cast<unsigned>(nchunks_of(nr)), static_cast<unsigned>(batch));
-  ADJWT_TRACED("conv_residual", 0, st, k_conv_residual<<<grid, kThreads, smem, st>>>(n, k, h, s, x, r));
+  ADJWT_TRACED("conv_residual", 0, st, pdl_launch(k_conv_residual, grid, kThreads, smem, st, n, k, h, s, x, r));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }

@@ -18,6 +18,7 @@ constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* a, int na, double sa, const double* b,
                                                            int nb, double sb, double* out) {
+  pdl_entry();
   __shared__ double red[kThreads / 32];
   double ta = 0.0, tb = 0.0;
   for (int i = threadIdx.x; i < na; i += kThreads) ta += a[i];
@@ -29,17 +30,19 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const double* a, int 
 }
 
 __global__ void __launch_bounds__(kThreads) k_sq_norm(const float* v, int64_t count, double* partials, int absval) {
+  pdl_entry();
   __shared__ double red[kThreads / 32];
-  double acc = 0.0;
+  float acc = 0.0f;  // per-thread float32 partial, float64 across the block and the grid
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads) {
-    const double x = v[i];
-    acc += absval ? fabs(x) : x * x;
+    const float x = v[i];
+    acc = absval ? acc + fabsf(x) : fmaf(x, x, acc);
   }
-  const double t = block_sum<kThreads>(acc, red);
+  const double t = block_sum<kThreads>((double)acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
 __global__ void k_scale(float* v, int64_t count, const double* sq_norm) {
+  pdl_entry();
   const float s = static_cast<float>(1.0 / sqrt(sq_norm[0]));
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     v[i] *= s;
@@ -96,12 +99,12 @@ int objective_async(const adjwt_fista_problem* pr, const float* x, const FistaWs
   rc = launch_blur_residual_norm(pr->blur, W.u, pr->b, W.part_b, s, &nb);
   if (rc) return rc;
   if (!have_l1) {
-    ADJWT_TRACED("l1_norm", 0, s, k_sq_norm<<<kNormBlocks, kThreads, 0, s>>>(x, pr->wt->num_coeffs, W.part_a, 1));
+    ADJWT_TRACED("l1_norm", 0, s, pdl_launch(k_sq_norm, kNormBlocks, kThreads, 0, s, x, pr->wt->num_coeffs, W.part_a, 1));
     ADJWT_CUDA_CHECK(cudaGetLastError());
     l1_slots = kNormBlocks;
   }
   ADJWT_TRACED("sum_partials", 0, s,
-               k_sum_partials<<<1, kThreads, 0, s>>>(W.part_a, l1_slots, pr->lambda, W.part_b, nb, 1.0, W.scalars));
+               pdl_launch(k_sum_partials, 1, kThreads, 0, s, W.part_a, l1_slots, pr->lambda, W.part_b, nb, 1.0, W.scalars));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
@@ -110,7 +113,7 @@ int objective_async(const adjwt_fista_problem* pr, const float* x, const FistaWs
 
 int launch_sum_partials(const double* a, int na, double sa, const double* b, int nb, double sb, double* out,
                         cudaStream_t s) {
-  ADJWT_TRACED("sum_partials", 0, s, k_sum_partials<<<1, kThreads, 0, s>>>(a, na, sa, b, nb, sb, out));
+  ADJWT_TRACED("sum_partials", 0, s, pdl_launch(k_sum_partials, 1, kThreads, 0, s, a, na, sa, b, nb, sb, out));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
@@ -157,10 +160,10 @@ int fista_lipschitz_impl(const adjwt_fista_problem* pr, float* v, int iters, voi
   const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
   const int64_t C = pr->wt->num_coeffs;
   auto normalise = [&]() -> int {
-    ADJWT_TRACED("sq_norm", 0, s, k_sq_norm<<<kNormBlocks, kThreads, 0, s>>>(v, C, W.part_a, 0));
+    ADJWT_TRACED("sq_norm", 0, s, pdl_launch(k_sq_norm, kNormBlocks, kThreads, 0, s, v, C, W.part_a, 0));
     ADJWT_TRACED("sum_partials", 0, s,
-                 k_sum_partials<<<1, kThreads, 0, s>>>(W.part_a, kNormBlocks, 1.0, nullptr, 0, 0.0, W.scalars));
-    ADJWT_TRACED("scale", 0, s, k_scale<<<kNormBlocks, kThreads, 0, s>>>(v, C, W.scalars));
+                 pdl_launch(k_sum_partials, 1, kThreads, 0, s, W.part_a, kNormBlocks, 1.0, nullptr, 0, 0.0, W.scalars));
+    ADJWT_TRACED("scale", 0, s, pdl_launch(k_scale, kNormBlocks, kThreads, 0, s, v, C, W.scalars));
     ADJWT_CUDA_CHECK(cudaGetLastError());
     return ADJWT_OK;
   };

@@ -76,6 +76,7 @@ constexpr int kAP = 8;
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
+  pdl_entry();
   constexpr int Lp = L - 1;
   constexpr int E = 2 * kTile + L - 2;  // extended samples feeding one tile
   constexpr int EP = E | 1;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
   __syncthreads();
 
   // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
-  double l1 = 0.0;
+  float l1 = 0.0f;  // per-thread float32 partial of |x_k|, float64 across the block
   {
     const int kk = lane, f = warp & 1, lb = warp >> 1;
     const int k = k0 + kk;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
             if (!full && lbase + p >= a.nc) x = y = 0.0f;
             xn[p] = x;
             yn[p] = y;
-            l1 += fabs((double)x);
+            if (a.l1) l1 += fabsf(x);
           }
           if (full) {
 #pragma unroll
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
     }
   }
   if (a.l1) {
-    const double tot = block_sum<kThreads>(l1, red);
+    const double tot = block_sum<kThreads>((double)l1, red);
     if (tid == 0) a.l1[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 }
@@ -324,6 +325,7 @@ __device__ __forceinline__ void pair_block(const float (&c0)[SynGeo<L>::NC], con
 
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
+  pdl_entry();
   using G = SynGeo<L>;
   constexpr int Lp = L - 1;
   __shared__ float C[4][G::KM][G::KP];
@@ -568,6 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
 // extended domain (periodic-extension borders, tiny images).
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_synthesis_gather(const SynArgs a, int border_only, int64_t count) {
+  pdl_entry();
   constexpr int Lp = L - 1;
   const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (idx >= count) return;
@@ -713,7 +716,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     slot += ncta;
     const char* name = !adjoint ? "wt_analysis" : (prox.x ? "wt_adjoint_prox" : "wt_adjoint");
     int rc = dispatch_L(fb.L, [&](auto Lc) {
-      ADJWT_TRACED(name, j, s, k_analysis<decltype(Lc)::value><<<grid, kThreads, 0, s>>>(a));
+      ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kThreads, 0, s, a));
       return ADJWT_OK;
     });
     if (rc) return rc;
@@ -752,14 +755,14 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
       if (L.generic_synth) {
         const int64_t count = (int64_t)a.Nr * a.Nc;
         const unsigned nb = (unsigned)((count + kThreads - 1) / kThreads);
-        ADJWT_TRACED("wt_synth_gather", j, s, k_synthesis_gather<LL><<<nb, kThreads, 0, s>>>(a, 0, count));
+        ADJWT_TRACED("wt_synth_gather", j, s, pdl_launch(k_synthesis_gather<LL>, nb, kThreads, 0, s, a, 0, count));
       } else {
         dim3 grid((a.Nc + kTile - 1) / kTile, (a.Nr + kTile - 1) / kTile);
-        ADJWT_TRACED("wt_synth", j, s, k_synthesis<LL><<<grid, kThreads, 0, s>>>(a));
+        ADJWT_TRACED("wt_synth", j, s, pdl_launch(k_synthesis<LL>, grid, kThreads, 0, s, a));
         if (p->bc == kPpd) {
           const int64_t count = (int64_t)2 * Lp * a.Nc + (int64_t)(a.Nr - 2 * Lp) * 2 * Lp;
           const unsigned nb = (unsigned)((count + kThreads - 1) / kThreads);
-          ADJWT_TRACED("wt_synth_gather", j, s, k_synthesis_gather<LL><<<nb, kThreads, 0, s>>>(a, 1, count));
+          ADJWT_TRACED("wt_synth_gather", j, s, pdl_launch(k_synthesis_gather<LL>, nb, kThreads, 0, s, a, 1, count));
         }
       }
       return ADJWT_OK;
