@@ -73,6 +73,13 @@ typedef struct adjwt_blur_plan adjwt_blur_plan;
 const char* adjwt_last_error(void);
 int adjwt_version(void);
 
+/* Device status word of the current device.  Kernels that stage tiles with
+ * the TMA unit bound every wait on an asynchronous copy (about one second);
+ * one that gives up records ADJWT_ERR_TIMEOUT here and returns without
+ * writing its outputs.  Reads the word into *status_out (0 = no failure)
+ * after synchronising the device, and resets it to 0 when clear != 0. */
+int adjwt_device_status(int* status_out, int clear);
+
 /* ------------------------------------------------------------------ wavelets
  * Plan of a J-level 2D transform of a rows x cols image.  Band lengths per
  * level and axis: n = floor((N + 3L')/2) for ZERO/SYM/PPD (the full
@@ -119,15 +126,20 @@ int adjwt_blur_plan_create(adjwt_blur_plan** out, int rows, int cols, const doub
                            const double* taps_c, int kc, int bc);
 void adjwt_blur_plan_destroy(adjwt_blur_plan* plan);
 int adjwt_blur_image_pitch(const adjwt_blur_plan* plan);
+/* Workspace of blur_normal: float64 partial sums followed by one image-sized
+ * scratch buffer holding R u - b between the two passes. */
 size_t adjwt_blur_workspace_size(const adjwt_blur_plan* plan);
 
 /* out = R in. */
 int blur(const adjwt_blur_plan* plan, const float* in, float* out, adjwt_stream_t stream);
 /* out = R^* in = E_r^T C_valid^T in (correlation, then fold the extension). */
 int blur_adjoint(const adjwt_blur_plan* plan, const float* in, float* out, adjwt_stream_t stream);
-/* Fused image-space data gradient g = R^*(R u - b) in one pass; if
- * half_sq_out (DEVICE double) is non-NULL it receives 1/2 ||R u - b||^2
- * (float64 accumulation).  b may be NULL (taken as 0). */
+/* Image-space data gradient g = R^*(R u - b) (the residual step of Sec. I);
+ * if half_sq_out (DEVICE double) is non-NULL it receives 1/2 ||R u - b||^2
+ * (float32 per thread, float64 across threads).  b may be NULL (taken as 0).
+ * With a workspace of adjwt_blur_workspace_size bytes (required when
+ * half_sq_out is set) and PSF radii <= 12, it runs as two TMA-staged passes
+ * through the scratch image; with ws == NULL, as one fused tiled kernel. */
 int blur_normal(const adjwt_blur_plan* plan, const float* u, const float* b, float* g, double* half_sq_out,
                 void* ws, size_t ws_bytes, adjwt_stream_t stream);
 

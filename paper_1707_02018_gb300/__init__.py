@@ -184,6 +184,13 @@ class BlurPlan:
         return out
 
 
+def device_status(clear=True):
+    """Device status word (0, or ADJWT_ERR_TIMEOUT after a bounded wait gave up); synchronises."""
+    v = C.c_int()
+    _lib.check(lib().adjwt_device_status(C.byref(v), int(bool(clear))))
+    return v.value
+
+
 def blur(plan, x, out=None, stream=None):
     _need(x, plan.rows * plan.image_pitch, "in")
     out = torch.zeros_like(x) if out is None else out
@@ -198,14 +205,19 @@ def blur_adjoint(plan, x, out=None, stream=None):
     return out
 
 
-def blur_normal(plan, u, b=None, g=None, want_norm=False, ws=None, stream=None):
-    """g = R^*(R u - b); with want_norm also returns 1/2 ||R u - b||^2 (float64 device scalar)."""
+def blur_normal(plan, u, b=None, g=None, want_norm=False, ws=None, stream=None, scratch=True):
+    """g = R^*(R u - b); with want_norm also returns 1/2 ||R u - b||^2 (float64 device scalar).
+
+    With a workspace (scratch=True or want_norm) radii <= 12 run as two
+    TMA-staged passes through a scratch image; without one, as a single
+    fused tiled kernel."""
     _need(u, plan.rows * plan.image_pitch, "u")
     g = torch.zeros_like(u) if g is None else g
     half = None
     wsp, nb = (None, 0)
     if want_norm:
         half = torch.zeros(1, dtype=torch.float64, device=u.device)
+    if want_norm or scratch or ws is not None:
         wsp, nb = _ws(plan.workspace_bytes, ws)
     _lib.check(lib().blur_normal(plan.handle, _ptr(u), _ptr(b), _ptr(g), _ptr(half), _ptr(wsp), nb, _stream(stream)))
     return (g, half) if want_norm else g

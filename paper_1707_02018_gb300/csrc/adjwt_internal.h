@@ -1,6 +1,7 @@
 // Internal types shared by the host plan code and the CUDA kernels of libadjwt.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -69,6 +70,15 @@ inline cudaError_t set_smem(Kernel kernel, size_t bytes) {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
+
+// ---------------------------------------------------------------- device status, TMA descriptors
+// Address of the device status word of the current device (null on failure).
+int* device_status_ptr();
+// 2D float32 tensor map over rows x cols (row pitch in floats) with a
+// box_rows x box_cols box; out-of-range elements read as zero.
+int make_tmap_2d_f32(CUtensorMap* map, const float* base, int rows, int cols, int pitch_floats, int box_rows,
+                     int box_cols);
+int sm_count();
 
 // ---------------------------------------------------------------- tracing
 int trace_begin(const char* name, int tag, cudaStream_t s);
@@ -146,17 +156,26 @@ int wt_l1_partial_slots(const adjwt_wt_plan* p);
 
 // Blur family.
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s);
+// Fused R^*(R u - b).  With an image-sized scratch buffer v and a radius
+// <= 12 it runs as two persistent TMA-staged passes (v = R u - b, g = R^* v);
+// otherwise as one tiled kernel.  *nparts receives the number of float64
+// partials written.
 int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b, float* g, double* partials,
-                       cudaStream_t s, int* nparts);
+                       float* scratch_v, cudaStream_t s, int* nparts);
+size_t blur_partials_bytes(const adjwt_blur_plan* p);
+// Persistent TMA-staged single pass (radius <= 12): R u (- b, partials) or R^* v.
+bool tma_blur_supported(const adjwt_blur_plan* p);
+int tma_blur_partial_slots(const adjwt_blur_plan* p);
+int launch_tma_blur(const adjwt_blur_plan* p, bool adjoint, const float* in, const float* b, float* out,
+                    double* partials, cudaStream_t s, int* nparts);
 int launch_blur_residual_norm(const adjwt_blur_plan* p, const float* u, const float* b, double* partials,
                               cudaStream_t s, int* nparts);
 int blur_partial_slots(const adjwt_blur_plan* p);
-// Register-blocked tiles for radii <= 12 (which: 0 fused normal, 1 forward /
-// residual norm when out is null, 2 adjoint).
+// Register-blocked fused R^*(R u - b) tiles for radii <= 12, no scratch.
 bool tiled_blur_supported(const adjwt_blur_plan* p);
 int tiled_blur_grid_slots(const adjwt_blur_plan* p);
-int launch_tiled_blur(const adjwt_blur_plan* p, int which, const float* in, const float* b, float* out,
-                      double* partials, cudaStream_t s);
+int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b, float* out, double* partials,
+                      cudaStream_t s);
 
 // Deterministic sum of float64 partials: out[0] = scale0 * sum(a[0..na)) + scale1 * sum(b[0..nb)).
 int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,

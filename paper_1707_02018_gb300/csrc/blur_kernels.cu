@@ -261,13 +261,15 @@ int launch(const char* name, K kernel, const adjwt_blur_plan* p, const BlurArgs&
 }  // namespace
 
 int blur_partial_slots(const adjwt_blur_plan* p) {
-  if (tiled_blur_supported(p)) return tiled_blur_grid_slots(p);
   dim3 g = grid_of(p);
-  return static_cast<int>(g.x * g.y);
+  int slots = static_cast<int>(g.x * g.y);
+  if (tiled_blur_supported(p)) slots = std::max(slots, tiled_blur_grid_slots(p));
+  if (tma_blur_supported(p)) slots = std::max(slots, tma_blur_partial_slots(p));
+  return slots;
 }
 
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s) {
-  if (tiled_blur_supported(p)) return launch_tiled_blur(p, adjoint ? 2 : 1, in, nullptr, out, nullptr, s);
+  if (tma_blur_supported(p)) return launch_tma_blur(p, adjoint, in, nullptr, out, nullptr, s, nullptr);
   BlurArgs a;
   fill_args(p, &a);
   a.in = in;
@@ -277,9 +279,17 @@ int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjo
 }
 
 int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b, float* g, double* partials,
-                       cudaStream_t s, int* nparts) {
-  if (nparts) *nparts = blur_partial_slots(p);
-  if (tiled_blur_supported(p)) return launch_tiled_blur(p, 0, u, b, g, partials, s);
+                       float* scratch_v, cudaStream_t s, int* nparts) {
+  if (scratch_v && tma_blur_supported(p)) {  // v = R u - b, then g = R^* v
+    int rc = launch_tma_blur(p, false, u, b, scratch_v, partials, s, nparts);
+    if (rc) return rc;
+    return launch_tma_blur(p, true, scratch_v, nullptr, g, nullptr, s, nullptr);
+  }
+  if (tiled_blur_supported(p)) {
+    if (nparts) *nparts = tiled_blur_grid_slots(p);
+    return launch_tiled_blur(p, u, b, g, partials, s);
+  }
+  if (nparts) *nparts = static_cast<int>(grid_of(p).x * grid_of(p).y);
   BlurArgs a;
   fill_args(p, &a);
   a.in = u;
@@ -291,8 +301,8 @@ int launch_blur_normal(const adjwt_blur_plan* p, const float* u, const float* b,
 
 int launch_blur_residual_norm(const adjwt_blur_plan* p, const float* u, const float* b, double* partials,
                               cudaStream_t s, int* nparts) {
-  if (nparts) *nparts = blur_partial_slots(p);
-  if (tiled_blur_supported(p)) return launch_tiled_blur(p, 1, u, b, nullptr, partials, s);
+  if (tma_blur_supported(p)) return launch_tma_blur(p, false, u, b, nullptr, partials, s, nparts);
+  if (nparts) *nparts = static_cast<int>(grid_of(p).x * grid_of(p).y);
   BlurArgs a;
   fill_args(p, &a);
   a.in = u;

@@ -1,4 +1,4 @@
-// Register-blocked tile kernels for R, R^* and the fused R^*(R u - b), for
+// Register-blocked tile kernel for the fused R^*(R u - b) without scratch, for
 // PSF radii up to kTiledMaxRadius (compile-time radius; the shorter axis is
 // zero-padded to the same radius, which leaves the operator unchanged).
 //
@@ -26,7 +26,7 @@ constexpr int kTiledMaxRadius = 12;
 namespace {
 
 constexpr int kT = 64;        // output tile side
-constexpr int kRB = 8;        // outputs per thread per pass
+constexpr int kRB = 16;       // outputs per thread per pass
 constexpr int kNT = 256;      // threads per CTA
 
 __host__ __device__ constexpr int odd_up(int v) { return v | 1; }
@@ -47,12 +47,6 @@ struct Geo {
   static constexpr int T2P = odd_up(ceil_to(kT, kRB) + 2 * R);
   static constexpr int A_FLOATS = (UR * UP > VROWS * VP) ? UR * UP : VROWS * VP;
   static constexpr int B_FLOATS = (T1R * T1P > kT * T2P) ? T1R * T1P : kT * T2P;
-  // single-operator kernels (forward / adjoint): one halo of R
-  static constexpr int SR = ceil_to(kT, kRB) + 2 * R;
-  static constexpr int SC = kT + 2 * R;
-  static constexpr int SP = odd_up(ceil_to(kT, kRB) + 2 * R);
-  static constexpr int S_FLOATS = SR * SP;
-  static constexpr int S2_FLOATS = kT * odd_up(SC);
 };
 
 struct TiledArgs {
@@ -126,7 +120,7 @@ __device__ __forceinline__ void hpass(const float* __restrict__ in, int in_p, fl
   }
 }
 
-// Final horizontal pass straight to global memory (kRB outputs -> two float4).
+// Final horizontal pass straight to global memory (kRB outputs -> kRB/4 float4).
 template <int R, bool FLIP>
 __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in_p, const TiledArgs& a, int y0,
                                             int x0, const float (&w)[2 * R + 1],
@@ -158,18 +152,23 @@ __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in
     const float* bb = bsub ? bsub + (size_t)y * a.pitch + x : nullptr;
     if (x + kRB <= a.cols) {
       if (bb) {
-        const float4 b0 = __ldg(reinterpret_cast<const float4*>(bb));
-        const float4 b1 = __ldg(reinterpret_cast<const float4*>(bb) + 1);
-        acc[0] -= b0.x; acc[1] -= b0.y; acc[2] -= b0.z; acc[3] -= b0.w;
-        acc[4] -= b1.x; acc[5] -= b1.y; acc[6] -= b1.z; acc[7] -= b1.w;
+#pragma unroll
+        for (int q = 0; q < kRB / 4; ++q) {
+          const float4 b4 = __ldg(reinterpret_cast<const float4*>(bb) + q);
+          acc[4 * q] -= b4.x;
+          acc[4 * q + 1] -= b4.y;
+          acc[4 * q + 2] -= b4.z;
+          acc[4 * q + 3] -= b4.w;
+        }
       }
       if (sq) {
 #pragma unroll
         for (int o = 0; o < kRB; ++o) *sq = fmaf(acc[o], acc[o], *sq);
       }
       if (dst) {
-        reinterpret_cast<float4*>(dst)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        reinterpret_cast<float4*>(dst)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+        for (int q = 0; q < kRB / 4; ++q)
+          reinterpret_cast<float4*>(dst)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
       }
     } else {
 #pragma unroll
@@ -332,80 +331,17 @@ __global__ void __launch_bounds__(kNT) k_blur_normal_t(const TiledArgs a) {
   }
 }
 
-// Forward R (optionally - b, optionally only the norm) or adjoint R^*.
-template <int R, bool ADJ>
-__global__ void __launch_bounds__(kNT) k_blur_single_t(const TiledArgs a) {
-  pdl_entry();
-  using G = Geo<R>;
-  extern __shared__ float sm[];
-  float* S = sm;                       // gathered input, SR x SP
-  float* T = S + G::S_FLOATS;          // after the vertical pass, kT x odd(SC)
-  int* src_c = reinterpret_cast<int*>(T + G::S2_FLOATS);
-  unsigned char* flip_r = reinterpret_cast<unsigned char*>(src_c + G::SC);
-  unsigned char* flip_c = flip_r + G::SR;
-  __shared__ double red[kNT / 32];
-  const int y0 = blockIdx.y * kT, x0 = blockIdx.x * kT;
-  const int tid = threadIdx.x;
-  const int mode = a.bc == 3 ? 2 : a.bc;
-  const bool sym = a.bc == 1;
-  const bool border = (y0 - R < 0) || (x0 - R < 0) || (y0 + kT + R > a.rows) || (x0 + kT + R > a.cols);
-  for (int c = tid; c < G::SC; c += kNT) src_c[c] = ext_src(x0 - R + c, a.cols, mode);
-  if (ADJ) {
-    for (int u = tid; u < G::SR; u += kNT) flip_r[u] = sym && odd_period(y0 - R + u, a.rows);
-    for (int c = tid; c < G::SP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
-  }
-  __syncthreads();
-  gather<G::SR, G::SC>(a.in, a.rows, a.cols, a.pitch, mode, y0 - R, x0 - R, S, G::SP, src_c);
-  __syncthreads();
-  float pr[2 * R + 1], pc[2 * R + 1];
-  load_taps<R>(a, pr, pc, !ADJ);
-  float sq = 0.0f;
-  const int TP = odd_up(G::SC);
-  if (ADJ && sym && border) {
-    vpass<R, true>(S, G::SP, T, TP, kT, G::SC, pr, flip_r);
-    __syncthreads();
-    hpass_store<R, true>(T, TP, a, y0, x0, pc, flip_c, nullptr, nullptr);
-  } else {
-    vpass<R, false>(S, G::SP, T, TP, kT, G::SC, pr, nullptr);
-    __syncthreads();
-    hpass_store<R, false>(T, TP, a, y0, x0, pc, nullptr, ADJ ? nullptr : a.b, a.partials ? &sq : nullptr);
-  }
-  if (!ADJ && a.partials) {
-    const double tot = block_sum<kNT>((double)sq, red);
-    if (tid == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * tot;
-  }
-}
-
 template <int R>
 size_t smem_normal_t() {
   using G = Geo<R>;
   return (size_t)(G::A_FLOATS + G::B_FLOATS) * 4 + G::UC * 4 + G::VROWS + G::VP + 16;
 }
 template <int R>
-size_t smem_single_t() {
-  using G = Geo<R>;
-  return (size_t)(G::S_FLOATS + G::S2_FLOATS) * 4 + G::SC * 4 + G::SR + G::SP + 16;
-}
-
-template <int R>
-int launch_r(int which, const TiledArgs& a, cudaStream_t s) {
+int launch_r(const TiledArgs& a, cudaStream_t s) {
   dim3 grid((a.cols + kT - 1) / kT, (a.rows + kT - 1) / kT);
-  if (which == 0) {
-    const size_t sm = smem_normal_t<R>();
-    ADJWT_CUDA_CHECK(set_smem(k_blur_normal_t<R>, sm));
-    ADJWT_TRACED("blur_normal", 0, s, pdl_launch(k_blur_normal_t<R>, grid, kNT, sm, s, a));
-  } else {
-    const size_t sm = smem_single_t<R>();
-    if (which == 1) {
-      ADJWT_CUDA_CHECK(
-          cudaFuncSetAttribute(k_blur_single_t<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      ADJWT_TRACED(a.out ? "blur" : "blur_residual", 0, s, pdl_launch(k_blur_single_t<R, false>, grid, kNT, sm, s, a));
-    } else {
-      ADJWT_CUDA_CHECK(
-          cudaFuncSetAttribute(k_blur_single_t<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      ADJWT_TRACED("blur_adjoint", 0, s, pdl_launch(k_blur_single_t<R, true>, grid, kNT, sm, s, a));
-    }
-  }
+  const size_t sm = smem_normal_t<R>();
+  ADJWT_CUDA_CHECK(set_smem(k_blur_normal_t<R>, sm));
+  ADJWT_TRACED("blur_normal", 0, s, pdl_launch(k_blur_normal_t<R>, grid, kNT, sm, s, a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
@@ -420,9 +356,9 @@ bool tiled_blur_supported(const adjwt_blur_plan* p) {
   return (p->kr / 2) <= kTiledMaxRadius && (p->kc / 2) <= kTiledMaxRadius;
 }
 
-// which: 0 = fused normal, 1 = forward (residual if out == null), 2 = adjoint
-int launch_tiled_blur(const adjwt_blur_plan* p, int which, const float* in, const float* b, float* out,
-                      double* partials, cudaStream_t s) {
+// Fused g = R^*(R u - b) in one kernel (no scratch image).
+int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b, float* out, double* partials,
+                      cudaStream_t s) {
   const int R = std::max(p->kr / 2, p->kc / 2);
   TiledArgs a{};
   a.in = in;
@@ -439,7 +375,7 @@ int launch_tiled_blur(const adjwt_blur_plan* p, int which, const float* in, cons
   switch (R) {
 #define ADJWT_R(r) \
   case r:          \
-    return launch_r<r>(which, a, s);
+    return launch_r<r>(a, s);
     ADJWT_R(0) ADJWT_R(1) ADJWT_R(2) ADJWT_R(3) ADJWT_R(4) ADJWT_R(5) ADJWT_R(6)
     ADJWT_R(7) ADJWT_R(8) ADJWT_R(9) ADJWT_R(10) ADJWT_R(11) ADJWT_R(12)
 #undef ADJWT_R

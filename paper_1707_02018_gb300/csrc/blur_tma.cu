@@ -1,0 +1,369 @@
+// Persistent TMA-staged single blur pass: R u (optionally - b, optionally
+// with per-CTA 1/2 ||R u - b||^2 partials) or R^* v, for radii up to
+// kTmaMaxRadius.  Same operator definitions as blur_kernels.cu.
+//
+// Output tiles are kTH x kTW.  A CTA walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with two staging buffers: while it filters tile
+// t, the TMA unit already copies the (kTH + 2R) x (kTW + 2 XA) input window of
+// the next tile into the other buffer (XA = R rounded up to 4 floats keeps the
+// box start 16-byte aligned).  Windows that leave the image are zero-filled
+// by the TMA unit, which is exactly the zero extension; under the symmetric
+// and periodic extensions such border windows are gathered by the threads
+// instead (through the extension map), and R^* takes the orientation-aware
+// taps there.
+//
+// Per tile: a vertical pass (a thread filters 16 rows of one column from a
+// register window, lanes on consecutive columns) writes an odd-pitch buffer
+// T; a horizontal pass (lanes on the 32 rows, a warp per 16-column block)
+// produces 16 consecutive outputs per thread and stores them as float4.
+#include <algorithm>
+
+#include "adjwt_internal.h"
+#include "device_common.cuh"
+#include "tma.cuh"
+
+namespace adjwt {
+
+constexpr int kTmaMaxRadius = 12;
+
+namespace {
+
+constexpr int kTH = 32;    // output rows per tile
+constexpr int kTW = 128;   // output columns per tile
+constexpr int kRB = 16;    // outputs per thread per pass
+constexpr int kPT = 288;   // threads: 9 warps (vertical pass items), 8 of them in the horizontal pass
+
+__host__ __device__ constexpr int up4(int v) { return (v + 3) / 4 * 4; }
+__host__ __device__ constexpr int up32(int v) { return (v + 31) / 32 * 32; }
+
+template <int R>
+struct TG {
+  static constexpr int XA = up4(R);           // staged columns left of the tile
+  static constexpr int BW = kTW + 2 * XA;     // box width (floats)
+  static constexpr int BH = kTH + 2 * R;      // box height (rows)
+  static constexpr int BUF = up32(BH * BW);   // floats per staging buffer (128-byte multiple)
+  static constexpr int VC = kTW + 2 * R;      // columns of the vertical-pass output
+  static constexpr int TP = VC | 1;           // odd pitch of T
+  static constexpr size_t smem_bytes() {
+    return 128 + (size_t)(2 * BUF + kTH * TP) * 4 + (size_t)(BH + BW) * 4 + BH + BW;
+  }
+};
+
+struct TmaBlurArgs {
+  const float* in;
+  const float* b;      // forward: subtract b (may be null)
+  float* out;          // may be null (forward: residual norm only)
+  double* partials;    // forward: per-CTA 1/2 sum (R u - b)^2 (may be null)
+  int* status;         // device status word (timeouts)
+  int rows, cols, pitch, bc;  // bc: 0 zero, 1 sym, 3 per
+  float pr[2 * kTmaMaxRadius + 1], pc[2 * kTmaMaxRadius + 1];  // taps as given, padded to 2R+1
+};
+
+__device__ __forceinline__ bool odd_period(int x, int N) { return (floor_div(x, N) & 1) != 0; }
+
+// Gather the extended window of tile (x0, y0) through the extension map.
+template <int R>
+__device__ __forceinline__ void gather_tile(const TmaBlurArgs& a, int mode, int x0, int y0, float* dst, int* src_r,
+                                            int* src_c) {
+  using G = TG<R>;
+  for (int i = threadIdx.x; i < G::BH; i += kPT) src_r[i] = ext_src(y0 - R + i, a.rows, mode);
+  for (int i = threadIdx.x; i < G::BW; i += kPT) src_c[i] = ext_src(x0 - G::XA + i, a.cols, mode);
+  __syncthreads();
+  constexpr int total = G::BH * G::BW, U = 8;
+  for (int b0 = threadIdx.x; b0 < total; b0 += U * kPT) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * kPT;
+      v[u] = 0.0f;
+      if (i < total) {
+        const int rr = i / G::BW, cc = i - rr * G::BW;
+        const int sr = src_r[rr], sc = src_c[cc];
+        if (sr >= 0 && sc >= 0) v[u] = __ldg(a.in + (size_t)sr * a.pitch + sc);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b0 + u * kPT;
+      if (i < total) dst[i] = v[u];
+    }
+  }
+}
+
+// T[r][c] = sum_t w[t] S[r + t][c + XA - R]; r < kTH, c < VC
+template <int R, bool FLIP>
+__device__ __forceinline__ void vertical(const float* __restrict__ S, float* __restrict__ T, const float (&w)[2 * R + 1],
+                                         const unsigned char* __restrict__ flip_r) {
+  using G = TG<R>;
+  constexpr int K = 2 * R + 1, NW = kRB + 2 * R;
+  for (int item = threadIdx.x; item < 2 * G::VC; item += kPT) {
+    const int rb = item >= G::VC ? 1 : 0, c = item - rb * G::VC;
+    const float* src = S + kRB * rb * G::BW + c + (G::XA - R);
+    float acc[kRB];
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) acc[o] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const float v = src[j * G::BW];
+      bool f = false;
+      if (FLIP) f = flip_r[kRB * rb + j] != 0;
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) {
+        const int t = j - o;
+        if (t >= 0 && t < K) acc[o] = fmaf(FLIP ? (f ? w[K - 1 - t] : w[t]) : w[t], v, acc[o]);
+      }
+    }
+    float* dst = T + kRB * rb * G::TP + c;
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) dst[o * G::TP] = acc[o];
+  }
+}
+
+// out[y0 + r][x0 + 16 blk + o] = sum_t w[t] T[r][16 blk + o + t] (- b), warp = blk, lane = r
+template <int R, bool ADJ, bool FLIP>
+__device__ __forceinline__ void horizontal(const float* __restrict__ T, const TmaBlurArgs& a, int x0, int y0,
+                                           const float (&w)[2 * R + 1], const unsigned char* __restrict__ flip_c,
+                                           float& sq) {
+  using G = TG<R>;
+  constexpr int K = 2 * R + 1, NW = kRB + 2 * R;
+  const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
+  if (warp >= kTW / kRB) return;
+  const int y = y0 + r, x = x0 + kRB * warp;
+  if (y >= a.rows || x >= a.cols) return;
+  const bool full = x + kRB <= a.cols;
+  float bv[kRB];
+  const bool sub = !ADJ && a.b != nullptr;
+  if (sub) {
+    const float* bb = a.b + (size_t)y * a.pitch + x;
+    if (full) {
+#pragma unroll
+      for (int q = 0; q < kRB / 4; ++q) {
+        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bb) + q);
+        bv[4 * q] = b4.x;
+        bv[4 * q + 1] = b4.y;
+        bv[4 * q + 2] = b4.z;
+        bv[4 * q + 3] = b4.w;
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < kRB; ++o) bv[o] = x + o < a.cols ? __ldg(bb + o) : 0.0f;
+    }
+  }
+  const float* src = T + r * G::TP + kRB * warp;
+  float acc[kRB];
+#pragma unroll
+  for (int o = 0; o < kRB; ++o) acc[o] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const float v = src[j];
+    bool f = false;
+    if (FLIP) f = flip_c[kRB * warp + j] != 0;
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) {
+      const int t = j - o;
+      if (t >= 0 && t < K) acc[o] = fmaf(FLIP ? (f ? w[K - 1 - t] : w[t]) : w[t], v, acc[o]);
+    }
+  }
+  if (sub) {
+#pragma unroll
+    for (int o = 0; o < kRB; ++o) acc[o] -= bv[o];
+  }
+  if (!ADJ && a.partials) {
+#pragma unroll
+    for (int o = 0; o < kRB; ++o)
+      if (full || x + o < a.cols) sq = fmaf(acc[o], acc[o], sq);
+  }
+  if (!a.out) return;
+  float* dst = a.out + (size_t)y * a.pitch + x;
+  if (full) {
+#pragma unroll
+    for (int q = 0; q < kRB / 4; ++q)
+      reinterpret_cast<float4*>(dst)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int o = 0; o < kRB; ++o)
+      if (x + o < a.cols) dst[o] = acc[o];
+  }
+}
+
+template <int R, bool ADJ>
+__global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid_constant__ CUtensorMap map, const TmaBlurArgs a) {
+  pdl_entry();
+  using G = TG<R>;
+  constexpr int K = 2 * R + 1;
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t bar[2];
+  __shared__ double red[kPT / 32];
+  unsigned char* base = dyn + ((128 - (smem_u32(dyn) & 127)) & 127);
+  float* buf[2] = {reinterpret_cast<float*>(base), reinterpret_cast<float*>(base) + G::BUF};
+  float* T = buf[1] + G::BUF;
+  int* src_r = reinterpret_cast<int*>(T + kTH * G::TP);
+  int* src_c = src_r + G::BH;
+  unsigned char* flip_r = reinterpret_cast<unsigned char*>(src_c + G::BW);
+  unsigned char* flip_c = flip_r + G::BH;
+
+  const int tid = threadIdx.x;
+  const int tiles_x = (a.cols + kTW - 1) / kTW;
+  const int ntiles = tiles_x * ((a.rows + kTH - 1) / kTH);
+  const int mode = a.bc == 3 ? 2 : a.bc;
+  const bool sym = a.bc == 1;
+  // taps: R is a convolution (reversed taps), R^* a correlation (taps as given)
+  float wr[K], wc[K];
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    wr[t] = ADJ ? a.pr[t] : a.pr[K - 1 - t];
+    wc[t] = ADJ ? a.pc[t] : a.pc[K - 1 - t];
+  }
+  auto border = [&](int x0, int y0) {
+    return y0 - R < 0 || x0 - R < 0 || y0 + kTH + R > a.rows || x0 + kTW + R > a.cols;
+  };
+  // windows leaving the image take the TMA unit only under the zero extension
+  auto via_tma = [&](int x0, int y0) { return a.bc == 0 || !border(x0, y0); };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t phase = 0, pending = 0;  // per buffer: parity of the next wait, copy in flight
+  auto issue = [&](int t, int b) {
+    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[b], G::BH * G::BW * 4);
+      tma_load_2d(buf[b], &map, &bar[b], x0 - G::XA, y0 - R);
+    }
+    pending |= 1u << b;
+  };
+  auto drain = [&]() {
+    for (int b = 0; b < 2; ++b)
+      if (pending & (1u << b)) mbar_wait(&bar[b], (phase >> b) & 1);
+  };
+
+  float sq = 0.0f;
+  int t = blockIdx.x, b = 0;
+  if (t < ntiles) {
+    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
+    if (via_tma(x0, y0)) {
+      issue(t, 0);
+    } else {
+      gather_tile<R>(a, mode, x0, y0, buf[0], src_r, src_c);
+      __syncthreads();
+    }
+  }
+  for (; t < ntiles; t += gridDim.x, b ^= 1) {
+    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
+    const int tn = t + gridDim.x;
+    int xn = 0, yn = 0;
+    bool next_gather = false;
+    if (tn < ntiles) {
+      const int tyn = tn / tiles_x;
+      yn = tyn * kTH;
+      xn = (tn - tyn * tiles_x) * kTW;
+      if (via_tma(xn, yn))
+        issue(tn, b ^ 1);
+      else
+        next_gather = true;
+    }
+    bool ok = true;
+    if (pending & (1u << b)) {
+      ok = mbar_wait(&bar[b], (phase >> b) & 1);
+      if (ok) {
+        phase ^= 1u << b;
+        pending &= ~(1u << b);
+      }
+    }
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
+      drain();
+      return;
+    }
+    const bool flip = ADJ && sym && border(x0, y0);
+    if (flip) {
+      for (int i = tid; i < G::BH; i += kPT) flip_r[i] = odd_period(y0 - R + i, a.rows);
+      for (int i = tid; i < G::VC; i += kPT) flip_c[i] = odd_period(x0 - R + i, a.cols);
+      __syncthreads();
+      vertical<R, true>(buf[b], T, wr, flip_r);
+      __syncthreads();
+      horizontal<R, ADJ, true>(T, a, x0, y0, wc, flip_c, sq);
+    } else {
+      vertical<R, false>(buf[b], T, wr, nullptr);
+      __syncthreads();
+      horizontal<R, ADJ, false>(T, a, x0, y0, wc, nullptr, sq);
+    }
+    if (next_gather) gather_tile<R>(a, mode, xn, yn, buf[b ^ 1], src_r, src_c);
+    __syncthreads();  // T and the gathered buffer are reused next iteration
+  }
+  if (!ADJ && a.partials) {
+    const double tot = block_sum<kPT>((double)sq, red);
+    if (tid == 0) a.partials[blockIdx.x] = 0.5 * tot;
+  }
+}
+
+template <int R, bool ADJ>
+int launch_r(const TmaBlurArgs& a, cudaStream_t s, int* nparts) {
+  using G = TG<R>;
+  const size_t smem = G::smem_bytes();
+  auto kern = k_blur_tma<R, ADJ>;
+  ADJWT_CUDA_CHECK(set_smem(kern, smem));
+  static int occ = 0;  // resident CTAs per SM (same on every device of one process)
+  if (!occ) {
+    int v = 0;
+    ADJWT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kPT, smem));
+    occ = std::max(v, 1);
+  }
+  const int ntiles = ((a.cols + kTW - 1) / kTW) * ((a.rows + kTH - 1) / kTH);
+  const int grid = std::min(ntiles, sm_count() * occ);
+  CUtensorMap map;
+  int rc = make_tmap_2d_f32(&map, a.in, a.rows, a.cols, a.pitch, G::BH, G::BW);
+  if (rc) return rc;
+  if (nparts) *nparts = grid;
+  const char* name = ADJ ? "blur_adjoint" : (a.out ? "blur" : "blur_residual");
+  ADJWT_TRACED(name, 0, s, pdl_launch(kern, grid, kPT, smem, s, map, a));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+}  // namespace
+
+bool tma_blur_supported(const adjwt_blur_plan* p) {
+  return (p->kr / 2) <= kTmaMaxRadius && (p->kc / 2) <= kTmaMaxRadius;
+}
+
+// The grid never exceeds the tile count, which bounds the partial slots.
+int tma_blur_partial_slots(const adjwt_blur_plan* p) {
+  return ((p->cols + kTW - 1) / kTW) * ((p->rows + kTH - 1) / kTH);
+}
+
+int launch_tma_blur(const adjwt_blur_plan* p, bool adjoint, const float* in, const float* b, float* out,
+                    double* partials, cudaStream_t s, int* nparts) {
+  const int R = std::max(p->kr / 2, p->kc / 2);
+  TmaBlurArgs a{};
+  a.in = in;
+  a.b = adjoint ? nullptr : b;
+  a.out = out;
+  a.partials = adjoint ? nullptr : partials;
+  a.status = device_status_ptr();
+  a.rows = p->rows;
+  a.cols = p->cols;
+  a.pitch = p->image_pitch;
+  a.bc = p->bc;
+  const int orr = R - p->kr / 2, oc = R - p->kc / 2;
+  for (int t = 0; t < p->kr; ++t) a.pr[orr + t] = static_cast<float>(p->taps_r[t]);
+  for (int t = 0; t < p->kc; ++t) a.pc[oc + t] = static_cast<float>(p->taps_c[t]);
+  if (nparts) *nparts = 0;
+  switch (R) {
+#define ADJWT_R(r)                                                                       \
+  case r:                                                                                \
+    return adjoint ? launch_r<r, true>(a, s, nparts) : launch_r<r, false>(a, s, nparts);
+    ADJWT_R(0) ADJWT_R(1) ADJWT_R(2) ADJWT_R(3) ADJWT_R(4) ADJWT_R(5) ADJWT_R(6)
+    ADJWT_R(7) ADJWT_R(8) ADJWT_R(9) ADJWT_R(10) ADJWT_R(11) ADJWT_R(12)
+#undef ADJWT_R
+    default:
+      return fail(ADJWT_ERR_INVALID_ARG, "TMA blur: radius above 12");
+  }
+}
+
+}  // namespace adjwt

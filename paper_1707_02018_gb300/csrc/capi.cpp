@@ -159,13 +159,18 @@ extern "C" int blur_normal(const adjwt_blur_plan* p, const float* u, const float
   if (overlap(u, nb, g, nb) || (b && overlap(b, nb, g, nb)))
     return fail(ADJWT_ERR_ALIAS, "blur_normal: g overlaps an input");
   double* parts = nullptr;
-  if (half_sq_out) {
+  float* v = nullptr;
+  if (half_sq_out || ws) {
     rc = check_ws(ws, ws_bytes, adjwt_blur_workspace_size(p), "blur_normal");
     if (rc) return rc;
-    parts = static_cast<double*>(ws);
+    if (overlap(ws, adjwt_blur_workspace_size(p), u, nb) || overlap(ws, adjwt_blur_workspace_size(p), g, nb) ||
+        (b && overlap(ws, adjwt_blur_workspace_size(p), b, nb)))
+      return fail(ADJWT_ERR_ALIAS, "blur_normal: workspace overlaps a tensor");
+    parts = half_sq_out ? static_cast<double*>(ws) : nullptr;
+    v = reinterpret_cast<float*>(static_cast<char*>(ws) + blur_partials_bytes(p));
   }
   int np = 0;
-  rc = launch_blur_normal(p, u, b, g, parts, stream, &np);
+  rc = launch_blur_normal(p, u, b, g, parts, v, stream, &np);
   if (rc) return rc;
   if (half_sq_out) return launch_sum_partials(parts, np, 1.0, nullptr, 0, 0.0, half_sq_out, stream);
   return ADJWT_OK;

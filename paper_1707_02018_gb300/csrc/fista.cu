@@ -55,6 +55,7 @@ struct FistaWs {
   float* ll1;
   float* u;
   float* g;
+  float* bv;  // blur scratch image (R u - b)
   double* part_a;
   double* part_b;
   double* scalars;  // [0] result, [1] scratch
@@ -75,6 +76,7 @@ FistaWs layout_ws(const adjwt_fista_problem* pr, char* base) {
   L.ll1 = reinterpret_cast<float*>(take(w->ll_buf_floats[1] * sizeof(float)));
   L.u = reinterpret_cast<float*>(take(img));
   L.g = reinterpret_cast<float*>(take(img));
+  L.bv = reinterpret_cast<float*>(take(img));
   const int slots = std::max(std::max(wt_l1_partial_slots(w), blur_partial_slots(pr->blur)), kNormBlocks);
   L.part_a = reinterpret_cast<double*>(take(slots * sizeof(double)));
   L.part_b = reinterpret_cast<double*>(take(slots * sizeof(double)));
@@ -125,7 +127,7 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
   const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
   int rc = launch_wt_synth(pr->wt, st->y, W.u, W.ll0, W.ll1, s);
   if (rc) return rc;
-  rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, s, nullptr);
+  rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr);
   if (rc) return rc;
   const double t = st->t;
   const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
@@ -173,7 +175,7 @@ int fista_lipschitz_impl(const adjwt_fista_problem* pr, float* v, int iters, voi
   for (int it = 0; it < iters; ++it) {
     rc = launch_wt_synth(pr->wt, v, W.u, W.ll0, W.ll1, s);
     if (rc) return rc;
-    rc = launch_blur_normal(pr->blur, W.u, nullptr, W.g, nullptr, s, nullptr);
+    rc = launch_blur_normal(pr->blur, W.u, nullptr, W.g, nullptr, W.bv, s, nullptr);
     if (rc) return rc;
     rc = launch_wt_analysis(pr->wt, W.g, v, true, none, W.ll0, W.ll1, s, nullptr);
     if (rc) return rc;

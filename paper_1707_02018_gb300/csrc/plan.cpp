@@ -218,7 +218,15 @@ extern "C" void adjwt_blur_plan_destroy(adjwt_blur_plan* p) { delete p; }
 
 extern "C" int adjwt_blur_image_pitch(const adjwt_blur_plan* p) { return p ? p->image_pitch : 0; }
 
+namespace adjwt {
+size_t blur_partials_bytes(const adjwt_blur_plan* p) {
+  return static_cast<size_t>(round_up(static_cast<int64_t>(blur_partial_slots(p)) * 8 + 8, 256));
+}
+}  // namespace adjwt
+
+// partial sums, then one image-sized scratch buffer (R u - b between the two passes)
 extern "C" size_t adjwt_blur_workspace_size(const adjwt_blur_plan* p) {
   if (!p) return 0;
-  return static_cast<size_t>(round_up(static_cast<int64_t>(blur_partial_slots(p)) * 8 + 8, 256));
+  const size_t img = static_cast<size_t>(round_up(static_cast<int64_t>(p->rows) * p->image_pitch * 4, 256));
+  return blur_partials_bytes(p) + img;
 }

@@ -54,10 +54,16 @@ def test_full_size_15x15(adj, bc):
     plan = adj.BlurPlan(rows, cols, p, p, bc)
     u = piecewise_smooth_image(rows, cols, 21)
     b = piecewise_smooth_image(rows, cols, 22)
-    g, half = adj.blur_normal(plan, image_dev(plan, u), image_dev(plan, b), want_norm=True)
+    du = image_dev(plan, u)
+    g, half = adj.blur_normal(plan, du, image_dev(plan, b), want_norm=True)
     gw, hw = oblur.blur_normal(u, b, p, p, bc)
     assert_close(to_host_image(g, rows, cols), gw, what=f"R^*(Ru-b) 2048 {bc}")
     assert abs(float(half) - hw) <= 1e-5 * hw
+    # single passes: every CTA of the persistent grid walks several tiles
+    assert_close(to_host_image(adj.blur(plan, du), rows, cols), oblur.blur(u, p, p, bc), what=f"R 2048 {bc}")
+    assert_close(to_host_image(adj.blur_adjoint(plan, du), rows, cols), oblur.blur_adjoint(u, p, p, bc),
+                 what=f"R^* 2048 {bc}")
+    assert adj.device_status() == 0
 
 
 @pytest.mark.parametrize("kr,kc", [(65, 1), (27, 5), (25, 25), (1, 1)])
@@ -88,3 +94,30 @@ def test_gpu_blur_dot_product(adj):
         lhs = float((adj.blur(plan, x).double() * y.double()).sum())
         rhs = float((x.double() * adj.blur_adjoint(plan, y).double()).sum())
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("kr,kc", [(15, 15), (25, 3), (1, 9), (7, 1)])
+def test_blur_tma_and_tiled_paths(adj, bc, kr, kc):
+    """R and R^* run as persistent TMA-staged passes; R^*(R u - b) with a
+    workspace as two such passes, without one as a single fused tiled kernel.
+    All against the oracle on shapes spanning several tiles in each direction
+    with ragged edges; the device status word stays clear."""
+    pr = random_taps(kr, kr + 11) if kr > 1 else np.array([1.0])
+    pc = random_taps(kc, kc + 12) if kc > 1 else np.array([1.0])
+    for rows, cols in [(200, 300), (131, 257), (64, 128), (13, 600)]:
+        plan = adj.BlurPlan(rows, cols, pr, pc, bc)
+        u = random_vector((rows, cols), rows + 3 * cols)
+        b = random_vector((rows, cols), rows + 5 * cols)
+        du, db = image_dev(plan, u), image_dev(plan, b)
+        gw, hw = oblur.blur_normal(u, b, pr, pc, bc)
+        g1, h1 = adj.blur_normal(plan, du, db, want_norm=True)
+        g0 = adj.blur_normal(plan, du, db, scratch=False)
+        what = f"{bc} {kr}x{kc} {rows}x{cols}"
+        assert_close(to_host_image(g1, rows, cols), gw, what="stream " + what)
+        assert_close(to_host_image(g0, rows, cols), gw, what="tiled " + what)
+        assert abs(float(h1) - hw) <= 1e-5 * hw
+        assert_close(to_host_image(adj.blur(plan, du), rows, cols), oblur.blur(u, pr, pc, bc), what="R " + what)
+        assert_close(to_host_image(adj.blur_adjoint(plan, du), rows, cols), oblur.blur_adjoint(u, pr, pc, bc),
+                     what="R^* " + what)
+    assert adj.device_status() == 0
