@@ -8,9 +8,10 @@
 // the next tile into the other buffer (XA = R rounded up to 4 floats keeps the
 // box start 16-byte aligned).  Windows that leave the image are zero-filled
 // by the TMA unit, which is exactly the zero extension; under the symmetric
-// and periodic extensions such border windows are gathered by the threads
-// instead (through the extension map), and R^* takes the orientation-aware
-// taps there.
+// and periodic extensions the threads then overwrite the off-image cells of
+// such border windows through the extension map, and R^* takes the
+// orientation-aware taps there (unless the PSF is palindromic, where flipping
+// changes nothing).
 //
 // Per tile: a vertical pass (a thread filters 16 rows of one column from a
 // register window, lanes on consecutive columns) writes an odd-pitch buffer
@@ -45,7 +46,7 @@ struct TG {
   static constexpr int VC = kTW + 2 * R;      // columns of the vertical-pass output
   static constexpr int TP = VC | 1;           // odd pitch of T
   static constexpr size_t smem_bytes() {
-    return 128 + (size_t)(2 * BUF + kTH * TP) * 4 + (size_t)(BH + BW) * 4 + BH + BW;
+    return 128 + (size_t)(2 * BUF + kTH * TP) * 4 + BH + BW;
   }
 };
 
@@ -56,39 +57,60 @@ struct TmaBlurArgs {
   double* partials;    // forward: per-CTA 1/2 sum (R u - b)^2 (may be null)
   int* status;         // device status word (timeouts)
   int rows, cols, pitch, bc;  // bc: 0 zero, 1 sym, 3 per
+  int sym_taps;        // both tap vectors palindromic: R^* needs no orientation flips
   float pr[2 * kTmaMaxRadius + 1], pc[2 * kTmaMaxRadius + 1];  // taps as given, padded to 2R+1
 };
 
 __device__ __forceinline__ bool odd_period(int x, int N) { return (floor_div(x, N) & 1) != 0; }
 
-// Gather the extended window of tile (x0, y0) through the extension map.
-template <int R>
-__device__ __forceinline__ void gather_tile(const TmaBlurArgs& a, int mode, int x0, int y0, float* dst, int* src_r,
-                                            int* src_c) {
-  using G = TG<R>;
-  for (int i = threadIdx.x; i < G::BH; i += kPT) src_r[i] = ext_src(y0 - R + i, a.rows, mode);
-  for (int i = threadIdx.x; i < G::BW; i += kPT) src_c[i] = ext_src(x0 - G::XA + i, a.cols, mode);
-  __syncthreads();
-  constexpr int total = G::BH * G::BW, U = 8;
-  for (int b0 = threadIdx.x; b0 < total; b0 += U * kPT) {
-    float v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = b0 + u * kPT;
-      v[u] = 0.0f;
-      if (i < total) {
-        const int rr = i / G::BW, cc = i - rr * G::BW;
-        const int sr = src_r[rr], sc = src_c[cc];
-        if (sr >= 0 && sc >= 0) v[u] = __ldg(a.in + (size_t)sr * a.pitch + sc);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = b0 + u * kPT;
-      if (i < total) dst[i] = v[u];
-    }
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Source of virtual index x under the symmetric / periodic extension, with a
+// division-free path for the first reflection or wrap.
+__device__ __forceinline__ int ext_near(int x, int N, int mode) {
+  if (x >= 0 && x < N) return x;
+  if (x >= -N && x < 2 * N) {
+    if (mode == 1) return x < 0 ? -1 - x : 2 * N - 1 - x;
+    return x < 0 ? x + N : x - N;
   }
+  return ext_src(x, N, mode);
 }
+
+// Off-image cells of a staged window, as strips: rows above / below the
+// image (full width), then the columns left / right of it on the other rows.
+// The TMA unit zero-fills them; under the symmetric and periodic extensions
+// the threads overwrite them with their sources.
+template <int R>
+struct Strips {
+  int x0, y0, rlo, rhi, clo, chi, side, ntop, nbot, total;
+  __device__ __forceinline__ Strips(const TmaBlurArgs& a, int x0_, int y0_) : x0(x0_), y0(y0_) {
+    using G = TG<R>;
+    rlo = clampi(R - y0, 0, G::BH);
+    rhi = clampi(a.rows - (y0 - R), rlo, G::BH);
+    clo = clampi(G::XA - x0, 0, G::BW);
+    chi = clampi(a.cols - (x0 - G::XA), clo, G::BW);
+    side = clo + (G::BW - chi);
+    ntop = rlo * G::BW;
+    nbot = (G::BH - rhi) * G::BW;
+    total = ntop + nbot + (rhi - rlo) * side;
+  }
+  // staged cell index of off-image cell i < total
+  __device__ __forceinline__ int cell(int i) const {
+    using G = TG<R>;
+    if (i < ntop) return i;
+    if (i < ntop + nbot) return rhi * G::BW + (i - ntop);
+    const int j = i - ntop - nbot, rr = j / side, k = j - rr * side;
+    return (rlo + rr) * G::BW + (k < clo ? k : chi + (k - clo));
+  }
+  __device__ __forceinline__ float load(const TmaBlurArgs& a, int mode, int c) const {
+    using G = TG<R>;
+    const int rr = c / G::BW, cc = c - rr * G::BW;
+    const int sr = ext_near(y0 - R + rr, a.rows, mode), sc = ext_near(x0 - G::XA + cc, a.cols, mode);
+    return __ldg(a.in + (size_t)sr * a.pitch + sc);
+  }
+};
+
+constexpr int kFillRegs = 6;  // off-image cells per thread fetched before the TMA wait
 
 // T[r][c] = sum_t w[t] S[r + t][c + XA - R]; r < kTH, c < VC
 template <int R, bool FLIP>
@@ -194,12 +216,9 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
   __shared__ double red[kPT / 32];
-  unsigned char* base = dyn + ((128 - (smem_u32(dyn) & 127)) & 127);
-  float* buf[2] = {reinterpret_cast<float*>(base), reinterpret_cast<float*>(base) + G::BUF};
-  float* T = buf[1] + G::BUF;
-  int* src_r = reinterpret_cast<int*>(T + kTH * G::TP);
-  int* src_c = src_r + G::BH;
-  unsigned char* flip_r = reinterpret_cast<unsigned char*>(src_c + G::BW);
+  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));  // buffer b at buf0 + b * BUF
+  float* T = buf0 + 2 * G::BUF;
+  unsigned char* flip_r = reinterpret_cast<unsigned char*>(T + kTH * G::TP);
   unsigned char* flip_c = flip_r + G::BH;
 
   const int tid = threadIdx.x;
@@ -214,11 +233,10 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
     wr[t] = ADJ ? a.pr[t] : a.pr[K - 1 - t];
     wc[t] = ADJ ? a.pc[t] : a.pc[K - 1 - t];
   }
+  // does the staged window leave the image?
   auto border = [&](int x0, int y0) {
-    return y0 - R < 0 || x0 - R < 0 || y0 + kTH + R > a.rows || x0 + kTW + R > a.cols;
+    return y0 - R < 0 || x0 - G::XA < 0 || y0 + kTH + R > a.rows || x0 + kTW + G::XA > a.cols;
   };
-  // windows leaving the image take the TMA unit only under the zero extension
-  auto via_tma = [&](int x0, int y0) { return a.bc == 0 || !border(x0, y0); };
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -233,7 +251,7 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
     if (tid == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&bar[b], G::BH * G::BW * 4);
-      tma_load_2d(buf[b], &map, &bar[b], x0 - G::XA, y0 - R);
+      tma_load_2d(buf0 + b * G::BUF, &map, &bar[b], x0 - G::XA, y0 - R);
     }
     pending |= 1u << b;
   };
@@ -244,28 +262,21 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
 
   float sq = 0.0f;
   int t = blockIdx.x, b = 0;
-  if (t < ntiles) {
-    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
-    if (via_tma(x0, y0)) {
-      issue(t, 0);
-    } else {
-      gather_tile<R>(a, mode, x0, y0, buf[0], src_r, src_c);
-      __syncthreads();
-    }
-  }
+  if (t < ntiles) issue(t, 0);
   for (; t < ntiles; t += gridDim.x, b ^= 1) {
     const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
-    const int tn = t + gridDim.x;
-    int xn = 0, yn = 0;
-    bool next_gather = false;
-    if (tn < ntiles) {
-      const int tyn = tn / tiles_x;
-      yn = tyn * kTH;
-      xn = (tn - tyn * tiles_x) * kTW;
-      if (via_tma(xn, yn))
-        issue(tn, b ^ 1);
-      else
-        next_gather = true;
+    if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
+    // off-image cells of a border window: fetch them while the copy is in flight
+    const bool edge = border(x0, y0);
+    const bool fill = edge && a.bc != 0;
+    Strips<R> st(a, x0, y0);
+    float fv[kFillRegs];
+    if (fill) {
+#pragma unroll
+      for (int u = 0; u < kFillRegs; ++u) {
+        const int i = tid + u * kPT;
+        fv[u] = i < st.total ? st.load(a, mode, st.cell(i)) : 0.0f;
+      }
     }
     bool ok = true;
     if (pending & (1u << b)) {
@@ -280,21 +291,33 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
       drain();
       return;
     }
-    const bool flip = ADJ && sym && border(x0, y0);
+    float* S = buf0 + b * G::BUF;
+    if (fill) {
+#pragma unroll
+      for (int u = 0; u < kFillRegs; ++u) {
+        const int i = tid + u * kPT;
+        if (i < st.total) S[st.cell(i)] = fv[u];
+      }
+      for (int i = tid + kFillRegs * kPT; i < st.total; i += kPT) {  // large overhangs (tiny images)
+        const int c = st.cell(i);
+        S[c] = st.load(a, mode, c);
+      }
+      __syncthreads();
+    }
+    const bool flip = ADJ && sym && edge && !a.sym_taps;
     if (flip) {
       for (int i = tid; i < G::BH; i += kPT) flip_r[i] = odd_period(y0 - R + i, a.rows);
       for (int i = tid; i < G::VC; i += kPT) flip_c[i] = odd_period(x0 - R + i, a.cols);
       __syncthreads();
-      vertical<R, true>(buf[b], T, wr, flip_r);
+      vertical<R, true>(S, T, wr, flip_r);
       __syncthreads();
       horizontal<R, ADJ, true>(T, a, x0, y0, wc, flip_c, sq);
     } else {
-      vertical<R, false>(buf[b], T, wr, nullptr);
+      vertical<R, false>(S, T, wr, nullptr);
       __syncthreads();
       horizontal<R, ADJ, false>(T, a, x0, y0, wc, nullptr, sq);
     }
-    if (next_gather) gather_tile<R>(a, mode, xn, yn, buf[b ^ 1], src_r, src_c);
-    __syncthreads();  // T and the gathered buffer are reused next iteration
+    __syncthreads();  // T and this staging buffer are rewritten next
   }
   if (!ADJ && a.partials) {
     const double tot = block_sum<kPT>((double)sq, red);
@@ -350,6 +373,9 @@ int launch_tma_blur(const adjwt_blur_plan* p, bool adjoint, const float* in, con
   a.cols = p->cols;
   a.pitch = p->image_pitch;
   a.bc = p->bc;
+  a.sym_taps = 1;
+  for (int t = 0; t < p->kr; ++t) a.sym_taps &= p->taps_r[t] == p->taps_r[p->kr - 1 - t];
+  for (int t = 0; t < p->kc; ++t) a.sym_taps &= p->taps_c[t] == p->taps_c[p->kc - 1 - t];
   const int orr = R - p->kr / 2, oc = R - p->kc / 2;
   for (int t = 0; t < p->kr; ++t) a.pr[orr + t] = static_cast<float>(p->taps_r[t]);
   for (int t = 0; t < p->kc; ++t) a.pc[oc + t] = static_cast<float>(p->taps_c[t]);
