@@ -153,6 +153,11 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
 int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs, bool adjoint,
                        const ProxArgs& prox, float* llbuf0, float* llbuf1, cudaStream_t s, int* l1_slots_used);
 int wt_l1_partial_slots(const adjwt_wt_plan* p);
+// Interior rectangle of level j's output reconstructed by the persistent TMA
+// kernel (empty for small levels), and its launcher.
+void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1);
+int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], float* out, int out_pitch,
+                     cudaStream_t s);
 
 // Blur family.
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s);

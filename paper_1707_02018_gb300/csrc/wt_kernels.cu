@@ -279,7 +279,35 @@ struct SynArgs {
   const float* winv_r;
   const float* winv_c;
   float g[2][kMaxTaps];  // synthesis filters lo / hi
+  // tiles (kTile units) [in_r0, in_r1) x [in_c0, in_c1) are left to the TMA
+  // kernel; the grid then enumerates the other tiles of the tiles_r x tiles_c
+  // grid (rows above, rows below, then the columns beside the rectangle)
+  int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;
 };
+
+// Tile of this CTA: blockIdx directly, or the border enumeration above.
+__device__ __forceinline__ void syn_tile(const SynArgs& a, int* ty, int* tx) {
+  if (a.in_r1 <= a.in_r0) {
+    *ty = blockIdx.y;
+    *tx = blockIdx.x;
+    return;
+  }
+  const int i = blockIdx.x, TC = a.tiles_c;
+  const int ntop = a.in_r0 * TC, nbot = (a.tiles_r - a.in_r1) * TC;
+  if (i < ntop) {
+    *ty = i / TC;
+    *tx = i - *ty * TC;
+  } else if (i < ntop + nbot) {
+    const int j = i - ntop;
+    *ty = a.in_r1 + j / TC;
+    *tx = j - (*ty - a.in_r1) * TC;
+  } else {
+    const int j = i - ntop - nbot, side = a.in_c0 + (TC - a.in_c1);
+    const int rr = j / side, k = j - rr * side;
+    *ty = a.in_r0 + rr;
+    *tx = k < a.in_c0 ? k : a.in_c1 + (k - a.in_c0);
+  }
+}
 
 // ---------------------------------------------------------------- synthesis
 // One CTA: kTile x kTile output pixels.  Along an axis the outputs x of the
@@ -335,7 +363,9 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   static_assert(kTile * G::YP <= 2 * G::XM * G::KP, "Y must fit in H");
 
   const int tid = threadIdx.x;
-  const int t0r = blockIdx.y * kTile, t0c = blockIdx.x * kTile;
+  int tile_y, tile_x;
+  syn_tile(a, &tile_y, &tile_x);
+  const int t0r = tile_y * kTile, t0c = tile_x * kTile;
   const bool sym = a.mode == 1;
   float g0[L], g1[L];
 #pragma unroll
@@ -440,13 +470,23 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
     return;
   }
 
-  // coefficient tiles of the four bands (periodic wrap for PER, zeros outside otherwise)
-  const int nkk = nk[0] * nk[1];
-  staged_copy<4 * G::KM * G::KM>(
-      4 * nkk,
+  // weights 1/c of this tile's output rows and columns (fold E^dagger)
+  __shared__ float s_wr[kTile], s_wc[kTile];
+  if (tid < 2 * kTile) {
+    const int ax = tid / kTile, u = tid - ax * kTile;
+    const float* winv = ax ? a.winv_c : a.winv_r;
+    const int t = (ax ? t0c : t0r) + u, N = ax ? a.Nc : a.Nr;
+    (ax ? s_wc : s_wr)[u] = (winv && t < N) ? __ldg(winv + t) : 1.0f;
+  }
+  // coefficient tiles of the four bands (periodic wrap for PER, zeros
+  // outside otherwise); compile-time strides keep the index arithmetic cheap
+  constexpr int KK = G::KM * G::KM;
+  staged_copy<4 * KK>(
+      4 * KK,
       [&](int i) {
-        const int b = i / nkk, rem = i - b * nkk;
-        const int kk = rem / nk[1], ll = rem - kk * nk[1];
+        const int b = i / KK, rem = i - b * KK;
+        const int kk = rem / G::KM, ll = rem - kk * G::KM;
+        if (kk >= nk[0] || ll >= nk[1]) return 0.0f;
         int k = ka[0] + kk, l = ka[1] + ll;
         if (a.mode == 3) {
           k = pos_mod(k, a.nr);
@@ -457,17 +497,18 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
         return __ldg(a.band[b] + (size_t)k * a.band_pitch + l);
       },
       [&](int i, float v) {
-        const int b = i / nkk, rem = i - b * nkk;
-        const int kk = rem / nk[1];
-        C[b][kk][rem - kk * nk[1]] = v;
+        const int b = i / KK, rem = i - b * KK;
+        const int kk = rem / G::KM;
+        C[b][kk][rem - kk * G::KM] = v;
       });
   __syncthreads();
 
   // column pass: H[hb][x][l] over the virtual rows, both vertical bands summed
-  for (int item = tid; item < 2 * nk[1] * nblk[0]; item += kThreads) {
-    const int blk = item / (2 * nk[1]);
-    const int rem = item - blk * 2 * nk[1];
-    const int hb = rem / nk[1], ll = rem - hb * nk[1];
+  for (int item = tid; item < 2 * G::KM * nblk[0]; item += kThreads) {
+    const int blk = item / (2 * G::KM);
+    const int rem = item - blk * 2 * G::KM;
+    const int hb = rem / G::KM, ll = rem - hb * G::KM;
+    if (ll >= nk[1]) continue;
     float c0[G::NC], c1[G::NC], out[2 * kSP];
 #pragma unroll
     for (int j = 0; j < G::NC; ++j) {
@@ -488,10 +529,11 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   __syncthreads();
 
   // fold rows (E^dagger along the vertical axis)
-  for (int i = tid; i < 2 * kTile * nk[1]; i += kThreads) {
-    const int hb = i / (kTile * nk[1]);
-    const int rem = i - hb * kTile * nk[1];
-    const int tt = rem / nk[1], ll = rem - tt * nk[1];
+  for (int i = tid; i < 2 * kTile * G::KM; i += kThreads) {
+    const int hb = i / (kTile * G::KM);
+    const int rem = i - hb * kTile * G::KM;
+    const int tt = rem / G::KM, ll = rem - tt * G::KM;
+    if (ll >= nk[1]) continue;
     const int t = t0r + tt;
     float v = 0.0f;
     if (t < a.Nr) {
@@ -500,7 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
         if (t < Lp) v += H[hb][-1 - t - xa[0]][ll];
         if (t >= a.Nr - Lp) v += H[hb][2 * a.Nr - 1 - t - xa[0]][ll];
       }
-      if (a.winv_r) v *= __ldg(a.winv_r + t);
+      v *= s_wr[tt];
     }
     Gf[hb][tt][ll] = v;
   }
@@ -545,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
           if (tc < Lp) s += Y[tt][-1 - tc - xa[1]];
           if (tc >= a.Nc - Lp) s += Y[tt][2 * a.Nc - 1 - tc - xa[1]];
         }
-        if (a.winv_c) s *= __ldg(a.winv_c + tc);
+        s *= s_wc[c4 + u];
       }
       v[u] = s;
     }
@@ -750,15 +792,32 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
       a.g[0][t] = static_cast<float>(fb.rec_lo[t]);
       a.g[1][t] = static_cast<float>(fb.rec_hi[t]);
     }
-    int rc = dispatch_L(fb.L, [&](auto Lc) {
+    int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
       constexpr int LL = decltype(Lc)::value;
       if (L.generic_synth) {
         const int64_t count = (int64_t)a.Nr * a.Nc;
         const unsigned nb = (unsigned)((count + kThreads - 1) / kThreads);
         ADJWT_TRACED("wt_synth_gather", j, s, pdl_launch(k_synthesis_gather<LL>, nb, kThreads, 0, s, a, 0, count));
       } else {
-        dim3 grid((a.Nc + kTile - 1) / kTile, (a.Nr + kTile - 1) / kTile);
-        ADJWT_TRACED("wt_synth", j, s, pdl_launch(k_synthesis<LL>, grid, kThreads, 0, s, a));
+        a.tiles_c = (a.Nc + kTile - 1) / kTile;
+        a.tiles_r = (a.Nr + kTile - 1) / kTile;
+        int r0, r1, c0, c1;
+        synth_tma_rect(p, j, &r0, &r1, &c0, &c1);
+        dim3 grid(a.tiles_c, a.tiles_r);
+        if (r1 > r0) {
+          a.in_r0 = r0 / kTile;
+          a.in_r1 = r1 / kTile;
+          a.in_c0 = c0 / kTile;
+          a.in_c1 = c1 / kTile;
+          grid = dim3(a.tiles_r * a.tiles_c - (a.in_r1 - a.in_r0) * (a.in_c1 - a.in_c0), 1);
+        }
+        if (grid.x > 0)
+          ADJWT_TRACED("wt_synth", j, s, pdl_launch(k_synthesis<LL>, grid, kThreads, 0, s, a));
+        if (r1 > r0) {
+          ADJWT_CUDA_CHECK(cudaGetLastError());
+          int rc = launch_synth_tma(p, j, a.band, a.out, a.out_pitch, s);
+          if (rc) return rc;
+        }
         if (p->bc == kPpd) {
           const int64_t count = (int64_t)2 * Lp * a.Nc + (int64_t)(a.Nr - 2 * Lp) * 2 * Lp;
           const unsigned nb = (unsigned)((count + kThreads - 1) / kThreads);

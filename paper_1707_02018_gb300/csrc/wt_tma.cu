@@ -1,0 +1,364 @@
+// Persistent TMA-staged reconstruction W = E^dagger S for the full tiles of a
+// level that need no fold and no weight: every full tile under the zero and
+// circular extensions (band cells outside the band are zero, or wrapped by
+// the threads after the copy), the interior tiles under the symmetric and
+// redundant periodic ones.  The tiled kernel of wt_kernels.cu takes the
+// remaining tiles of the level.
+//
+// Output tiles are kTH x kTW pixels of LL_{j-1}.  Along an axis, the outputs
+// of a tile starting at an even t0 come in pairs (t0 + 2p, t0 + 2p + 1) that
+// read the coefficients Kb + p - q (+ e when phi = 1), q < L/2, with filter
+// taps (e xor phi) + 2q, Kb = floor((t0 + off - 1)/2) (off = 2L' for the
+// extended modes, L' for PER); phi is the same for every tile of a level.
+// The four band tiles a tile needs (rows ka_r .. ka_r + BR, columns from ka_c
+// rounded down to 16 bytes) are copied by the TMA unit into one of two
+// staging buffers while the CTA reconstructs the previous tile:
+//   column pass: per horizontal band pair (LL,LH) / (HL,HH), a thread makes
+//                16 consecutive rows of one coefficient column from a
+//                register window (lanes on consecutive columns);
+//   row pass:    a thread makes 16 consecutive pixels of one row (lanes on
+//                rows, odd pitch) and stores them as float4.
+#include <algorithm>
+
+#include "adjwt_internal.h"
+#include "device_common.cuh"
+#include "tma.cuh"
+
+namespace adjwt {
+namespace {
+
+constexpr int kTH = 32;    // output rows per tile
+constexpr int kTW = 128;   // output columns per tile
+constexpr int kP = 8;      // output pairs per thread and pass
+constexpr int kNT = 288;   // 9 warps: column-pass items; 8 of them in the row pass
+constexpr int kWrapCols = 16;  // PER: the box of a full tile overhangs the band end by at most
+constexpr int kWrapRows = 8;   // this many columns / rows (checked on the host)
+
+__host__ __device__ constexpr int up4(int v) { return (v + 3) / 4 * 4; }
+__host__ __device__ constexpr int up32(int v) { return (v + 31) / 32 * 32; }
+
+template <int L>
+struct SG {
+  static constexpr int NC = kP + L / 2;             // coefficient window per thread
+  static constexpr int BR = kTH / 2 + L / 2 + 1;    // staged band rows (>= every window row)
+  static constexpr int BC = up4(3 + kTW / 2 + L / 2 + 1);  // staged band columns (16-byte start slack)
+  static constexpr int BOX = BR * BC;                // floats of one band box
+  static constexpr int BAND = up32(BOX);             // band stride in a buffer (128-byte aligned)
+  static constexpr int BUF = 4 * BAND;               // floats per staging buffer (4 bands)
+  static constexpr int NKC = kTW / 2 + L / 2;       // coefficient columns of the column pass (max)
+  static constexpr int GP = (NKC + 1) | 1;          // odd pitch of the column-pass output
+  static constexpr size_t smem_bytes() { return 128 + (size_t)(2 * BUF + 2 * kTH * GP) * 4; }
+};
+
+struct SynTmaArgs {
+  float* out;
+  int out_pitch;
+  int phi_r, phi_c;       // pair phase per axis
+  int ka_r0, ka_c0;       // first coefficient of tile 0 minus t0/2, per axis
+  int d_c;                // ka_c minus its 16-byte-aligned start
+  int nk_c;               // coefficient columns used by a tile
+  int ty0, tx0, ntx, ntiles;  // tile rectangle (tile units)
+  int wrap;               // PER: overhanging band cells wrap around
+  int nr, nc, band_pitch; // band extents (for the wrap fill)
+  const float* band[4];
+  int* status;
+  float g[2][kMaxTaps];   // synthesis filters lo / hi
+};
+
+// 2 kP outputs from two coefficient windows (pairs p: outputs 2p, 2p+1)
+template <int L, int PHI>
+__device__ __forceinline__ void pairs(const float (&c0)[SG<L>::NC], const float (&c1)[SG<L>::NC],
+                                      const SynTmaArgs& a, float (&out)[2 * kP]) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < L / 2; ++q) {
+        const int j = p - q + L / 2 - 1 + (PHI ? e : 0);
+        const int m = (PHI ? 1 - e : e) + 2 * q;
+        acc = fmaf(c0[j], a.g[0][m], acc);
+        acc = fmaf(c1[j], a.g[1][m], acc);
+      }
+      out[2 * p + e] = acc;
+    }
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CUtensorMap m0,
+                                                      const __grid_constant__ CUtensorMap m1,
+                                                      const __grid_constant__ CUtensorMap m2,
+                                                      const __grid_constant__ CUtensorMap m3, const SynTmaArgs a) {
+  pdl_entry();
+  using G = SG<L>;
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t bar[2];
+  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
+  float* Gf = buf0 + 2 * G::BUF;  // [2][kTH][GP]
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t phase = 0, pending = 0;
+  auto tile_origin = [&](int t, int& t0r, int& t0c) {
+    const int ty = t / a.ntx;
+    t0r = (a.ty0 + ty) * kTH;
+    t0c = (a.tx0 + t - ty * a.ntx) * kTW;
+  };
+  auto issue = [&](int t, int b) {
+    int t0r, t0c;
+    tile_origin(t, t0r, t0c);
+    if (tid == 0) {
+      const int y = t0r / 2 + a.ka_r0, x = t0c / 2 + a.ka_c0 - a.d_c;
+      float* dst = buf0 + b * G::BUF;
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[b], 4 * G::BOX * 4);
+      tma_load_2d(dst, &m0, &bar[b], x, y);
+      tma_load_2d(dst + G::BAND, &m1, &bar[b], x, y);
+      tma_load_2d(dst + 2 * G::BAND, &m2, &bar[b], x, y);
+      tma_load_2d(dst + 3 * G::BAND, &m3, &bar[b], x, y);
+    }
+    pending |= 1u << b;
+  };
+
+  int t = blockIdx.x, b = 0;
+  if (t < a.ntiles) issue(t, 0);
+  for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
+    int t0r, t0c;
+    tile_origin(t, t0r, t0c);
+    if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
+    // PER: band cells of the box past the band end (zero-filled by the copy)
+    // take their circularly wrapped values.  For full tiles the overhang is at
+    // most kWrapCols columns and kWrapRows rows (one wrap); the cells are
+    // fetched into registers while the copy is in flight.
+    constexpr int RS = G::BR * kWrapCols, BS = kWrapRows * G::BC;
+    constexpr int NRS = (4 * RS + kNT - 1) / kNT, NBS = (4 * BS + kNT - 1) / kNT;
+    const int wy = t0r / 2 + a.ka_r0, wx = t0c / 2 + a.ka_c0 - a.d_c;
+    const int rhi = min(max(a.nr - wy, 0), G::BR), chi = min(max(a.nc - wx, 0), G::BC);
+    const int side = G::BC - chi, below = G::BR - rhi;
+    const bool wrap = a.wrap && (side > 0 || below > 0);
+    float rv[NRS], bv[NBS];
+    if (wrap) {
+#pragma unroll
+      for (int u = 0; u < NRS; ++u) {  // right strip: rows [0, rhi), columns [chi, BC)
+        const int i = tid + u * kNT, bb = i / RS, rem = i - bb * RS, rr = rem / kWrapCols, k = rem - rr * kWrapCols;
+        rv[u] = 0.0f;
+        if (i < 4 * RS && rr < rhi && k < side) {
+          const float* src = bb == 0 ? a.band[0] : (bb == 1 ? a.band[1] : (bb == 2 ? a.band[2] : a.band[3]));
+          rv[u] = __ldg(src + (size_t)(wy + rr) * a.band_pitch + k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NBS; ++u) {  // bottom strip: rows [rhi, BR), all columns
+        const int i = tid + u * kNT, bb = i / BS, rem = i - bb * BS, r2 = rem / G::BC, cc = rem - r2 * G::BC;
+        bv[u] = 0.0f;
+        if (i < 4 * BS && r2 < below) {
+          const float* src = bb == 0 ? a.band[0] : (bb == 1 ? a.band[1] : (bb == 2 ? a.band[2] : a.band[3]));
+          const int col = wx + cc >= a.nc ? wx + cc - a.nc : wx + cc;
+          bv[u] = __ldg(src + (size_t)r2 * a.band_pitch + col);
+        }
+      }
+    }
+    bool ok = mbar_wait(&bar[b], (phase >> b) & 1);
+    if (ok) {
+      phase ^= 1u << b;
+      pending &= ~(1u << b);
+    }
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
+      for (int bb = 0; bb < 2; ++bb)
+        if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
+      return;
+    }
+    float* S = buf0 + b * G::BUF;
+    if (wrap) {
+#pragma unroll
+      for (int u = 0; u < NRS; ++u) {
+        const int i = tid + u * kNT, bb = i / RS, rem = i - bb * RS, rr = rem / kWrapCols, k = rem - rr * kWrapCols;
+        if (i < 4 * RS && rr < rhi && k < side) S[bb * G::BAND + rr * G::BC + chi + k] = rv[u];
+      }
+#pragma unroll
+      for (int u = 0; u < NBS; ++u) {
+        const int i = tid + u * kNT, bb = i / BS, rem = i - bb * BS, r2 = rem / G::BC, cc = rem - r2 * G::BC;
+        if (i < 4 * BS && r2 < below) S[bb * G::BAND + (rhi + r2) * G::BC + cc] = bv[u];
+      }
+      __syncthreads();
+    }
+    // column pass: item = (hb, row block, coefficient column)
+    for (int item = tid; item < 2 * 2 * a.nk_c; item += kNT) {
+      const int hb = item >= 2 * a.nk_c ? 1 : 0;
+      const int rem = item - hb * 2 * a.nk_c;
+      const int rb = rem >= a.nk_c ? 1 : 0, ll = rem - rb * a.nk_c;
+      const float* s0 = S + (2 * hb) * G::BAND + (kP * rb) * G::BC + a.d_c + ll;
+      const float* s1 = s0 + G::BAND;
+      float c0[G::NC], c1[G::NC], out[2 * kP];
+#pragma unroll
+      for (int j = 0; j < G::NC; ++j) {
+        c0[j] = s0[j * G::BC];
+        c1[j] = s1[j * G::BC];
+      }
+      if (a.phi_r)
+        pairs<L, 1>(c0, c1, a, out);
+      else
+        pairs<L, 0>(c0, c1, a, out);
+      float* g = Gf + (hb * kTH + 2 * kP * rb) * G::GP + ll;
+#pragma unroll
+      for (int o = 0; o < 2 * kP; ++o) g[o * G::GP] = out[o];
+    }
+    __syncthreads();
+    // row pass: warp = 16-pixel block, lane = row
+    {
+      const int warp = tid >> 5, r = tid & 31;
+      if (warp < kTW / (2 * kP)) {
+        const float* g0 = Gf + r * G::GP + kP * warp;
+        const float* g1 = g0 + kTH * G::GP;
+        float c0[G::NC], c1[G::NC], out[2 * kP];
+#pragma unroll
+        for (int j = 0; j < G::NC; ++j) {
+          c0[j] = g0[j];
+          c1[j] = g1[j];
+        }
+        if (a.phi_c)
+          pairs<L, 1>(c0, c1, a, out);
+        else
+          pairs<L, 0>(c0, c1, a, out);
+        float4* dst = reinterpret_cast<float4*>(a.out + (size_t)(t0r + r) * a.out_pitch + t0c + 2 * kP * warp);
+#pragma unroll
+        for (int q = 0; q < kP / 2; ++q)
+          dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+      }
+    }
+    __syncthreads();  // Gf and this staging buffer are rewritten next
+  }
+}
+
+// Interior tile range [lo, hi) along one axis (tile size T): tiles whose
+// outputs need no mirrored copy, no weight, and whose coefficients lie inside
+// the band.
+void interior_range(int N, int n, int T, int mode, int L, bool weighted, int* lo, int* hi) {
+  if (mode == kZero || mode == kPer) {  // zero fill / wrap fill cover the band edges
+    *lo = 0;
+    *hi = N / T;
+    return;
+  }
+  const int Lp = L - 1, off = mode == kPer ? Lp : 2 * Lp;
+  const bool sym = mode == kSym;
+  const int guard = (weighted || sym) ? Lp : 0;
+  *lo = 0;
+  *hi = 0;
+  bool found = false;
+  for (int t = 0; (t + 1) * T <= N; ++t) {
+    const int t0 = t * T;
+    bool ok = t0 >= guard && t0 + T <= N - guard;
+    if (sym) ok = ok && t0 >= Lp && t0 + T <= N - Lp;
+    const int phi = (t0 + off - 1) & 1;
+    const int Kb = (t0 + off - 1) >> 1;  // t0 + off - 1 >= 0
+    const int ka = Kb - (L / 2 - 1), nk = T / 2 + L / 2 - 1 + phi;
+    ok = ok && ka >= 0 && ka + nk <= n;
+    if (ok && !found) {
+      *lo = t;
+      found = true;
+    }
+    if (ok) *hi = t + 1;
+    if (!ok && found) break;
+  }
+}
+
+template <int L>
+int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[4], cudaStream_t s, int level) {
+  using G = SG<L>;
+  const size_t smem = G::smem_bytes();
+  ADJWT_CUDA_CHECK(set_smem(k_synth_tma<L>, smem));
+  static int occ = 0;
+  if (!occ) {
+    int v = 0;
+    ADJWT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_synth_tma<L>, kNT, smem));
+    occ = std::max(v, 1);
+  }
+  const int grid = std::min(a.ntiles, sm_count() * occ);
+  ADJWT_TRACED("wt_synth_tma", level, s,
+               pdl_launch(k_synth_tma<L>, grid, kNT, smem, s, maps[0], maps[1], maps[2], maps[3], a));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+}  // namespace
+
+// Pixel rectangle [r0, r1) x [c0, c1) of level j's output reconstructed by the
+// TMA kernel (empty when the level is small); the tiled kernel skips it.
+void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1) {
+  *r0 = *r1 = *c0 = *c1 = 0;
+  const Level& L = p->lv[j - 1];
+  if (L.generic_synth || L.ax[0].N < 256 || L.ax[1].N < 512) return;
+  const bool weighted = L.ax[0].winv != nullptr || p->bc == kPpd;
+  int ylo, yhi, xlo, xhi;
+  interior_range(L.ax[0].N, L.ax[0].n, kTH, p->bc, p->fb.L, weighted, &ylo, &yhi);
+  interior_range(L.ax[1].N, L.ax[1].n, kTW, p->bc, p->fb.L, weighted, &xlo, &xhi);
+  if (yhi - ylo < 2 || xhi - xlo < 1) return;
+  *r0 = ylo * kTH;
+  *r1 = yhi * kTH;
+  *c0 = xlo * kTW;
+  *c1 = xhi * kTW;
+}
+
+int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], float* out, int out_pitch,
+                     cudaStream_t s) {
+  int r0, r1, c0, c1;
+  synth_tma_rect(p, j, &r0, &r1, &c0, &c1);
+  if (r1 <= r0 || c1 <= c0) return ADJWT_OK;
+  const Level& L = p->lv[j - 1];
+  const int Lf = p->fb.L, Lp = Lf - 1, off = p->bc == kPer ? Lp : 2 * Lp;
+  SynTmaArgs a{};
+  a.out = out;
+  a.out_pitch = out_pitch;
+  // tiles start at even t0, so phi and ka - t0/2 are the same for every tile
+  a.phi_r = a.phi_c = (off - 1) & 1;
+  a.ka_r0 = a.ka_c0 = (off - 1 - a.phi_r) / 2 - (Lf / 2 - 1);
+  a.d_c = a.ka_c0 & 3;  // t0c / 2 is a multiple of 4
+  a.nk_c = kTW / 2 + Lf / 2 - 1 + a.phi_c;
+  a.ty0 = r0 / kTH;
+  a.tx0 = c0 / kTW;
+  a.ntx = (c1 - c0) / kTW;
+  a.ntiles = a.ntx * ((r1 - r0) / kTH);
+  a.wrap = p->bc == kPer;
+  // box origin of the last full tile (its overhang past the band end is the largest)
+  const int last_r = (r1 - kTH) / 2 + a.ka_r0, last_c = (c1 - kTW) / 2 + a.ka_c0 - a.d_c;
+  a.nr = L.ax[0].n;
+  a.nc = L.ax[1].n;
+  a.band_pitch = L.band_pitch;
+  for (int b = 0; b < 4; ++b) a.band[b] = band[b];
+  a.status = device_status_ptr();
+  for (int t = 0; t < Lf; ++t) {
+    a.g[0][t] = static_cast<float>(p->fb.rec_lo[t]);
+    a.g[1][t] = static_cast<float>(p->fb.rec_hi[t]);
+  }
+  return [&]() -> int {
+    switch (Lf) {
+#define ADJWT_L(LL)                                                                                     \
+  case LL: {                                                                                            \
+    if (a.wrap && (last_r + SG<LL>::BR - L.ax[0].n > kWrapRows || last_c + SG<LL>::BC - L.ax[1].n > kWrapCols)) \
+      return fail(ADJWT_ERR_SHAPE, "TMA reconstruction: periodic overhang above the staged bound");     \
+    CUtensorMap maps[4];                                                                                \
+    for (int b = 0; b < 4; ++b) {                                                                       \
+      int rc = make_tmap_2d_f32(&maps[b], band[b], L.ax[0].n, L.ax[1].n, L.band_pitch, SG<LL>::BR,      \
+                                SG<LL>::BC);                                                            \
+      if (rc) return rc;                                                                                \
+    }                                                                                                   \
+    return launch_l<LL>(a, maps, s, j);                                                                 \
+  }
+      ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
+#undef ADJWT_L
+      default:
+        return fail(ADJWT_ERR_INVALID_ARG, "unsupported filter length");
+    }
+  }();
+}
+
+}  // namespace adjwt

@@ -53,6 +53,24 @@ def test_adjoint_analysis_synthesis_parity(adj, w, mode):
         assert_close(to_host_image(out, rows, cols), want, what=f"W {w} {mode} {rows}x{cols}")
 
 
+@pytest.mark.parametrize("w", WAVELETS)
+@pytest.mark.parametrize("mode", MODES)
+def test_large_levels_interior_and_border_kernels(adj, w, mode):
+    """Levels of at least 256 x 512 pixels reconstruct their interior tiles
+    with the persistent TMA kernel and the rest with the tiled kernel."""
+    for rows, cols, J in [(300, 1100, 2), (520, 648, 3)]:
+        plan = adj.WtPlan(rows, cols, J, w, mode)
+        x = random_vector(plan.logical_size, rows * 7 + cols)
+        out = adj.wt_synth(plan, plan.pack(x))
+        want = owt.wt_synth(x, rows, cols, J, w, mode)
+        assert_close(to_host_image(out, rows, cols), want, what=f"W {w} {mode} {rows}x{cols} J{J}")
+        img = random_vector((rows, cols), rows + 3 * cols)
+        got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
+        assert_close(plan.unpack(got).cpu().numpy(), owt.wt_adjoint(img, J, w, mode),
+                     what=f"W^* {w} {mode} {rows}x{cols} J{J}")
+    assert adj.device_status() == 0
+
+
 @pytest.mark.parametrize("mode", ["sym", "per", "zero"])
 def test_full_size_cdf97_five_levels(adj, mode):
     """The 2048 x 2048, 5-level CDF 9/7 operators of the bench, compared in full."""
