@@ -158,6 +158,13 @@ int wt_l1_partial_slots(const adjwt_wt_plan* p);
 void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1);
 int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], float* out, int out_pitch,
                      cudaStream_t s);
+// Coefficient rectangle of level j computed by the persistent TMA analysis
+// kernel (W^*, optionally with the prox, or W^dagger), and its launcher;
+// *ncta receives the number of l1 partial slots it wrote.
+void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1, int* c0, int* c1);
+int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
+                   float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
+                   double* l1, const float* flo, const float* fhi, const char* name, cudaStream_t s, int* ncta);
 
 // Blur family.
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s);

@@ -44,6 +44,7 @@ struct AnaArgs {
   float step, thresh, beta;
   double* l1;     // per-CTA partials (null = skip)
   float flo[kMaxTaps], fhi[kMaxTaps];
+  int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;  // tiles left to the TMA kernel (see border_tile)
 };
 
 
@@ -67,6 +68,34 @@ __device__ __forceinline__ void staged_copy(int total, Src src, Dst dst) {
   }
 }
 
+// Tile of this CTA: blockIdx directly when no rectangle is left to a TMA
+// kernel, else the i-th tile of the tiles_r x tiles_c grid outside the
+// rectangle [r0, r1) x [c0, c1) (rows above, rows below, then the columns
+// beside it).
+__device__ __forceinline__ void border_tile(int r0, int r1, int c0, int c1, int tiles_r, int tiles_c, int* ty,
+                                            int* tx) {
+  if (r1 <= r0) {
+    *ty = blockIdx.y;
+    *tx = blockIdx.x;
+    return;
+  }
+  const int i = blockIdx.x, TC = tiles_c;
+  const int ntop = r0 * TC, nbot = (tiles_r - r1) * TC;
+  if (i < ntop) {
+    *ty = i / TC;
+    *tx = i - *ty * TC;
+  } else if (i < ntop + nbot) {
+    const int j = i - ntop;
+    *ty = r1 + j / TC;
+    *tx = j - (*ty - r1) * TC;
+  } else {
+    const int j = i - ntop - nbot, side = c0 + (TC - c1);
+    const int rr = j / side, k = j - rr * side;
+    *ty = r0 + rr;
+    *tx = k < c0 ? k : c1 + (k - c0);
+  }
+}
+
 // ---------------------------------------------------------------- analysis
 // One CTA: kTile x kTile outputs of each of the four bands.  Column pass:
 // each thread filters kAP consecutive outputs of one column from 2*kAP + L - 2
@@ -87,7 +116,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
   __shared__ float s_w[2][E];
   __shared__ double red[kThreads / 32];
 
-  const int k0 = blockIdx.y * kTile, l0 = blockIdx.x * kTile;
+  int tile_y, tile_x;
+  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
+  const int k0 = tile_y * kTile, l0 = tile_x * kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // first extended coordinate of each axis and whether the tile reads only
@@ -285,30 +316,6 @@ struct SynArgs {
   int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;
 };
 
-// Tile of this CTA: blockIdx directly, or the border enumeration above.
-__device__ __forceinline__ void syn_tile(const SynArgs& a, int* ty, int* tx) {
-  if (a.in_r1 <= a.in_r0) {
-    *ty = blockIdx.y;
-    *tx = blockIdx.x;
-    return;
-  }
-  const int i = blockIdx.x, TC = a.tiles_c;
-  const int ntop = a.in_r0 * TC, nbot = (a.tiles_r - a.in_r1) * TC;
-  if (i < ntop) {
-    *ty = i / TC;
-    *tx = i - *ty * TC;
-  } else if (i < ntop + nbot) {
-    const int j = i - ntop;
-    *ty = a.in_r1 + j / TC;
-    *tx = j - (*ty - a.in_r1) * TC;
-  } else {
-    const int j = i - ntop - nbot, side = a.in_c0 + (TC - a.in_c1);
-    const int rr = j / side, k = j - rr * side;
-    *ty = a.in_r0 + rr;
-    *tx = k < a.in_c0 ? k : a.in_c1 + (k - a.in_c0);
-  }
-}
-
 // ---------------------------------------------------------------- synthesis
 // One CTA: kTile x kTile output pixels.  Along an axis the outputs x of the
 // tile's virtual range [xa, xb) come in pairs (xa + 2p, xa + 2p + 1); with
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
 
   const int tid = threadIdx.x;
   int tile_y, tile_x;
-  syn_tile(a, &tile_y, &tile_x);
+  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
   const int t0r = tile_y * kTile, t0c = tile_x * kTile;
   const bool sym = a.mode == 1;
   float g0[L], g1[L];
@@ -698,11 +705,13 @@ int analysis_grid(const Level& L, dim3* g) {
 
 }  // namespace
 
+// Per level: the tiled kernel's CTAs plus the TMA kernel's (at most one per
+// 16 x 64 coefficient tile, which is no more than the 32 x 32 tile count).
 int wt_l1_partial_slots(const adjwt_wt_plan* p) {
   int total = 0;
   for (const Level& L : p->lv) {
     dim3 g;
-    total += analysis_grid(L, &g);
+    total += 2 * analysis_grid(L, &g);
   }
   return total;
 }
@@ -753,16 +762,39 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       }
     }
     dim3 grid;
-    const int ncta = analysis_grid(L, &grid);
-    a.l1 = (prox.x && prox.l1_partials) ? prox.l1_partials + slot : nullptr;
+    int ncta = analysis_grid(L, &grid);
+    a.tiles_c = grid.x;
+    a.tiles_r = grid.y;
+    int r0, r1, c0, c1;  // coefficient rectangle of the TMA kernel
+    ana_tma_rect(p, j, adjoint, &r0, &r1, &c0, &c1);
+    if (r1 > r0) {
+      a.in_r0 = r0 / kTile;
+      a.in_r1 = r1 / kTile;
+      a.in_c0 = c0 / kTile;
+      a.in_c1 = c1 / kTile;
+      ncta -= (a.in_r1 - a.in_r0) * (a.in_c1 - a.in_c0);
+      grid = dim3(ncta, 1);
+    }
+    const bool want_l1 = prox.x && prox.l1_partials;
+    a.l1 = want_l1 ? prox.l1_partials + slot : nullptr;
     slot += ncta;
     const char* name = !adjoint ? "wt_analysis" : (prox.x ? "wt_adjoint_prox" : "wt_adjoint");
-    int rc = dispatch_L(fb.L, [&](auto Lc) {
-      ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kThreads, 0, s, a));
-      return ADJWT_OK;
-    });
-    if (rc) return rc;
-    ADJWT_CUDA_CHECK(cudaGetLastError());
+    if (ncta > 0) {
+      int rc = dispatch_L(fb.L, [&](auto Lc) {
+        ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kThreads, 0, s, a));
+        return ADJWT_OK;
+      });
+      if (rc) return rc;
+      ADJWT_CUDA_CHECK(cudaGetLastError());
+    }
+    if (r1 > r0) {
+      int used = 0;
+      const char* tname = !adjoint ? "wt_analysis_tma" : (prox.x ? "wt_adjoint_prox_tma" : "wt_adjoint_tma");
+      int rc = launch_ana_tma(p, j, adjoint, a.in, a.in_pitch, a.dst, a.px, a.py, a.out_pitch, a.step, a.thresh,
+                              a.beta, want_l1 ? prox.l1_partials + slot : nullptr, a.flo, a.fhi, tname, s, &used);
+      if (rc) return rc;
+      slot += used;
+    }
   }
   if (l1_slots_used) *l1_slots_used = slot;
   return ADJWT_OK;

@@ -31,6 +31,7 @@ constexpr int kTH = 32;    // output rows per tile
 constexpr int kTW = 128;   // output columns per tile
 constexpr int kP = 8;      // output pairs per thread and pass
 constexpr int kNT = 288;   // 9 warps: column-pass items; 8 of them in the row pass
+constexpr int kSplitMin = 1024;  // levels shared with the tiled kernel: both sides at least this long
 constexpr int kWrapCols = 16;  // PER: the box of a full tile overhangs the band end by at most
 constexpr int kWrapRows = 8;   // this many columns / rows (checked on the host)
 
@@ -302,6 +303,10 @@ void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, in
   interior_range(L.ax[0].N, L.ax[0].n, kTH, p->bc, p->fb.L, weighted, &ylo, &yhi);
   interior_range(L.ax[1].N, L.ax[1].n, kTW, p->bc, p->fb.L, weighted, &xlo, &xhi);
   if (yhi - ylo < 2 || xhi - xlo < 1) return;
+  // sharing a level with the tiled kernel pays only on large levels: the
+  // tiled kernel's border tiles cost about as much as the whole of a small one
+  const bool whole = ylo == 0 && xlo == 0 && yhi * kTH == L.ax[0].N && xhi * kTW == L.ax[1].N;
+  if (!whole && (L.ax[0].N < kSplitMin || L.ax[1].N < kSplitMin)) return;
   *r0 = ylo * kTH;
   *r1 = yhi * kTH;
   *c0 = xlo * kTW;
@@ -359,6 +364,323 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
         return fail(ADJWT_ERR_INVALID_ARG, "unsupported filter length");
     }
   }();
+}
+
+
+// ===================================================================== analysis
+// Persistent TMA-staged W^* (+ the FISTA prox) / W^dagger for the full tiles
+// of a level whose input window needs no weight, mirror or wrap (every full
+// tile under the zero extension: the TMA unit's zero fill is the extension).
+// A tile is kAR x kAC coefficients of each band; its input window is
+// (2 kAR + L - 2) x (2 kAC + L - 2) samples of the extended signal, staged by
+// the TMA unit into one of two buffers while the previous tile is filtered:
+//   column pass: a thread filters 8 coefficient rows of one window column
+//                with both analysis filters from a register window;
+//   row pass:    lanes on (vertical filter, coefficient row), a warp per
+//                8-coefficient block; both horizontal filters, then the
+//                plain store or the prox epilogue (loads first, float4).
+namespace {
+
+constexpr int kAR = 16;    // coefficient rows per tile
+constexpr int kAC = 64;    // coefficient columns per tile
+constexpr int kAP = 8;     // outputs per thread and pass
+
+template <int L>
+struct AG {
+  static constexpr int ER = 2 * kAR + L - 2;      // window rows
+  static constexpr int EC = 2 * kAC + L - 2;      // window columns
+  static constexpr int BC = up4(EC + 3);          // box columns (16-byte start slack)
+  static constexpr int BUF = up32(ER * BC);
+  static constexpr int NW = 2 * kAP + L - 2;      // register window per thread
+  static constexpr int VP = EC | 1;               // odd pitch of the column-pass output
+  static constexpr size_t smem_bytes() { return 128 + (size_t)(2 * BUF + 2 * kAR * VP) * 4; }
+};
+
+struct AnaTmaArgs {
+  int sh;                 // image index of extended sample e is e - sh
+  int d_c;                // window column start minus its 16-byte-aligned start
+  int ty0, tx0, ntx, ntiles;
+  int out_pitch;
+  float* dst[4];          // plain destinations (LL, LH, HL, HH)
+  float* px[4];           // prox state (non-null => prox band)
+  float* py[4];
+  float step, thresh, beta;
+  double* l1;             // per-CTA partials of |x| (null = skip)
+  int* status;
+  float flo[kMaxTaps], fhi[kMaxTaps];
+};
+
+template <int L, bool PROX>
+__global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
+    k_ana_tma(const __grid_constant__ CUtensorMap map, const AnaTmaArgs a) {
+  pdl_entry();
+  using G = AG<L>;
+  constexpr int Lp = L - 1;
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t bar[2];
+  __shared__ double red[kNT / 32];
+  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
+  float* V = buf0 + 2 * G::BUF;  // [2][kAR][VP]
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t phase = 0, pending = 0;
+  auto tile_origin = [&](int t, int& k0, int& l0) {
+    const int ty = t / a.ntx;
+    k0 = (a.ty0 + ty) * kAR;
+    l0 = (a.tx0 + t - ty * a.ntx) * kAC;
+  };
+  auto issue = [&](int t, int b) {
+    int k0, l0;
+    tile_origin(t, k0, l0);
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[b], G::ER * G::BC * 4);
+      tma_load_2d(buf0 + b * G::BUF, &map, &bar[b], 2 * l0 + 1 - Lp - a.sh - a.d_c, 2 * k0 + 1 - Lp - a.sh);
+    }
+    pending |= 1u << b;
+  };
+
+  float l1 = 0.0f;
+  int t = blockIdx.x, b = 0;
+  if (t < a.ntiles) issue(t, 0);
+  for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
+    int k0, l0;
+    tile_origin(t, k0, l0);
+    if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
+    // row-pass thread: (vertical filter f, coefficient row kk), 8-coefficient block = warp
+    const int warp = tid >> 5, lane = tid & 31, f = lane >> 4, kk = lane & 15;
+    const bool rower = warp < kAC / kAP;
+    const size_t row = (size_t)(k0 + kk) * a.out_pitch + l0 + kAP * warp;
+    auto pick = [&](float* const (&arr)[4], int bnd) -> float* {
+      return bnd == 0 ? arr[0] : (bnd == 1 ? arr[1] : (bnd == 2 ? arr[2] : arr[3]));
+    };
+    float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
+    float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
+    // prox state of this tile: requested before the copy completes
+    float yv[2][kAP], xv[2][kAP];
+    if (PROX && rower) {
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        if (!pxs[hb]) continue;
+#pragma unroll
+        for (int q = 0; q < kAP / 4; ++q) {
+          const float4 y4 = reinterpret_cast<const float4*>(pys[hb] + row)[q];
+          const float4 x4 = reinterpret_cast<const float4*>(pxs[hb] + row)[q];
+          yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
+          xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
+        }
+      }
+    }
+    bool ok = mbar_wait(&bar[b], (phase >> b) & 1);
+    if (ok) {
+      phase ^= 1u << b;
+      pending &= ~(1u << b);
+    }
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
+      for (int bb = 0; bb < 2; ++bb)
+        if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
+      return;
+    }
+    const float* S = buf0 + b * G::BUF + a.d_c;
+    // column pass: V[f][kk][ec] = sum_t f[t] T[2 kk + L' - t][ec]
+    for (int item = tid; item < 2 * G::EC; item += kNT) {
+      const int rb = item >= G::EC ? 1 : 0, ec = item - rb * G::EC;
+      const float* src = S + 2 * kAP * rb * G::BC + ec;
+      float w[G::NW];
+#pragma unroll
+      for (int j = 0; j < G::NW; ++j) w[j] = src[j * G::BC];
+      float* v0 = V + (kAP * rb) * G::VP + ec;
+      float* v1 = v0 + kAR * G::VP;
+#pragma unroll
+      for (int p = 0; p < kAP; ++p) {
+        float lo = 0.0f, hi = 0.0f;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+          lo = fmaf(a.flo[q], w[2 * p + Lp - q], lo);
+          hi = fmaf(a.fhi[q], w[2 * p + Lp - q], hi);
+        }
+        v0[p * G::VP] = lo;
+        v1[p * G::VP] = hi;
+      }
+    }
+    __syncthreads();
+    // row pass + store / prox epilogue
+    if (rower) {
+      const float* src = V + (f * kAR + kk) * G::VP + 2 * kAP * warp;
+      float w[G::NW];
+#pragma unroll
+      for (int j = 0; j < G::NW; ++j) w[j] = src[j];
+      float res[2][kAP];
+#pragma unroll
+      for (int p = 0; p < kAP; ++p) {
+        float lo = 0.0f, hi = 0.0f;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+          lo = fmaf(a.flo[q], w[2 * p + Lp - q], lo);
+          hi = fmaf(a.fhi[q], w[2 * p + Lp - q], hi);
+        }
+        res[0][p] = lo;
+        res[1][p] = hi;
+      }
+      float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        if (PROX && pxs[hb]) {
+          float xn[kAP], yn[kAP];
+#pragma unroll
+          for (int p = 0; p < kAP; ++p) {
+            const float v = yv[hb][p] - a.step * res[hb][p];
+            const float mag = fabsf(v) - a.thresh;
+            const float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
+            xn[p] = x;
+            yn[p] = fmaf(a.beta, x - xv[hb][p], x);
+            if (a.l1) l1 += fabsf(x);
+          }
+#pragma unroll
+          for (int q = 0; q < kAP / 4; ++q) {
+            reinterpret_cast<float4*>(pxs[hb] + row)[q] =
+                make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
+            reinterpret_cast<float4*>(pys[hb] + row)[q] =
+                make_float4(yn[4 * q], yn[4 * q + 1], yn[4 * q + 2], yn[4 * q + 3]);
+          }
+        } else if (dst[hb]) {
+#pragma unroll
+          for (int q = 0; q < kAP / 4; ++q)
+            reinterpret_cast<float4*>(dst[hb] + row)[q] =
+                make_float4(res[hb][4 * q], res[hb][4 * q + 1], res[hb][4 * q + 2], res[hb][4 * q + 3]);
+        }
+      }
+    }
+    __syncthreads();  // V and this staging buffer are rewritten next
+  }
+  if (a.l1) {
+    const double tot = block_sum<kNT>((double)l1, red);
+    if (tid == 0) a.l1[blockIdx.x] = tot;
+  }
+}
+
+// Full coefficient tiles [lo, hi) (tile size T) along one axis whose input
+// window stays inside [guard, N - guard) (any window under ZERO).
+void ana_range(int N, int n, int T, int mode, int L, bool weighted, int* lo, int* hi) {
+  const int Lp = L - 1, sh = mode == kPer ? 0 : Lp, E = 2 * T + L - 2;
+  const int guard = weighted ? Lp : 0;
+  *lo = *hi = 0;
+  bool found = false;
+  for (int t = 0; (t + 1) * T <= n; ++t) {
+    const int first = 2 * t * T + 1 - Lp - sh, last = first + E - 1;
+    const bool ok = mode == kZero || (first >= guard && last < N - guard);
+    if (ok && !found) {
+      *lo = t;
+      found = true;
+    }
+    if (ok) *hi = t + 1;
+    if (!ok && found) break;
+  }
+}
+
+template <int L, bool PROX>
+int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, const char* name, int level,
+                  int* ncta) {
+  using G = AG<L>;
+  const size_t smem = G::smem_bytes();
+  auto kern = k_ana_tma<L, PROX>;
+  ADJWT_CUDA_CHECK(set_smem(kern, smem));
+  static int occ = 0;
+  if (!occ) {
+    int v = 0;
+    ADJWT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kNT, smem));
+    occ = std::max(v, 1);
+  }
+  const int grid = std::min(a.ntiles, sm_count() * occ);
+  *ncta = grid;
+  ADJWT_TRACED(name, level, s, pdl_launch(kern, grid, kNT, smem, s, map, a));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+template <int L>
+int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, const char* name, int level,
+                 int* ncta) {
+  const bool prox = a.px[0] || a.px[1] || a.px[2] || a.px[3];
+  return prox ? launch_ana_lp<L, true>(a, map, s, name, level, ncta)
+              : launch_ana_lp<L, false>(a, map, s, name, level, ncta);
+}
+
+}  // namespace
+
+// Coefficient rectangle [r0, r1) x [c0, c1) of level j's bands computed by
+// the TMA kernel (rows aligned to 32, columns to 64; empty for small levels).
+void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1, int* c0, int* c1) {
+  *r0 = *r1 = *c0 = *c1 = 0;
+  const Level& L = p->lv[j - 1];
+  if (L.ax[0].N < 256 || L.ax[1].N < 512) return;
+  const bool weighted = adjoint && L.ax[0].winv != nullptr;
+  int ylo, yhi, xlo, xhi;
+  ana_range(L.ax[0].N, L.ax[0].n, kAR, p->bc, p->fb.L, weighted, &ylo, &yhi);
+  ana_range(L.ax[1].N, L.ax[1].n, kAC, p->bc, p->fb.L, weighted, &xlo, &xhi);
+  int rr0 = (ylo * kAR + 31) / 32 * 32, rr1 = yhi * kAR / 32 * 32;
+  if (rr1 - rr0 < 64 || xhi <= xlo) return;
+  const bool whole = rr0 == 0 && xlo == 0 && rr1 == L.ax[0].n && xhi * kAC == L.band_pitch;
+  if (!whole && (L.ax[0].N < kSplitMin || L.ax[1].N < kSplitMin)) return;
+  *r0 = rr0;
+  *r1 = rr1;
+  *c0 = xlo * kAC;
+  *c1 = xhi * kAC;
+}
+
+int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
+                   float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
+                   double* l1, const float* flo, const float* fhi, const char* name, cudaStream_t s, int* ncta) {
+  *ncta = 0;
+  int r0, r1, c0, c1;
+  ana_tma_rect(p, j, adjoint, &r0, &r1, &c0, &c1);
+  if (r1 <= r0 || c1 <= c0) return ADJWT_OK;
+  const Level& L = p->lv[j - 1];
+  const int Lf = p->fb.L, Lp = Lf - 1;
+  AnaTmaArgs a{};
+  a.sh = p->bc == kPer ? 0 : Lp;
+  const int first_c = 2 * c0 + 1 - Lp - a.sh;  // window start of column tile 0; tiles add 2 kAC (16-byte multiple)
+  a.d_c = ((first_c % 4) + 4) % 4;
+  a.ty0 = r0 / kAR;
+  a.tx0 = c0 / kAC;
+  a.ntx = (c1 - c0) / kAC;
+  a.ntiles = a.ntx * ((r1 - r0) / kAR);
+  a.out_pitch = out_pitch;
+  for (int b = 0; b < 4; ++b) {
+    a.dst[b] = dst[b];
+    a.px[b] = px[b];
+    a.py[b] = py[b];
+  }
+  a.step = step;
+  a.thresh = thresh;
+  a.beta = beta;
+  a.l1 = l1;
+  a.status = device_status_ptr();
+  for (int t = 0; t < Lf; ++t) {
+    a.flo[t] = flo[t];
+    a.fhi[t] = fhi[t];
+  }
+  switch (Lf) {
+#define ADJWT_L(LL)                                                                                        \
+  case LL: {                                                                                               \
+    CUtensorMap map;                                                                                       \
+    int rc = make_tmap_2d_f32(&map, in, L.ax[0].N, L.ax[1].N, in_pitch, AG<LL>::ER, AG<LL>::BC);           \
+    if (rc) return rc;                                                                                     \
+    return launch_ana_l<LL>(a, map, s, name, j, ncta);                                                     \
+  }
+    ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
+#undef ADJWT_L
+    default:
+      return fail(ADJWT_ERR_INVALID_ARG, "unsupported filter length");
+  }
 }
 
 }  // namespace adjwt

@@ -76,6 +76,26 @@ def test_fista_steps_other_boundaries(adj, mode):
     assert rel_err(wt.unpack(f.x).cpu().numpy(), x) <= 1e-4
 
 
+@pytest.mark.parametrize("mode", ["sym", "zero", "per", "ppd"])
+def test_fista_steps_large_levels(adj, mode):
+    """1024 x 1088, db4 J=2: level 1 runs the prox in the persistent TMA
+    analysis kernel (with the tiled kernel on the border tiles unless the TMA
+    tiles cover the level)."""
+    bc = "per" if mode in ("per", "ppd") else mode
+    prob, wt, bl, db = _setup(adj, 1024, 1088, 2, "db4", mode, 9, 1.5, 1e-3, 21, bc=bc)
+    L = 1.01  # a few steps at a fixed step size: parity does not need the estimated L_f
+    f = adj.Fista(wt, bl, db, 1e-3, L)
+    x, y, t = np.zeros(wt.logical_size), np.zeros(wt.logical_size), 1.0
+    for k in range(1, 5):
+        x, y, t = ofista.fista_step(prob, x, y, t, L)
+        Fg = f.step(objective=(k % 2 == 0))
+        if k % 2 == 0:
+            assert abs(Fg - prob.objective(x)) <= 1e-5 * prob.objective(x)
+    assert rel_err(wt.unpack(f.x).cpu().numpy(), x) <= 1e-4
+    assert rel_err(wt.unpack(f.y).cpu().numpy(), y) <= 1e-4
+    assert adj.device_status() == 0
+
+
 def test_identity_blur_closed_form(adj):
     """R = I, circular db2: one step with L_f = 1 lands on soft(W^T b, lambda)."""
     rows = cols = 32

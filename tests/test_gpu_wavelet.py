@@ -56,9 +56,10 @@ def test_adjoint_analysis_synthesis_parity(adj, w, mode):
 @pytest.mark.parametrize("w", WAVELETS)
 @pytest.mark.parametrize("mode", MODES)
 def test_large_levels_interior_and_border_kernels(adj, w, mode):
-    """Levels of at least 256 x 512 pixels reconstruct their interior tiles
-    with the persistent TMA kernel and the rest with the tiled kernel."""
-    for rows, cols, J in [(300, 1100, 2), (520, 648, 3)]:
+    """Persistent TMA kernels: on levels they cover whole (512 x 1024 under
+    PER / ZERO) and, on levels of at least 1024 x 1024, on the tiles they can
+    take with the tiled kernel on the rest."""
+    for rows, cols, J in [(1056, 1100, 2), (512, 1024, 3)]:
         plan = adj.WtPlan(rows, cols, J, w, mode)
         x = random_vector(plan.logical_size, rows * 7 + cols)
         out = adj.wt_synth(plan, plan.pack(x))
@@ -68,6 +69,9 @@ def test_large_levels_interior_and_border_kernels(adj, w, mode):
         got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
         assert_close(plan.unpack(got).cpu().numpy(), owt.wt_adjoint(img, J, w, mode),
                      what=f"W^* {w} {mode} {rows}x{cols} J{J}")
+        got = adj.wt_analysis(plan, image_dev(plan, img))
+        assert_close(plan.unpack(got).cpu().numpy(), owt.wt_pinv(img, J, w, mode),
+                     what=f"W^dagger {w} {mode} {rows}x{cols} J{J}")
     assert adj.device_status() == 0
 
 
