@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kTile = kSynthTile;
 constexpr int kThreads = 256;
+constexpr int kAnaThreads = 288;  // analysis: 9 warps take the 4 x (2 kTile + L - 2) column items in one round
 
 struct AnaArgs {
   const float* in;
@@ -52,18 +53,18 @@ struct AnaArgs {
 // staging of a tile keeps several loads in flight.
 // MAXN bounds `total` at compile time, so every load of a tile is issued
 // before the first shared-memory store: one memory round trip per tile.
-template <int MAXN, typename Src, typename Dst>
+template <int MAXN, int NT = kThreads, typename Src, typename Dst>
 __device__ __forceinline__ void staged_copy(int total, Src src, Dst dst) {
-  constexpr int U = (MAXN + kThreads - 1) / kThreads;
+  constexpr int U = (MAXN + NT - 1) / NT;
   float v[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int i = threadIdx.x + u * kThreads;
+    const int i = threadIdx.x + u * NT;
     v[u] = i < total ? src(i) : 0.0f;
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int i = threadIdx.x + u * kThreads;
+    const int i = threadIdx.x + u * NT;
     if (i < total) dst(i, v[u]);
   }
 }
@@ -104,7 +105,7 @@ __device__ __forceinline__ void border_tile(int r0, int r1, int c0, int c1, int 
 constexpr int kAP = 8;
 
 template <int L>
-__global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
+__global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
   pdl_entry();
   constexpr int Lp = L - 1;
   constexpr int E = 2 * kTile + L - 2;  // extended samples feeding one tile
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
   __shared__ float V[2][kTile][EP];
   __shared__ int s_src[2][E];
   __shared__ float s_w[2][E];
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kAnaThreads / 32];
 
   int tile_y, tile_x;
   border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
 
   if (fast) {
     const float* src = a.in + (size_t)(e0r - sh) * a.in_pitch + (e0c - sh);
-    staged_copy<E * E>(
+    staged_copy<E * E, kAnaThreads>(
         E * E,
         [&](int i) {
           const int er = i / E;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
           T[er][i - er * E] = v;
         });
   } else {
-    for (int i = tid; i < 2 * E; i += kThreads) {
+    for (int i = tid; i < 2 * E; i += kAnaThreads) {
       const int axis = i / E, el = i - axis * E;
       const int e = (axis == 0 ? e0r : e0c) + el;
       const int N = axis == 0 ? a.Nr : a.Nc;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
       s_w[axis][el] = (s >= 0 && winv) ? __ldg(winv + s) : 1.0f;
     }
     __syncthreads();
-    staged_copy<E * E>(
+    staged_copy<E * E, kAnaThreads>(
         E * E,
         [&](int i) {
           const int er = i / E, ec = i - er * E;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
   __syncthreads();
 
   // column pass: V[f][kk][ec] = sum_t f[t] T[2 kk + L' - t][ec]
-  for (int item = tid; item < E * (kTile / kAP); item += kThreads) {
+  for (int item = tid; item < E * (kTile / kAP); item += kAnaThreads) {
     const int kb = item / E, ec = item - kb * E;
     float w[NW];
 #pragma unroll
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
 
   // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
   float l1 = 0.0f;  // per-thread float32 partial of |x_k|, float64 across the block
-  {
+  if (warp < 2 * (kTile / kAP)) {  // the ninth warp has no row-pass item
     const int kk = lane, f = warp & 1, lb = warp >> 1;
     const int k = k0 + kk;
     float w[NW];
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_analysis(const AnaArgs a) {
     }
   }
   if (a.l1) {
-    const double tot = block_sum<kThreads>((double)l1, red);
+    const double tot = block_sum<kAnaThreads>((double)l1, red);
     if (tid == 0) a.l1[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 }
@@ -781,7 +782,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     const char* name = !adjoint ? "wt_analysis" : (prox.x ? "wt_adjoint_prox" : "wt_adjoint");
     if (ncta > 0) {
       int rc = dispatch_L(fb.L, [&](auto Lc) {
-        ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kThreads, 0, s, a));
+        ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kAnaThreads, 0, s, a));
         return ADJWT_OK;
       });
       if (rc) return rc;

@@ -31,7 +31,7 @@ constexpr int kTH = 32;    // output rows per tile
 constexpr int kTW = 128;   // output columns per tile
 constexpr int kP = 8;      // output pairs per thread and pass
 constexpr int kNT = 288;   // 9 warps: column-pass items; 8 of them in the row pass
-constexpr int kSplitMin = 1024;  // levels shared with the tiled kernel: both sides at least this long
+constexpr int kSplitMin = 1536;  // levels shared with the tiled kernel: both sides at least this long
 constexpr int kWrapCols = 16;  // PER: the box of a full tile overhangs the band end by at most
 constexpr int kWrapRows = 8;   // this many columns / rows (checked on the host)
 

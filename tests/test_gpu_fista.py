@@ -78,11 +78,11 @@ def test_fista_steps_other_boundaries(adj, mode):
 
 @pytest.mark.parametrize("mode", ["sym", "zero", "per", "ppd"])
 def test_fista_steps_large_levels(adj, mode):
-    """1024 x 1088, db4 J=2: level 1 runs the prox in the persistent TMA
+    """1600 x 1664, db4 J=2: level 1 runs the prox in the persistent TMA
     analysis kernel (with the tiled kernel on the border tiles unless the TMA
     tiles cover the level)."""
     bc = "per" if mode in ("per", "ppd") else mode
-    prob, wt, bl, db = _setup(adj, 1024, 1088, 2, "db4", mode, 9, 1.5, 1e-3, 21, bc=bc)
+    prob, wt, bl, db = _setup(adj, 1600, 1664, 2, "db4", mode, 9, 1.5, 1e-3, 21, bc=bc)
     L = 1.01  # a few steps at a fixed step size: parity does not need the estimated L_f
     f = adj.Fista(wt, bl, db, 1e-3, L)
     x, y, t = np.zeros(wt.logical_size), np.zeros(wt.logical_size), 1.0

@@ -58,8 +58,8 @@ def test_adjoint_analysis_synthesis_parity(adj, w, mode):
 def test_large_levels_interior_and_border_kernels(adj, w, mode):
     """Persistent TMA kernels: on levels they cover whole (512 x 1024 under
     PER / ZERO) and, on levels of at least 1024 x 1024, on the tiles they can
-    take with the tiled kernel on the rest."""
-    for rows, cols, J in [(1056, 1100, 2), (512, 1024, 3)]:
+    take with the tiled kernel on the rest (levels of at least 1536 x 1536)."""
+    for rows, cols, J in [(1600, 1664, 2), (512, 1024, 3)]:
         plan = adj.WtPlan(rows, cols, J, w, mode)
         x = random_vector(plan.logical_size, rows * 7 + cols)
         out = adj.wt_synth(plan, plan.pack(x))
