@@ -72,7 +72,7 @@ def channel_bytes():
             "flops": 2 * B * (n + k - 1) * k + 4 * B * n * k}
 
 
-# DRAM bytes per launch measured by ncu for the current kernels (profiles/)
+# DRAM bytes (read + write) of one launch of the bench workload, measured by ncu on the current kernels
 NCU_TRAFFIC = {"conv_gradient": 134410752 + 35026176}
 
 
@@ -336,8 +336,7 @@ def ours(args):
         achieved = cb["flops"] / (top_ms * 1e-3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": NCU_TRAFFIC.get(top),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                  "(profiles/k_conv_grad_256x65536x64.md)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this workload",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
     else:
         achieved = alg.get(top, 0.0) / (top_ms * 1e-3) / 1e9
