@@ -161,11 +161,15 @@ def build_workload(adj, torch, rank):
 
 class Lanes:
     """One CUDA stream per independent problem (the three boundary problems and
-    the channel gradient), forked from and joined back into the caller's stream."""
+    the channel gradient), forked from and joined back into the caller's stream.
+    The FISTA lanes get the high stream priority: their level kernels are short
+    and latency bound, so the block scheduler gives them SMs first and the
+    throughput-bound channel gradient (last lane) fills the rest."""
 
     def __init__(self, torch, n):
         self.torch = torch
-        self.streams = [torch.cuda.Stream() for _ in range(n)]
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        self.streams = [torch.cuda.Stream(priority=hi) for _ in range(n - 1)] + [torch.cuda.Stream(priority=lo)]
         self.events = [torch.cuda.Event() for _ in range(n + 1)]
 
     def fork(self):
