@@ -214,6 +214,19 @@ size_t adjwt_fista_workspace_size(const adjwt_fista_problem* prob);
 int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* ws, size_t ws_bytes,
                double* objective_out, adjwt_stream_t stream);
 
+/* The same iteration with the momentum t_k resident in the workspace (no
+ * counterpart in the paper: it makes an iteration a pure sequence of stream
+ * operations that can be captured in a CUDA graph and replayed, e.g. to run
+ * many independent problems concurrently).  x (x_{k-1} -> x_k) and y
+ * (y_k -> y_{k+1}) are device coefficient vectors; the workspace holds t_k,
+ * which adjwt_fista_device_reset sets to 1 (start of a solve) and every call
+ * advances.  If objective_dev (DEVICE double, 8-byte aligned) is non-NULL it
+ * receives F(x_k).  Nothing synchronises.  Errors as fista_step, plus ALIAS
+ * when the workspace overlaps x or y. */
+int fista_step_device(const adjwt_fista_problem* prob, float* x, float* y, void* ws, size_t ws_bytes,
+                      double* objective_dev, adjwt_stream_t stream);
+int adjwt_fista_device_reset(const adjwt_fista_problem* prob, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+
 /* F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1 into *objective_out (HOST);
  * synchronises the stream. */
 int adjwt_fista_objective(const adjwt_fista_problem* prob, const float* x, void* ws, size_t ws_bytes,

@@ -291,6 +291,23 @@ class Fista:
                                     C.byref(out) if objective else None, _stream(stream)))
         return out.value if objective else None
 
+    def reset_device(self, x0=None, stream=None):
+        """Start a solve whose momentum lives on the device: x = y = x0 (or 0), t = 1."""
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            self.x.zero_()
+            if x0 is not None:
+                self.x.copy_(x0)
+            self.y.copy_(self.x)
+        _lib.check(lib().adjwt_fista_device_reset(C.byref(self.problem), _ptr(self.ws), self.ws.numel(), _stream(st)))
+
+    def step_device(self, objective_out=None, stream=None):
+        """One iteration with no host state and no synchronisation (capturable
+        in a CUDA graph); objective_out: optional 1-element float64 device
+        tensor that receives F(x_k)."""
+        _lib.check(lib().fista_step_device(C.byref(self.problem), _ptr(self.x), _ptr(self.y), _ptr(self.ws),
+                                           self.ws.numel(), _ptr(objective_out), _stream(stream)))
+
     def objective(self, x=None, stream=None):
         out = C.c_double()
         x = self.x if x is None else x

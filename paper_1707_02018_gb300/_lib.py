@@ -52,6 +52,8 @@ PROTOTYPES = {
     "conv_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "adjwt_fista_workspace_size": (SZ, [C.POINTER(FistaProblem)]),
     "fista_step": (C.c_int, [C.POINTER(FistaProblem), C.POINTER(FistaState), VP, SZ, DP, VP]),
+    "fista_step_device": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, SZ, VP, VP]),
+    "adjwt_fista_device_reset": (C.c_int, [C.POINTER(FistaProblem), VP, SZ, VP]),
     "adjwt_fista_objective": (C.c_int, [C.POINTER(FistaProblem), VP, VP, SZ, DP, VP]),
     "adjwt_fista_lipschitz": (C.c_int, [C.POINTER(FistaProblem), VP, C.c_int, VP, SZ, DP, VP]),
     "adjwt_trace_enable": (C.c_int, [C.c_int]),

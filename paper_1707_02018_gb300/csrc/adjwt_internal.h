@@ -62,13 +62,23 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 }
 #endif
 
+// Whether (kernel, current device) already has at least `bytes` of dynamic
+// shared memory enabled; records it when `mark` is set.
+bool smem_attr_known(const void* kernel, size_t bytes, bool mark);
+
 // Opt a kernel into `bytes` of dynamic shared memory and the largest shared
-// carveout, so that several such CTAs can be resident on one SM.
+// carveout, so that several such CTAs can be resident on one SM.  Done once
+// per kernel and device, so that later launches (e.g. under stream capture)
+// make no attribute calls.
 template <typename Kernel>
 inline cudaError_t set_smem(Kernel kernel, size_t bytes) {
+  const void* key = reinterpret_cast<const void*>(kernel);
+  if (smem_attr_known(key, bytes, false)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) smem_attr_known(key, bytes, true);
+  return e;
 }
 
 // ---------------------------------------------------------------- device status, TMA descriptors
@@ -143,6 +153,7 @@ struct ProxArgs {
   float thresh;      // lambda/L_f
   float beta;        // (t_k - 1)/t_{k+1}
   double* l1_partials;  // per-CTA partial sums of |x_k| (null = skip)
+  const double* beta_dev;  // non-null: momentum factor read from device memory instead of beta
 };
 
 // W (wt_synth): coeffs -> image.  ws holds the LL ping-pong buffers.
@@ -164,7 +175,8 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1, int* c0, int* c1);
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
                    float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
-                   double* l1, const float* flo, const float* fhi, const char* name, cudaStream_t s, int* ncta);
+                   const double* beta_dev, double* l1, const float* flo, const float* fhi, const char* name,
+                   cudaStream_t s, int* ncta);
 
 // Blur family.
 int launch_blur(const adjwt_blur_plan* p, const float* in, float* out, bool adjoint, cudaStream_t s);

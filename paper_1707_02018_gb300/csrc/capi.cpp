@@ -28,6 +28,9 @@ size_t fista_workspace_bytes(const adjwt_fista_problem* pr);
 int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, double* objective_out,
                     cudaStream_t s);
 int fista_objective_impl(const adjwt_fista_problem* pr, const float* x, void* ws, double* out, cudaStream_t s);
+int fista_step_device_impl(const adjwt_fista_problem* pr, float* x, float* y, void* ws, double* objective_dev,
+                           cudaStream_t s);
+int fista_device_reset_impl(const adjwt_fista_problem* pr, void* ws, cudaStream_t s);
 int fista_lipschitz_impl(const adjwt_fista_problem* pr, float* v, int iters, void* ws, double* out,
                          cudaStream_t s);
 
@@ -296,6 +299,34 @@ extern "C" int conv_residual(int batch, int64_t n, int k, const float* h, const 
 extern "C" size_t adjwt_fista_workspace_size(const adjwt_fista_problem* pr) {
   if (!pr || !pr->wt || !pr->blur) return 0;
   return fista_workspace_bytes(pr);
+}
+
+extern "C" int fista_step_device(const adjwt_fista_problem* pr, float* x, float* y, void* ws, size_t ws_bytes,
+                                 double* objective_dev, adjwt_stream_t stream) {
+  int rc = check_problem(pr);
+  if (rc) return rc;
+  rc = check_ptr(x, "x");
+  if (!rc) rc = check_ptr(y, "y");
+  if (rc) return rc;
+  if (objective_dev && (reinterpret_cast<uintptr_t>(objective_dev) & 7u))
+    return fail(ADJWT_ERR_ALIGN, "fista_step_device: objective_dev is not 8-byte aligned");
+  const size_t cb = pr->wt->num_coeffs * 4;
+  if (overlap(x, cb, y, cb)) return fail(ADJWT_ERR_ALIAS, "fista_step_device: x and y overlap");
+  rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "fista_step_device");
+  if (rc) return rc;
+  const size_t wb = fista_workspace_bytes(pr);
+  if (overlap(ws, wb, x, cb) || overlap(ws, wb, y, cb))
+    return fail(ADJWT_ERR_ALIAS, "fista_step_device: workspace overlaps the state");
+  return fista_step_device_impl(pr, x, y, ws, objective_dev, stream);
+}
+
+extern "C" int adjwt_fista_device_reset(const adjwt_fista_problem* pr, void* ws, size_t ws_bytes,
+                                        adjwt_stream_t stream) {
+  int rc = check_problem(pr);
+  if (rc) return rc;
+  rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "adjwt_fista_device_reset");
+  if (rc) return rc;
+  return fista_device_reset_impl(pr, ws, stream);
 }
 
 extern "C" int fista_step(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, size_t ws_bytes,

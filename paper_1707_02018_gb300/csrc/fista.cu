@@ -48,6 +48,27 @@ __global__ void k_scale(float* v, int64_t count, const double* sq_norm) {
     v[i] *= s;
 }
 
+// Device-resident momentum: m[0] = t_k; one thread advances it and stores
+// m[1] = (t_k - 1)/t_{k+1} for the prox epilogues of the same iteration.
+__global__ void k_momentum(double* m) {
+  pdl_entry();
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double t = m[0];
+    // rounded like the host's 0.5 * (1 + sqrt(1 + 4 t t)): no fused multiply-add
+    const double t1 = 0.5 * (1.0 + sqrt(__dadd_rn(1.0, __dmul_rn(4.0 * t, t))));
+    m[1] = (t - 1.0) / t1;
+    m[0] = t1;
+  }
+}
+
+__global__ void k_momentum_reset(double* m) {
+  pdl_entry();
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    m[0] = 1.0;
+    m[1] = 0.0;
+  }
+}
+
 constexpr int kNormBlocks = 304;  // 2 x 152 SMs
 
 struct FistaWs {
@@ -59,6 +80,7 @@ struct FistaWs {
   double* part_a;
   double* part_b;
   double* scalars;  // [0] result, [1] scratch
+  double* momentum; // [0] t_k, [1] beta (device-resident momentum)
   size_t bytes;
 };
 
@@ -81,6 +103,7 @@ FistaWs layout_ws(const adjwt_fista_problem* pr, char* base) {
   L.part_a = reinterpret_cast<double*>(take(slots * sizeof(double)));
   L.part_b = reinterpret_cast<double*>(take(slots * sizeof(double)));
   L.scalars = reinterpret_cast<double*>(take(4 * sizeof(double)));
+  L.momentum = reinterpret_cast<double*>(take(2 * sizeof(double)));
   L.bytes = off;
   return L;
 }
@@ -92,9 +115,10 @@ int finish_scalar(double* dev, double* host, cudaStream_t s) {
   return ADJWT_OK;
 }
 
-// F(x) into ws.scalars[0] (device), using ws.u and the partial buffers.
+// F(x) into *out (device; ws.scalars by default), using ws.u and the partial buffers.
 int objective_async(const adjwt_fista_problem* pr, const float* x, const FistaWs& W, bool have_l1, int l1_slots,
-                    cudaStream_t s) {
+                    cudaStream_t s, double* out = nullptr) {
+  if (!out) out = W.scalars;
   int rc = launch_wt_synth(pr->wt, x, W.u, W.ll0, W.ll1, s);
   if (rc) return rc;
   int nb = 0;
@@ -106,7 +130,7 @@ int objective_async(const adjwt_fista_problem* pr, const float* x, const FistaWs
     l1_slots = kNormBlocks;
   }
   ADJWT_TRACED("sum_partials", 0, s,
-               pdl_launch(k_sum_partials, 1, kThreads, 0, s, W.part_a, l1_slots, pr->lambda, W.part_b, nb, 1.0, W.scalars));
+               pdl_launch(k_sum_partials, 1, kThreads, 0, s, W.part_a, l1_slots, pr->lambda, W.part_b, nb, 1.0, out));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
@@ -148,6 +172,40 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
     if (rc) return rc;
     return finish_scalar(W.scalars, objective_out, s);
   }
+  return ADJWT_OK;
+}
+
+// One iteration with the momentum t_k kept in the workspace: no host state and
+// no synchronisation, so a sequence of iterations can be captured in a CUDA
+// graph and replayed.  With objective_dev (device) non-null, F(x_k) is
+// written there.
+int fista_step_device_impl(const adjwt_fista_problem* pr, float* x, float* y, void* ws, double* objective_dev,
+                           cudaStream_t s) {
+  const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
+  ADJWT_TRACED("momentum", 0, s, pdl_launch(k_momentum, 1, 32, 0, s, W.momentum));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  int rc = launch_wt_synth(pr->wt, y, W.u, W.ll0, W.ll1, s);
+  if (rc) return rc;
+  rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr);
+  if (rc) return rc;
+  ProxArgs prox{};
+  prox.x = x;
+  prox.y = y;
+  prox.step = static_cast<float>(1.0 / pr->lipschitz);
+  prox.thresh = static_cast<float>(pr->lambda / pr->lipschitz);
+  prox.beta_dev = W.momentum + 1;
+  prox.l1_partials = objective_dev ? W.part_a : nullptr;
+  int l1_slots = 0;
+  rc = launch_wt_analysis(pr->wt, W.g, nullptr, true, prox, W.ll0, W.ll1, s, &l1_slots);
+  if (rc) return rc;
+  if (objective_dev) return objective_async(pr, x, W, true, l1_slots, s, objective_dev);
+  return ADJWT_OK;
+}
+
+int fista_device_reset_impl(const adjwt_fista_problem* pr, void* ws, cudaStream_t s) {
+  const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
+  ADJWT_TRACED("momentum", 0, s, pdl_launch(k_momentum_reset, 1, 32, 0, s, W.momentum));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <vector>
 
 #include "adjwt_internal.h"
 
@@ -33,6 +34,33 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 }  // namespace
+
+namespace {
+struct SmemAttr {
+  const void* kernel;
+  int device;
+  size_t bytes;
+};
+std::mutex g_attr_mu;
+std::vector<SmemAttr> g_attrs;
+}  // namespace
+
+bool smem_attr_known(const void* kernel, size_t bytes, bool mark) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  for (auto& a : g_attrs)
+    if (a.kernel == kernel && a.device == dev) {
+      if (a.bytes >= bytes) return true;
+      if (mark) {
+        a.bytes = bytes;
+        return true;
+      }
+      return false;
+    }
+  if (mark) g_attrs.push_back({kernel, dev, bytes});
+  return mark;
+}
 
 int* device_status_ptr() {
   int dev = 0;

@@ -43,6 +43,7 @@ struct AnaArgs {
   float* py[4];
   int out_pitch;
   float step, thresh, beta;
+  const double* beta_dev;  // non-null: beta from device memory
   double* l1;     // per-CTA partials (null = skip)
   float flo[kMaxTaps], fhi[kMaxTaps];
   int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;  // tiles left to the TMA kernel (see border_tile)
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
 
   // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
   float l1 = 0.0f;  // per-thread float32 partial of |x_k|, float64 across the block
+  const float beta = a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
   if (warp < 2 * (kTile / kAP)) {  // the ninth warp has no row-pass item
     const int kk = lane, f = warp & 1, lb = warp >> 1;
     const int k = k0 + kk;
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
             const float v = yv[hb][p] - a.step * res[hb][p];
             const float mag = fabsf(v) - a.thresh;
             float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
-            float y = fmaf(a.beta, x - xv[hb][p], x);
+            float y = fmaf(beta, x - xv[hb][p], x);
             if (!full && lbase + p >= a.nc) x = y = 0.0f;
             xn[p] = x;
             yn[p] = y;
@@ -753,6 +755,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     a.step = prox.step;
     a.thresh = prox.thresh;
     a.beta = prox.beta;
+    a.beta_dev = prox.beta_dev;
     for (int t = 0; t < fb.L; ++t) {
       if (adjoint) {  // dual analysis filters: synthesis filters reversed (Eq. 3, Eq. 4)
         a.flo[t] = static_cast<float>(fb.rec_lo[fb.L - 1 - t]);
@@ -792,7 +795,8 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       int used = 0;
       const char* tname = !adjoint ? "wt_analysis_tma" : (prox.x ? "wt_adjoint_prox_tma" : "wt_adjoint_tma");
       int rc = launch_ana_tma(p, j, adjoint, a.in, a.in_pitch, a.dst, a.px, a.py, a.out_pitch, a.step, a.thresh,
-                              a.beta, want_l1 ? prox.l1_partials + slot : nullptr, a.flo, a.fhi, tname, s, &used);
+                              a.beta, a.beta_dev, want_l1 ? prox.l1_partials + slot : nullptr, a.flo, a.fhi, tname,
+                              s, &used);
       if (rc) return rc;
       slot += used;
     }

@@ -405,6 +405,7 @@ struct AnaTmaArgs {
   float* px[4];           // prox state (non-null => prox band)
   float* py[4];
   float step, thresh, beta;
+  const double* beta_dev; // non-null: beta from device memory
   double* l1;             // per-CTA partials of |x| (null = skip)
   int* status;
   float flo[kMaxTaps], fhi[kMaxTaps];
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   };
 
   float l1 = 0.0f;
+  const float beta = PROX && a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
   int t = blockIdx.x, b = 0;
   if (t < a.ntiles) issue(t, 0);
   for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
             const float mag = fabsf(v) - a.thresh;
             const float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
             xn[p] = x;
-            yn[p] = fmaf(a.beta, x - xv[hb][p], x);
+            yn[p] = fmaf(beta, x - xv[hb][p], x);
             if (a.l1) l1 += fabsf(x);
           }
 #pragma unroll
@@ -638,7 +640,8 @@ void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1,
 
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
                    float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
-                   double* l1, const float* flo, const float* fhi, const char* name, cudaStream_t s, int* ncta) {
+                   const double* beta_dev, double* l1, const float* flo, const float* fhi, const char* name,
+                   cudaStream_t s, int* ncta) {
   *ncta = 0;
   int r0, r1, c0, c1;
   ana_tma_rect(p, j, adjoint, &r0, &r1, &c0, &c1);
@@ -662,6 +665,7 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
   a.step = step;
   a.thresh = thresh;
   a.beta = beta;
+  a.beta_dev = beta_dev;
   a.l1 = l1;
   a.status = device_status_ptr();
   for (int t = 0; t < Lf; ++t) {
