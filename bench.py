@@ -245,6 +245,20 @@ def fista_time_to_tol(adj, torch, pr, tol=1e-4, ref_iters=3000, check_every=10, 
             "F_star_iterations": ref_iters, "check_every": check_every, "boundary": pr["bc"]}
 
 
+def adjoint_vs_pinv(adj, torch, pr, iters=300):
+    """F(x_k) after `iters` FISTA iterations with the exact adjoint W^* and with
+    W^dagger in its place (the comparison the paper makes), same problem and L_f."""
+    f = pr["fista"]
+    g = adj.Fista(pr["wt"], pr["bl"], pr["b"], LAM, f.problem.lipschitz, gradient="pinv")
+    f.reset()
+    for _ in range(iters):
+        f.step()
+        g.step()
+    fa, fp = f.objective(), g.objective()
+    f.reset()
+    return {"iterations": iters, "boundary": pr["bc"], "F_adjoint": fa, "F_pinv": fp, "ratio_pinv_over_adjoint": fp / fa}
+
+
 # Batched solves: independent deblurring problems of uneven sizes, depths,
 # wavelets and PSF widths (symmetric boundaries), all to the same relative
 # objective tolerance.
@@ -485,6 +499,7 @@ def ours(args):
     if rank == 0 and not args.no_solve:
         extra["fista_sec_to_1e-4"] = fista_time_to_tol(adj, torch, probs[1])
         extra["fista_batched_vs_plain_to_1e-4"] = batched_vs_plain(adj, torch)
+        extra["fista_adjoint_vs_pinv"] = adjoint_vs_pinv(adj, torch, probs[1])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

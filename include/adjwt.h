@@ -195,7 +195,12 @@ typedef struct {
   const float* b;   /* device image (observed, blurred) */
   double lambda;    /* > 0 */
   double lipschitz; /* L_f > 0, e.g. from adjwt_fista_lipschitz */
+  int gradient;     /* ADJWT_GRAD_ADJOINT (0): grad f = W^* R^*(R W y - b);
+                       ADJWT_GRAD_PINV (1): W^dagger in place of W^*, the
+                       substitute the paper compares against (Sec. I-B, I-C) */
 } adjwt_fista_problem;
+
+enum { ADJWT_GRAD_ADJOINT = 0, ADJWT_GRAD_PINV = 1 };
 
 typedef struct {
   float* x;  /* device coeffs: x_{k-1} on entry, x_k on return       */

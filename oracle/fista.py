@@ -13,6 +13,11 @@ prints none of its constants, so these are readings):
 lambda applies to every coefficient, the coarse LL band included.
 L_f = 1.01 * (power-iteration estimate of ||W^* R^* R W||), the estimate being
 ||A^* A v|| after `iters` normalised iterations from a caller-supplied start.
+
+Problem(gradient="pinv") is the variant the paper argues against (Sec. I-A,
+the W^dagger vs W^* discussion of Sec. I-B, I-C): the analysis operator
+W^dagger stands in for W^* in grad f, so the iteration no longer follows the
+gradient of F unless W^dagger = W^* (orthogonal filters, periodic boundary).
 """
 
 from dataclasses import dataclass
@@ -35,12 +40,20 @@ class Problem:
     blur_bc: str       # zero / sym / per
     b: np.ndarray
     lam: float
+    gradient: str = "adjoint"  # "adjoint": W^*;  "pinv": W^dagger in its place
 
     def A(self, x):
         u = _wt.wt_synth(x, self.rows, self.cols, self.levels, self.wavelet, self.mode)
         return _blur.blur(u, self.p_rows, self.p_cols, self.blur_bc)
 
     def At(self, v):
+        """The operator used in grad f: A^* = W^* R^*, or W^dagger R^* for gradient="pinv"."""
+        g = _blur.blur_adjoint(v, self.p_rows, self.p_cols, self.blur_bc)
+        if self.gradient == "pinv":
+            return _wt.wt_pinv(g, self.levels, self.wavelet, self.mode)
+        return _wt.wt_adjoint(g, self.levels, self.wavelet, self.mode)
+
+    def At_exact(self, v):
         g = _blur.blur_adjoint(v, self.p_rows, self.p_cols, self.blur_bc)
         return _wt.wt_adjoint(g, self.levels, self.wavelet, self.mode)
 
@@ -68,7 +81,7 @@ def power_iteration(prob: Problem, v0, iters=50):
     v = v / np.linalg.norm(v)
     lam = 0.0
     for _ in range(iters):
-        w = prob.At(prob.A(v))
+        w = prob.At_exact(prob.A(v))
         lam = float(np.linalg.norm(w))
         v = w / lam
     return lam

@@ -266,9 +266,13 @@ def conv_residual(h, s, x=None, r=None, stream=None):
 class Fista:
     """FISTA state and problem for min 1/2||R W x - b||^2 + lam ||x||_1 on one GPU."""
 
-    def __init__(self, wt_plan, blur_plan, b, lam, lipschitz=1.0):
+    GRADIENT = {"adjoint": 0, "pinv": 1}
+
+    def __init__(self, wt_plan, blur_plan, b, lam, lipschitz=1.0, gradient="adjoint"):
+        """gradient="pinv" puts W^dagger where W^* belongs (the comparison the paper makes)."""
         self.wt, self.blur, self.b = wt_plan, blur_plan, b
-        self.problem = FistaProblem(wt_plan.handle, blur_plan.handle, b.data_ptr(), float(lam), float(lipschitz))
+        self.problem = FistaProblem(wt_plan.handle, blur_plan.handle, b.data_ptr(), float(lam), float(lipschitz),
+                                    self.GRADIENT[gradient])
         self.ws = workspace(lib().adjwt_fista_workspace_size(C.byref(self.problem)))
         self.x = torch.zeros(wt_plan.num_coeffs, dtype=torch.float32, device="cuda")
         self.y = torch.zeros_like(self.x)

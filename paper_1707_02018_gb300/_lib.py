@@ -16,7 +16,8 @@ DP = C.POINTER(C.c_double)
 
 
 class FistaProblem(C.Structure):
-    _fields_ = [("wt", VP), ("blur", VP), ("b", VP), ("lam", C.c_double), ("lipschitz", C.c_double)]
+    _fields_ = [("wt", VP), ("blur", VP), ("b", VP), ("lam", C.c_double), ("lipschitz", C.c_double),
+                ("gradient", C.c_int)]
 
 
 class FistaState(C.Structure):

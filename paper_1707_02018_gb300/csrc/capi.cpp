@@ -90,6 +90,8 @@ int check_problem(const adjwt_fista_problem* pr) {
   if (!(pr->lambda >= 0.0) || !std::isfinite(pr->lambda)) return fail(ADJWT_ERR_INVALID_ARG, "fista: bad lambda");
   if (!(pr->lipschitz > 0.0) || !std::isfinite(pr->lipschitz))
     return fail(ADJWT_ERR_INVALID_ARG, "fista: lipschitz must be finite and > 0");
+  if (pr->gradient != ADJWT_GRAD_ADJOINT && pr->gradient != ADJWT_GRAD_PINV)
+    return fail(ADJWT_ERR_INVALID_ARG, "fista: unknown gradient mode");
   return check_ptr(pr->b, "b");
 }
 

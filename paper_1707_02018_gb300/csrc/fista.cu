@@ -163,7 +163,7 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
   prox.beta = static_cast<float>((t - 1.0) / t1);
   prox.l1_partials = objective_out ? W.part_a : nullptr;
   int l1_slots = 0;
-  rc = launch_wt_analysis(pr->wt, W.g, nullptr, true, prox, W.ll0, W.ll1, s, &l1_slots);
+  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0, W.ll1, s, &l1_slots);
   if (rc) return rc;
   st->t = t1;
   st->k += 1;
@@ -196,7 +196,7 @@ int fista_step_device_impl(const adjwt_fista_problem* pr, float* x, float* y, vo
   prox.beta_dev = W.momentum + 1;
   prox.l1_partials = objective_dev ? W.part_a : nullptr;
   int l1_slots = 0;
-  rc = launch_wt_analysis(pr->wt, W.g, nullptr, true, prox, W.ll0, W.ll1, s, &l1_slots);
+  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0, W.ll1, s, &l1_slots);
   if (rc) return rc;
   if (objective_dev) return objective_async(pr, x, W, true, l1_slots, s, objective_dev);
   return ADJWT_OK;

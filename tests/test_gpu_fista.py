@@ -132,3 +132,34 @@ def test_full_size_two_steps_sym(adj):
         f.step()
     assert rel_err(wt.unpack(f.x).cpu().numpy(), x) <= 1e-4
     assert rel_err(wt.unpack(f.y).cpu().numpy(), y) <= 1e-4
+
+
+@pytest.mark.parametrize("w,mode,bc", [("cdf97", "sym", "sym"), ("db2", "per", "per")])
+def test_pinv_gradient_variant(adj, w, mode, bc):
+    """gradient="pinv" (W^dagger in place of W^*) follows the oracle's variant;
+    it stalls above the exact-adjoint objective for a biorthogonal transform
+    with symmetric boundaries and coincides with it for an orthogonal one with
+    circular boundaries."""
+    import dataclasses
+    prob_e, wt, bl, db = _setup(adj, 96, 80, 2, w, mode, 7, 1.2, 2e-3, 31, bc=bc)
+    prob_p = dataclasses.replace(prob_e, gradient="pinv")
+    L = ofista.lipschitz(prob_e, random_vector(wt.logical_size, 2), iters=30)
+    fe = adj.Fista(wt, bl, db, 2e-3, L)
+    fp = adj.Fista(wt, bl, db, 2e-3, L, gradient="pinv")
+    x, y, t = np.zeros(wt.logical_size), np.zeros(wt.logical_size), 1.0
+    for k in range(1, 21):
+        x, y, t = ofista.fista_step(prob_p, x, y, t, L)
+        Fg = fp.step(objective=(k % 10 == 0))
+        if k % 10 == 0:
+            assert abs(Fg - prob_p.objective(x)) <= 1e-5 * prob_p.objective(x)
+    assert rel_err(wt.unpack(fp.x).cpu().numpy(), x) <= 1e-4
+    for _ in range(20):
+        fe.step()
+    for _ in range(130):
+        fe.step()
+        fp.step()
+    Fe, Fp = fe.objective(), fp.objective()
+    if mode == "sym":
+        assert Fp > 1.1 * Fe
+    else:
+        assert abs(Fp - Fe) <= 1e-5 * Fe

@@ -77,3 +77,30 @@ def test_objective_and_soft_threshold():
     res = blur.blur(wavelet.wt_synth(x, 16, 12, 2, "db2", "sym"), prob.p_rows, prob.p_cols, "sym") - prob.b
     assert abs(prob.objective(x) - (0.5 * np.sum(res ** 2) + 1e-3 * np.abs(x).sum())) < 1e-12
     assert abs(fista.t_next(1.0) - (1 + np.sqrt(5)) / 2) < 1e-15
+
+
+def test_pinv_in_place_of_adjoint_fails_to_minimise():
+    """The paper's comparison (Sec. I-B, I-C): FISTA with W^dagger standing in
+    for W^* no longer descends F for a biorthogonal transform with symmetric
+    boundaries, while for an orthogonal transform with circular (or zero)
+    boundaries W^dagger = W^* and the two runs coincide."""
+    from oracle import blur as ob
+    from oracle import fista as ofista
+    from oracle.layout import num_coeffs
+    from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
+    r, c, lam = 48, 40, 2e-3
+    p = ob.gaussian_psf(7, 1.2)
+    out = {}
+    for w, mode, bc, L_len in [("cdf97", "sym", "sym", 10), ("db2", "per", "per", 4)]:
+        b = ob.blur(piecewise_smooth_image(r, c, 5), p, p, bc) + gaussian_noise((r, c), 6)
+        exact = ofista.Problem(r, c, 2, w, mode, p, p, bc, b, lam)
+        pinv = ofista.Problem(r, c, 2, w, mode, p, p, bc, b, lam, gradient="pinv")
+        L = ofista.lipschitz(exact, random_vector(num_coeffs(r, c, 2, L_len, mode), 1), 30)
+        assert ofista.lipschitz(pinv, random_vector(num_coeffs(r, c, 2, L_len, mode), 1), 30) == L
+        _, he = ofista.fista(exact, L, 150, record_every=150)
+        _, hp = ofista.fista(pinv, L, 150, record_every=150)
+        out[w] = (he[-1][1], hp[-1][1])
+    fe, fp = out["cdf97"]
+    assert fp > 1.1 * fe  # 1.42 vs 1.18 at this size
+    fe, fp = out["db2"]
+    assert abs(fp - fe) <= 1e-12 * fe
