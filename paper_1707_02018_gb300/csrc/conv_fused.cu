@@ -9,7 +9,8 @@
 //   r_loc[v] = r[m0 + v]               v < 4096 + kp + 32 (zero past n + k - 1)
 // and either loads r (conv_adjoint) or computes it on chip for the 4096
 // positions the chunk needs (conv_gradient; the kp - 1 overlap with the next
-// chunk is recomputed there).  Then
+// chunk is recomputed there).  The per-thread grad_h partials reuse the
+// s_loc space once the products are done.  Then
 //   grad_s[m0 + m] = sum_i h[i] r_loc[m + i]                        (m < CH)
 //   part[j]        = sum_{m < CH} s_loc[m + kp - 1] r_loc[m + j]     (j < k)
 // Every product loop is a 16-output sliding window: a thread keeps 16
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kNT, 4) k_conv_grad(int64_t n, int K, const fl
   float* h_sm = sm;                      // kp floats (16-aligned)
   float* s_loc = h_sm + kp;
   float* r_loc = s_loc + g.s_words();
-  float* red = r_loc + g.r_words();
+  float* red = s_loc;  // grad_h partials, written once every thread is done with s_loc
   const int b = blockIdx.y;
   const int64_t m0 = (int64_t)blockIdx.x * g.ch;
   const int64_t nr = n + K - 1;
@@ -236,6 +237,10 @@ __global__ void __launch_bounds__(kNT, 4) k_conv_grad(int64_t n, int K, const fl
           for (int o = 0; o < kW; ++o) acc[o] = fmaf(sval, buf[(o + mm) & (kW - 1)], acc[o]);
         }
       }
+    }
+    __syncthreads();  // red aliases s_loc
+    if (grp < g.groups) {
+      const int j0 = grp * kW;
 #pragma unroll
       for (int o = 0; o < kW; ++o) red[(j0 + o) * (g.tpg + 1) + lane_in_grp] = acc[o];
     }
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(kNT, 4) k_conv_grad(int64_t n, int K, const fl
 
 size_t fused_smem(int k) {
   const FusedGeo g(k);
-  return (size_t)(g.kp + g.s_words() + g.r_words() + g.red_words()) * sizeof(float);
+  return (size_t)(g.kp + g.s_words() + g.r_words()) * sizeof(float);  // red_words() <= s_words()
 }
 
 }  // namespace
