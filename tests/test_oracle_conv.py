@@ -86,3 +86,33 @@ def test_finite_difference_gradient():
         e = np.zeros(N)
         e[m] = eps
         assert abs((f(h, s + e) - f(h, s - e)) / (2 * eps) - gs[m]) < 1e-7
+
+
+def test_bce_gradient_finite_differences_and_parts():
+    """Eq. 6: the gradient of the smooth multichannel objective matches central
+    differences; D^T is the transpose of the dense difference matrix; the
+    Huber function is quadratic inside [-delta, delta] and linear outside."""
+    rng = np.random.default_rng(11)
+    C, N, K, lam_tv, delta = 2, 9, 5, 0.3, 0.1
+    s, H = rng.standard_normal(N), rng.standard_normal((C, K))
+    X = rng.standard_normal((C, N + K - 1))
+    gh, gs = conv.bce_gradient(s, H, X, lam_tv, delta)
+    eps = 1e-6
+    for c in range(C):
+        for j in range(K):
+            Hp, Hm = H.copy(), H.copy()
+            Hp[c, j] += eps
+            Hm[c, j] -= eps
+            fd = (conv.bce_smooth(s, Hp, X, lam_tv, delta) - conv.bce_smooth(s, Hm, X, lam_tv, delta)) / (2 * eps)
+            assert abs(fd - gh[c, j]) <= 1e-6 * (1 + abs(fd))
+    for m in range(N):
+        sp, sm = s.copy(), s.copy()
+        sp[m] += eps
+        sm[m] -= eps
+        fd = (conv.bce_smooth(sp, H, X, lam_tv, delta) - conv.bce_smooth(sm, H, X, lam_tv, delta)) / (2 * eps)
+        assert abs(fd - gs[m]) <= 1e-6 * (1 + abs(fd))
+    D = np.diff(np.eye(K), axis=0)  # (D h)[j] = h[j+1] - h[j]
+    v = rng.standard_normal(K - 1)
+    assert np.allclose(conv.tv_diff(H[0]), D @ H[0]) and np.allclose(conv.tv_diff_adjoint(v), D.T @ v)
+    z = np.array([-0.3, -0.1, 0.05, 0.1, 0.2])
+    assert np.allclose(conv.huber(z, 0.1), [0.1 * (0.3 - 0.05), 0.005, 0.00125, 0.005, 0.1 * (0.2 - 0.05)])
