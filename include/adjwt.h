@@ -186,6 +186,19 @@ int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const floa
 int conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                   adjwt_stream_t stream);
 
+/* Gradient of the smooth part of the augmented multichannel problem of
+ * Sec. II, Eq. 6: `channels` responses h_c (channels x k) share the source s
+ * (length n); observations x (channels x (n+k-1)); r_c = h_c * s - x_c;
+ *   f = sum_c ||r_c||^2 + (lambda_tv/delta) L_delta(D h_c),  (D h)[j] = h[j+1]-h[j],
+ *   grad_h[c] = 2 S^T r_c + (lambda_tv/delta) D^T clip(D h_c, -delta, delta),
+ *   grad_s    = sum_c 2 H_c^T r_c   (L_delta = Huber, clip = its derivative).
+ * Either output may be NULL.  delta > 0, lambda_tv >= 0 (INVALID_ARG);
+ * channels, n, k >= 1 and k <= 4096 (SHAPE).  Workspace:
+ * adjwt_bce_gradient_workspace_size bytes, 256-byte aligned. */
+size_t adjwt_bce_gradient_workspace_size(int channels, int64_t n, int k);
+int bce_gradient(int channels, int64_t n, int k, const float* s, const float* h, const float* x, double lambda_tv,
+                 double delta, float* grad_h, float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+
 /* --------------------------------------------------------------------- FISTA
  * min_x 1/2 ||R W x - b||^2 + lambda ||x||_1 (Eq. 1) with constant step
  * 1/lipschitz.  The wavelet and blur plans must describe the same image. */

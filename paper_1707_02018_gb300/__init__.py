@@ -184,6 +184,20 @@ class BlurPlan:
         return out
 
 
+def bce_gradient(s, h, x, lambda_tv, delta, ws=None, stream=None):
+    """(grad_h, grad_s) of the smooth part of Eq. 6 for channels h (C, k)
+    sharing the source s (n,), observations x (C, n + k - 1)."""
+    C, k = h.shape
+    n = s.shape[0]
+    assert x.shape == (C, n + k - 1)
+    gh = torch.empty(C, k, dtype=torch.float32, device=h.device)
+    gs = torch.empty(n, dtype=torch.float32, device=h.device)
+    wsp, nb = _ws(lib().adjwt_bce_gradient_workspace_size(C, n, k), ws)
+    _lib.check(lib().bce_gradient(C, n, k, _ptr(s), _ptr(h), _ptr(x), float(lambda_tv), float(delta), _ptr(gh),
+                                  _ptr(gs), _ptr(wsp), nb, _stream(stream)))
+    return gh, gs
+
+
 def device_status(clear=True):
     """Device status word (0, or ADJWT_ERR_TIMEOUT after a bounded wait gave up); synchronises."""
     v = C.c_int()

@@ -53,6 +53,8 @@ PROTOTYPES = {
     "conv_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "adjwt_fista_workspace_size": (SZ, [C.POINTER(FistaProblem)]),
     "fista_step": (C.c_int, [C.POINTER(FistaProblem), C.POINTER(FistaState), VP, SZ, DP, VP]),
+    "adjwt_bce_gradient_workspace_size": (SZ, [C.c_int, I64, C.c_int]),
+    "bce_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, SZ, VP]),
     "fista_step_device": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, SZ, VP, VP]),
     "adjwt_fista_device_reset": (C.c_int, [C.POINTER(FistaProblem), VP, SZ, VP]),
     "adjwt_fista_objective": (C.c_int, [C.POINTER(FistaProblem), VP, VP, SZ, DP, VP]),

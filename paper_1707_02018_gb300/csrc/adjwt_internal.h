@@ -222,6 +222,9 @@ int launch_conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, con
                                 float* grad_h, float* grad_s, cudaStream_t st);
 int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,
                          cudaStream_t st);
+// Eq. 6: grad_h <- 2 grad_h + (lambda_tv/delta) D^T clip(D h), grad_s = 2 sum_c gs_rows[c].
+int launch_bce_finish(int C, int64_t n, int k, const float* h, float* grad_h, const float* gs_rows, float* grad_s,
+                      double lambda_tv, double delta, cudaStream_t s);
 
 
 }  // namespace adjwt

@@ -234,6 +234,51 @@ extern "C" int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s,
   return launch_conv_adjoint_noalloc(batch, n, k, s, h, r, grad_h, grad_s, stream);
 }
 
+// Eq. 6 workspace: the replicated source and the per-channel source
+// gradients (C x n floats each), then the channel-gradient workspace.
+extern "C" size_t adjwt_bce_gradient_workspace_size(int channels, int64_t n, int k) {
+  if (channels <= 0 || n <= 0 || k <= 0) return 0;
+  const size_t rows = static_cast<size_t>(round_up((int64_t)channels * n * 4, 256));
+  return 2 * rows + adjwt_conv_gradient_workspace_size(channels, n, k);
+}
+
+extern "C" int bce_gradient(int channels, int64_t n, int k, const float* s, const float* h, const float* x,
+                            double lambda_tv, double delta, float* grad_h, float* grad_s, void* ws, size_t ws_bytes,
+                            adjwt_stream_t stream) {
+  if (channels < 1 || n < 1 || k < 1) return fail(ADJWT_ERR_SHAPE, "bce_gradient: need channels, n, k >= 1");
+  if (channels > 65535 || k > 4096) return fail(ADJWT_ERR_SHAPE, "bce_gradient: channels above 65535 or k above 4096");
+  if (!(delta > 0.0) || !std::isfinite(delta) || !(lambda_tv >= 0.0) || !std::isfinite(lambda_tv))
+    return fail(ADJWT_ERR_INVALID_ARG, "bce_gradient: need delta > 0 and lambda_tv >= 0, finite");
+  int rc = check_ptr(s, "s");
+  if (!rc) rc = check_ptr(h, "h");
+  if (!rc) rc = check_ptr(x, "x");
+  if (!rc && grad_h) rc = check_ptr(grad_h, "grad_h");
+  if (!rc && grad_s) rc = check_ptr(grad_s, "grad_s");
+  if (rc) return rc;
+  const size_t sb = (size_t)n * 4, hb = (size_t)channels * k * 4, xb = (size_t)channels * (n + k - 1) * 4;
+  const void* ins[3] = {s, h, x};
+  const size_t inb[3] = {sb, hb, xb};
+  for (int i = 0; i < 3; ++i) {
+    if (grad_h && overlap(grad_h, hb, ins[i], inb[i])) return fail(ADJWT_ERR_ALIAS, "bce_gradient: grad_h overlaps an input");
+    if (grad_s && overlap(grad_s, sb, ins[i], inb[i])) return fail(ADJWT_ERR_ALIAS, "bce_gradient: grad_s overlaps an input");
+  }
+  if (grad_h && grad_s && overlap(grad_h, hb, grad_s, sb)) return fail(ADJWT_ERR_ALIAS, "bce_gradient: outputs overlap");
+  const size_t need = adjwt_bce_gradient_workspace_size(channels, n, k);
+  rc = check_ws(ws, ws_bytes, need, "bce_gradient");
+  if (rc) return rc;
+  if (!grad_h && !grad_s) return ADJWT_OK;
+  const size_t rows = static_cast<size_t>(round_up((int64_t)channels * n * 4, 256));
+  float* s_rows = static_cast<float*>(ws);
+  float* gs_rows = reinterpret_cast<float*>(static_cast<char*>(ws) + rows);
+  void* cws = static_cast<char*>(ws) + 2 * rows;
+  for (int c = 0; c < channels; ++c)
+    ADJWT_CUDA_CHECK(cudaMemcpyAsync(s_rows + (size_t)c * n, s, sb, cudaMemcpyDeviceToDevice, stream));
+  rc = conv_gradient(channels, n, k, s_rows, h, x, nullptr, grad_h, grad_s ? gs_rows : nullptr, cws,
+                     adjwt_conv_gradient_workspace_size(channels, n, k), stream);
+  if (rc) return rc;
+  return launch_bce_finish(channels, n, k, h, grad_h, gs_rows, grad_s, lambda_tv, delta, stream);
+}
+
 extern "C" size_t adjwt_conv_gradient_workspace_size(int batch, int64_t n, int k) {
   if (batch <= 0 || n <= 0 || k <= 0) return 0;
   size_t bytes = adjwt_conv_adjoint_workspace_size(batch, n, k);

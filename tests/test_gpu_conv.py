@@ -90,3 +90,21 @@ def test_full_size_256x65536x64(adj):
     gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x))
     assert_close(gh.cpu().numpy(), wh, what="fused grad_h full")
     assert_close(gs.cpu().numpy(), ws, what="fused grad_s full")
+
+
+@pytest.mark.parametrize("C,n,k", [(2, 1767, 844), (2, 1717, 894), (3, 300, 17), (1, 5, 3), (2, 2000, 1500)])
+def test_bce_gradient_eq6(C, n, k):
+    """Eq. 6 (shared source, Huber-softened TV on the channels) at the paper's
+    estimated and true lengths (N_est = 1767, K_est = 844; N = 1717, K = 894),
+    small cases, and k above the fused kernel's limit."""
+    import paper_1707_02018_gb300 as adj
+    from oracle import conv as oconv
+    rng = np.random.default_rng(C * 1000 + k)
+    s, H = rng.standard_normal(n), rng.standard_normal((C, k))
+    X = rng.standard_normal((C, n + k - 1))
+    lam_tv, delta = 0.01, 0.1  # the paper's lambda_{h,TV} and delta
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float32, device="cuda").contiguous()  # noqa: E731
+    gh, gs = adj.bce_gradient(dev(s), dev(H), dev(X), lam_tv, delta)
+    wh, ws_ = oconv.bce_gradient(s, H, X, lam_tv, delta)
+    assert_close(gh.cpu().numpy(), wh, what=f"grad_h C{C} n{n} k{k}")
+    assert_close(gs.cpu().numpy(), ws_, what=f"grad_s C{C} n{n} k{k}")
