@@ -218,6 +218,14 @@ bool conv_fused_supported(int k);
 int64_t conv_fused_nchunks(int64_t n, int k);
 int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
                       float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st);
+// Tensor-core channel-gradient kernel for 49 <= k <= 64 (tcgen05 TF32 with a
+// float32-accurate three-product split); launch_conv_fused routes those k here
+// unless ADJWT_CONV_FP32 is set to a non-zero value in the environment.  Its
+// grad_h partials need at most as many slots as the register-blocked kernel's.
+bool conv_tc_supported(int k);
+int64_t conv_tc_nchunks(int64_t n);
+int launch_conv_tc(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
+                   float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st);
 int launch_conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
                                 float* grad_h, float* grad_s, cudaStream_t st);
 int launch_conv_residual(int batch, int64_t n, int k, const float* h, const float* s, const float* x, float* r,

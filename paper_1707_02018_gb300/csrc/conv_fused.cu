@@ -19,6 +19,8 @@
 // carry one pad word per 16 (index p -> p + p/16): the 16-word lane stride of
 // the windows then lands on 32 distinct banks, and with 16-aligned windows
 // all load offsets inside a 16-tap step are compile-time constants.
+#include <cstdlib>
+
 #include "adjwt_internal.h"
 #include "device_common.cuh"
 
@@ -274,6 +276,12 @@ bool conv_fused_supported(int k) { return k >= 1 && k <= kFusedMaxK; }
 int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
                       float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st) {
   if (batch == 0) return ADJWT_OK;
+  static const bool force_fp32 = [] {
+    const char* e = std::getenv("ADJWT_CONV_FP32");
+    return e && std::atoi(e) != 0;
+  }();
+  if (conv_tc_supported(k) && !force_fp32)
+    return launch_conv_tc(batch, n, k, s, h, x, r_in, r_out, grad_h, grad_s, partials, st);
   const int64_t nch = conv_fused_nchunks(n, k);
   if (nch > 0x7fffffff) return fail(ADJWT_ERR_SHAPE, "conv: n too large");
   const size_t smem = fused_smem(k);

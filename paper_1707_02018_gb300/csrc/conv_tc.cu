@@ -1,0 +1,414 @@
+// Channel gradient (Sec. II, Eq. 5) for 49 <= k <= 64 (taps zero-padded to
+// 64) on the 5th-generation tensor cores.
+//
+// A CTA owns a chunk of 4096 samples of one row, m0 .. m0 + 4095, seen as 128
+// blocks of 32 (block a, offset c: sample m0 + 32 a + c).  Two of the three
+// sums of Eq. 5 are then M = 128 (blocks) x N = 32 x K = 96 products:
+//   r[32a + c]      = sum_{q<96} W[a][q] H1[q][c],  W[a][q] = s[m0 - 64 + 32a + q],  H1[q][c] = h[c + 64 - q]
+//   grad_s[32a + c] = sum_{q<96} V[a][q] H2[q][c],  V[a][q] = r[m0 + 32a + q],       H2[q][c] = h[q - c]
+// issued with tcgen05.mma (kind::tf32, accumulators in tensor memory), and
+//   part[j] = sum_{a<128, c<32} s[m0 + 32a + c] r[m0 + 32a + c + j]      (j < k)
+// runs on the warp-level m16n8k8 TF32 MMA while the tensor core computes
+// grad_s.  Operands live in shared memory in the K-major no-swizzle layout as
+// block matrices B[a'][j] = x[base + 32 a' + j] stored [j/4][a'][4]: each row
+// of a 4-column slab is 16 bytes, so the K range [32 t, 32 t + 32) of W (or V)
+// is the same matrix t rows down (descriptor start + 16 t bytes).  The
+// Toeplitz factors are one band array per product, G[rho][k'] (8 columns), of
+// which K-step kk reads the 32 rows from 88 - 8 kk.  The 64 residuals past the
+// chunk (read by grad_s and grad_h of its last two blocks) come from the CUDA
+// cores.  Float32 accuracy: each operand is split into a TF32 high part and
+// the float remainder, and each K-step issues lo*hi, hi*lo and hi*hi.  About
+// 100 KB of shared memory per CTA, so two CTAs share an SM and one CTA's
+// loads overlap the other's products.  Every mbarrier wait is bounded.
+#include "adjwt_internal.h"
+#include "tma.cuh"
+
+namespace adjwt {
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kLb = 32;                  // block length (N of the products)
+constexpr int kBlocks = 128;             // blocks per chunk (M)
+constexpr int kChunk = kBlocks * kLb;    // 4096 samples owned per CTA
+constexpr int kKSteps = (kLb + 64) / 8;  // 12 K-steps of 8
+constexpr int kSRows = kBlocks + 4;      // s rows: s[m0 - 64] .. s[m0 + 4159]
+constexpr int kRNeed = kBlocks + 2;      // r rows read: r[m0] .. r[m0 + 4159]
+constexpr int kRRows = kBlocks + 4;      // r slab pitch (rows); 132 = 4 mod 8 keeps the fragment reads conflict-free
+constexpr int kGRows = 120;              // band rows: 31 + 88 + 1
+constexpr int kGOff = 88;                // K-step kk reads band rows kGOff - 8 kk ..
+constexpr int kXPitch = kLb + 1;         // staging tile pitch (conflict-free column access)
+
+// float offsets in dynamic shared memory (each a multiple of 32 floats)
+constexpr int kS_HI = 0;
+constexpr int kS_LO = kS_HI + kSRows * kLb;
+constexpr int kR_HI = kS_LO + kSRows * kLb;
+constexpr int kR_LO = kR_HI + kRRows * kLb;
+constexpr int kG1_HI = kR_LO + kRRows * kLb;
+constexpr int kG1_LO = kG1_HI + kGRows * 8;
+constexpr int kG2_HI = kG1_LO + kGRows * 8;
+constexpr int kG2_LO = kG2_HI + kGRows * 8;
+constexpr int kX = kG2_LO + kGRows * 8;
+constexpr int kH = kX + (kBlocks * kXPitch + 31) / 32 * 32;
+constexpr int kTotal = kH + 64;
+constexpr size_t kSmemBytes = 128 + (size_t)kTotal * 4;
+static_assert(kSmemBytes <= 113 * 1024, "two CTAs per SM");
+static_assert(32 * 129 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
+constexpr uint32_t kTmemCols = 64;
+
+__host__ __device__ constexpr int blk_idx(int row, int j, int rows) { return ((j >> 2) * rows + row) * 4 + (j & 3); }
+
+// v = hi + lo exactly: hi keeps the 10 explicit mantissa bits a TF32 operand
+// carries (so it is exact whether the tensor core truncates or rounds), lo is
+// the float remainder.
+__device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  lo = v - hi;
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // start >> 4 at [0,14), K-direction core-matrix stride >> 4 at [16,30),
+  // M/N-direction 8-row-group stride >> 4 at [32,46), descriptor version 1 at
+  // bit 46, no swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: f32 accumulate, tf32 A and B, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kLb >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_m16n8k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One product (36 MMAs: 12 K-steps x lo*hi, hi*lo, hi*hi) into tmem_d.
+// X: block matrix with slab pitch `rows` (hi at xh, lo at xl); G: band arrays.
+__device__ __forceinline__ void issue_product(uint32_t tmem_d, uint32_t xh, uint32_t xl, int rows, uint32_t gh,
+                                              uint32_t gl) {
+  const uint32_t lbo_x = rows * 16, lbo_g = kGRows * 16;
+#pragma unroll 1
+  for (int kk = 0; kk < kKSteps; ++kk) {
+    const uint32_t aoff = 2 * (kk & 3) * lbo_x + 16 * (kk >> 2);
+    const uint32_t boff = (kGOff - 8 * kk) * 16;
+    const uint64_t ah = umma_desc(xh + aoff, lbo_x, 128), al = umma_desc(xl + aoff, lbo_x, 128);
+    const uint64_t bh = umma_desc(gh + boff, lbo_g, 128), bl = umma_desc(gl + boff, lbo_g, 128);
+    umma_tf32(tmem_d, al, bh, kk > 0);
+    umma_tf32(tmem_d, ah, bl, 1);
+    umma_tf32(tmem_d, ah, bh, 1);
+  }
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_wait(bar, parity)) return true;
+  record_status(status, ADJWT_ERR_TIMEOUT);
+  return false;
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const float* __restrict__ s,
+                                                    const float* __restrict__ h, const float* __restrict__ x,
+                                                    const float* __restrict__ r_in, float* __restrict__ r_out,
+                                                    float* __restrict__ grad_s, float* __restrict__ part_h, int nchunks,
+                                                    int* status) {
+  pdl_entry();
+  extern __shared__ unsigned char dyn[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_holder;
+  float* sm = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
+  float* S_hi = sm + kS_HI;
+  float* S_lo = sm + kS_LO;
+  float* R_hi = sm + kR_HI;
+  float* R_lo = sm + kR_LO;
+  float* X = sm + kX;
+  float* h_sm = sm + kH;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t nr = n + K - 1;
+  const bool last = blockIdx.x == nchunks - 1;
+
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+
+  // ---- stage h, s (hi/lo block matrix), and x (fused) or r (given) ----
+  if (tid < 64) h_sm[tid] = tid < K ? __ldg(h + (size_t)b * K + tid) : 0.0f;
+  {
+    const float* srow = s + (size_t)b * n;
+    constexpr int total = kSRows * kLb, U = (total + kNT - 1) / kNT;
+    float v[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = tid + j * kNT;
+      const int64_t q = m0 - 64 + u;
+      v[j] = (u < total && q >= 0 && q < n) ? __ldg(srow + q) : 0.0f;
+    }
+    const float* rrow = FUSED ? (x ? x + (size_t)b * nr : nullptr) : r_in + (size_t)b * nr;
+    constexpr int rtotal = FUSED ? kChunk : kRNeed * kLb, W = (rtotal + kNT - 1) / kNT;
+    float w[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int u = tid + j * kNT;
+      const int64_t q = m0 + u;
+      w[j] = (rrow && u < rtotal && q < nr) ? __ldg(rrow + q) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = tid + j * kNT;
+      if (u < total) {
+        const int i = blk_idx(u / kLb, u % kLb, kSRows);
+        tf32_split(v[j], S_hi[i], S_lo[i]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int u = tid + j * kNT;
+      if (u < rtotal) {
+        if (FUSED) {
+          X[(u / kLb) * kXPitch + (u % kLb)] = w[j];
+        } else {
+          const int i = blk_idx(u / kLb, u % kLb, kRRows);
+          tf32_split(w[j], R_hi[i], R_lo[i]);
+        }
+      }
+    }
+  }
+  __syncthreads();  // h_sm ready
+  // Toeplitz bands: G1[rho][k'] = h[rho - k' - 24], G2[rho][k'] = h[k' - rho + 88]
+  for (int i = tid; i < kGRows * 8; i += kNT) {
+    const int rho = i >> 3, kq = i & 7;
+    const int i1 = rho - kq - (kGOff - 64), i2 = kq - rho + kGOff;
+    const float g1 = (i1 >= 0 && i1 < 64) ? h_sm[i1] : 0.0f;
+    const float g2 = (i2 >= 0 && i2 < 64) ? h_sm[i2] : 0.0f;
+    const int o = blk_idx(rho, kq, kGRows);
+    tf32_split(g1, sm[kG1_HI + o], sm[kG1_LO + o]);
+    tf32_split(g2, sm[kG2_HI + o], sm[kG2_LO + o]);
+  }
+  fence_proxy_async();  // generic-proxy writes of the operands -> tensor core
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  const uint32_t base = smem_u32(sm);
+  bool ok = true;
+
+  if (FUSED) {
+    // ---- r = h * s - x: product 1 into tmem columns [0, 32) ----
+    if (tid == 0) {
+      issue_product(tmem, base + kS_HI * 4, base + kS_LO * 4, kSRows, base + kG1_HI * 4, base + kG1_LO * 4);
+      umma_commit(&bar);
+    }
+    // meanwhile the CUDA cores form r on the 64 positions past the chunk
+    // (r rows 128 and 129): four threads per position, 16 taps each
+    {
+      const int e = tid >> 2, quarter = tid & 3;
+      const int p = kChunk + e;  // chunk-relative position; s[m0 + p - i] is s-array entry p + 64 - i
+      float acc = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int i = 16 * quarter + t;
+        const int u = p + 64 - i;
+        const int si = blk_idx(u / kLb, u % kLb, kSRows);
+        acc = fmaf(h_sm[i], S_hi[si] + S_lo[si], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (quarter == 0) {
+        const int64_t q = m0 + p;
+        float rv = 0.0f;
+        if (q < nr) rv = acc - (x ? __ldg(x + (size_t)b * nr + q) : 0.0f);
+        const int i = blk_idx(p / kLb, p % kLb, kRRows);
+        tf32_split(rv, R_hi[i], R_lo[i]);
+        if (last && r_out && p < kChunk + K - 1 && q < nr) r_out[(size_t)b * nr + q] = rv;
+      }
+    }
+    ok = wait_bar(&bar, 0, status);
+    tc_fence_after();
+    ok = __syncthreads_and(ok);
+    if (ok) {
+      const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
+#pragma unroll
+      for (int cc = 0; cc < 16; cc += 8) {
+        float d[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0 + cc, d);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int c = c0 + cc + e;
+          const int64_t q = m0 + kLb * a + c;
+          const float rv = q < nr ? d[e] - X[a * kXPitch + c] : 0.0f;
+          const int i = blk_idx(a, c, kRRows);
+          tf32_split(rv, R_hi[i], R_lo[i]);
+          X[a * kXPitch + c] = rv;  // for the coalesced r store
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+
+  // ---- grad_s: product 2 into tmem columns [32, 64), overlapped with grad_h ----
+  if (ok && grad_s && tid == 0) {
+    issue_product(tmem + kLb, base + kR_HI * 4, base + kR_LO * 4, kRRows, base + kG2_HI * 4, base + kG2_LO * 4);
+    umma_commit(&bar);
+  }
+  if (FUSED && ok && r_out) {
+    float* rrow = r_out + (size_t)b * nr;
+    for (int v = tid; v < kChunk; v += kNT) {
+      const int64_t q = m0 + v;
+      if (q < nr) rrow[q] = X[(v / kLb) * kXPitch + (v % kLb)];
+    }
+  }
+
+  // ---- grad_h partial: P[c][q] = sum_{a<128} s[32a + c] r[32a + q] (warp MMA) ----
+  // m tile mc = warp / 4 (rows c = 16 mc ..); its 10 n tiles (8 columns q
+  // each, from tile 2 mc) go 3, 3, 2, 2 to the four warps of the m tile.
+  if (ok && part_h) {
+    const int g = lane >> 2, t = lane & 3;
+    const int mc = warp >> 2, qw = warp & 3;
+    const int nq0 = 2 * mc + (qw < 2 ? 3 * qw : 2 * qw + 2);
+    const int ntiles = qw < 2 ? 3 : 2;
+    float acc[3][4];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[u][i] = 0.0f;
+    const int c_a = 16 * mc + g, c_b = c_a + 8;
+#pragma unroll 1
+    for (int kk = 0; kk < kBlocks / 8; ++kk) {
+      const int a0 = 8 * kk + t, a1 = a0 + 4;  // blocks; s of block a is s row a + 2
+      const int i0 = blk_idx(a0 + 2, c_a, kSRows), i1 = blk_idx(a0 + 2, c_b, kSRows);
+      const int i2 = blk_idx(a1 + 2, c_a, kSRows), i3 = blk_idx(a1 + 2, c_b, kSRows);
+      const uint32_t ah[4] = {__float_as_uint(S_hi[i0]), __float_as_uint(S_hi[i1]), __float_as_uint(S_hi[i2]),
+                              __float_as_uint(S_hi[i3])};
+      const uint32_t al[4] = {__float_as_uint(S_lo[i0]), __float_as_uint(S_lo[i1]), __float_as_uint(S_lo[i2]),
+                              __float_as_uint(S_lo[i3])};
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (u < ntiles) {
+          const int q = 8 * (nq0 + u) + g;  // r[32a + q]: row a + q / 32, column q % 32
+          const int j0 = blk_idx(a0 + q / kLb, q % kLb, kRRows), j1 = blk_idx(a1 + q / kLb, q % kLb, kRRows);
+          const uint32_t bh0 = __float_as_uint(R_hi[j0]), bl0 = __float_as_uint(R_lo[j0]);
+          const uint32_t bh1 = __float_as_uint(R_hi[j1]), bl1 = __float_as_uint(R_lo[j1]);
+          mma_m16n8k8(acc[u], al, bh0, bh1);
+          mma_m16n8k8(acc[u], ah, bl0, bl1);
+          mma_m16n8k8(acc[u], ah, bh0, bh1);
+        }
+      }
+    }
+    __syncthreads();  // P[32][129] and the partial sums reuse the s arrays
+    float* P = S_hi;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (u < ntiles) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = 16 * mc + g + 8 * (i >> 1), q = 8 * (nq0 + u) + 2 * t + (i & 1);
+          P[c * 129 + q] = acc[u][i];
+        }
+      }
+    __syncthreads();
+    float* red4 = P + 32 * 129;
+    {
+      const int j = tid & 63, quarter = tid >> 6;
+      float tsum = 0.0f;
+#pragma unroll
+      for (int c = 8 * quarter; c < 8 * quarter + 8; ++c) tsum += P[c * 129 + c + j];
+      red4[quarter * 64 + j] = tsum;
+    }
+    __syncthreads();
+    float* dst = part_h + ((size_t)b * nchunks + blockIdx.x) * K;
+    for (int j = tid; j < K; j += kNT) dst[j] = (red4[j] + red4[64 + j]) + (red4[128 + j] + red4[192 + j]);
+  }
+
+  // ---- grad_s out of tensor memory, through the staging tile ----
+  if (ok && grad_s) {
+    ok = wait_bar(&bar, FUSED ? 1 : 0, status);
+    tc_fence_after();
+    ok = __syncthreads_and(ok);  // also: the r store has finished reading X
+    if (ok) {
+      const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
+#pragma unroll
+      for (int cc = 0; cc < 16; cc += 8) {
+        float d[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kLb + c0 + cc, d);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) X[a * kXPitch + c0 + cc + e] = d[e];
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      float* out = grad_s + (size_t)b * n;
+      for (int v = tid; v < kChunk; v += kNT) {
+        const int64_t m = m0 + v;
+        if (m < n) out[m] = X[(v / kLb) * kXPitch + (v % kLb)];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+}  // namespace
+
+bool conv_tc_supported(int k) { return k >= 49 && k <= 64; }
+int64_t conv_tc_nchunks(int64_t n) { return (n + kChunk - 1) / kChunk; }
+
+int launch_conv_tc(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
+                   float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st) {
+  if (batch == 0) return ADJWT_OK;
+  const int64_t nch = conv_tc_nchunks(n);
+  if (nch > 0x7fffffff || batch > 65535) return fail(ADJWT_ERR_SHAPE, "conv: n or batch too large");
+  dim3 grid(static_cast<unsigned>(nch), static_cast<unsigned>(batch));
+  float* part = grad_h ? partials : nullptr;
+  auto kern = r_in ? k_conv_tc<false> : k_conv_tc<true>;
+  ADJWT_CUDA_CHECK(set_smem(kern, kSmemBytes));
+  ADJWT_TRACED(r_in ? "conv_adjoint" : "conv_gradient", 0, st,
+               pdl_launch(kern, grid, kNT, kSmemBytes, st, n, k, s, h, r_in ? nullptr : x, r_in,
+                          r_in ? nullptr : r_out, grad_s, part, static_cast<int>(nch), device_status_ptr()));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  if (grad_h) {
+    const int64_t total = (int64_t)batch * k;
+    const unsigned nb = static_cast<unsigned>((total + 255) / 256);
+    ADJWT_TRACED("conv_reduce", 0, st, conv_reduce(nb, k, static_cast<int>(nch), partials, grad_h, total, st));
+    ADJWT_CUDA_CHECK(cudaGetLastError());
+  }
+  return ADJWT_OK;
+}
+
+}  // namespace adjwt

@@ -35,7 +35,8 @@ def test_paper_k3_n5_exact(adj):
 
 
 @pytest.mark.parametrize("B,n,k", [(3, 5, 3), (2, 1, 1), (4, 1000, 64), (2, 1025, 7), (1, 3, 9), (5, 3000, 300),
-                                   (2, 2048, 257), (1, 4097, 1)])
+                                   (2, 2048, 257), (1, 4097, 1), (2, 8129, 64), (3, 16333, 57), (1, 20000, 49),
+                                   (2, 30, 64)])
 def test_conv_parity(adj, B, n, k):
     p = channel_problem(B, n, k, seed=B * 1000 + n + k)
     x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
@@ -49,10 +50,15 @@ def test_conv_parity(adj, B, n, k):
 
 
 @pytest.mark.parametrize("B,n,k", [(3, 5, 3), (2, 1, 1), (4, 1000, 64), (2, 4033, 64), (2, 8065, 64),
-                                   (1, 3, 9), (3, 3000, 300), (2, 5000, 1024), (2, 3000, 1025), (1, 7000, 17)])
+                                   (1, 3, 9), (3, 3000, 300), (2, 5000, 1024), (2, 3000, 1025), (1, 7000, 17),
+                                   (2, 8128, 64), (2, 8129, 64), (3, 16333, 57), (1, 24389, 49), (2, 63, 64),
+                                   (1, 1, 64), (2, 9000, 48), (2, 9000, 65)])
 def test_conv_gradient_fused_parity(adj, B, n, k):
-    """r = h * s - x and both gradients in one call (chunk edges at 4032 / 8064 for k = 64;
-    k = 1025 takes the two-kernel path with r in the workspace)."""
+    """r = h * s - x and both gradients in one call.  49 <= k <= 64 runs on
+    the tensor-core kernel (chunks of 8128 samples: edges at 8128, 16256 and
+    a ragged tail); k = 48 and 65 sit just outside it on the register-blocked
+    kernel (chunk edges at 4032 / 8064 for k = 64 there); k = 1025 takes the
+    two-kernel path with r in the workspace."""
     p = channel_problem(B, n, k, seed=B * 7 + n + k)
     x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
     r_want = oconv.conv_full(p["h_est"], p["s_est"]) - x
@@ -64,17 +70,23 @@ def test_conv_gradient_fused_parity(adj, B, n, k):
     assert_close(gs.cpu().numpy(), ws, what=f"grad_s {B}x{n}x{k}")
     gh2, gs2 = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x))     # without r out
     assert torch.equal(gh2, gh) and torch.equal(gs2, gs)
+    assert adj.device_status() == 0
 
 
-def test_one_gradient_only_and_empty(adj):
-    s, h = dev(random_vector((2, 50), 1)), dev(random_vector((2, 4), 2))
-    r = dev(random_vector((2, 53), 3))
+@pytest.mark.parametrize("k", [4, 64])
+def test_one_gradient_only_and_empty(adj, k):
+    n = 9000
+    sh, hh, rh = random_vector((2, n), 1), random_vector((2, k), 2), random_vector((2, n + k - 1), 3)
+    s, h, r = dev(sh), dev(hh), dev(rh)
+    wh, ws = oconv.conv_adjoint(sh, hh, rh)
     gh, gs = adj.conv_adjoint(s, h, r, grad_s=False)
-    assert gs is None and gh.shape == (2, 4)
+    assert gs is None and gh.shape == (2, k)
+    assert_close(gh.cpu().numpy(), wh, what="grad_h alone")
     gh2, gs2 = adj.conv_adjoint(s, h, r, grad_h=False)
-    assert gh2 is None and gs2.shape == (2, 50)
-    e = torch.empty(0, 50, device="cuda")
-    gh, gs = adj.conv_adjoint(e, torch.empty(0, 4, device="cuda"), torch.empty(0, 53, device="cuda"))
+    assert gh2 is None and gs2.shape == (2, n)
+    assert_close(gs2.cpu().numpy(), ws, what="grad_s alone")
+    e = torch.empty(0, n, device="cuda")
+    gh, gs = adj.conv_adjoint(e, torch.empty(0, k, device="cuda"), torch.empty(0, n + k - 1, device="cuda"))
     assert gh.numel() == 0 and gs.numel() == 0
 
 
