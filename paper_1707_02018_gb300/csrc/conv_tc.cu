@@ -9,7 +9,10 @@
 // issued with tcgen05.mma (kind::tf32, accumulators in tensor memory), and
 //   part[j] = sum_{a<128, c<32} s[m0 + 32a + c] r[m0 + 32a + c + j]      (j < k)
 // runs on the warp-level m16n8k8 TF32 MMA while the tensor core computes
-// grad_s.  Operands live in shared memory in the K-major no-swizzle layout as
+// grad_s: warp w takes blocks 16 w .. 16 w + 15 for the whole band of
+// P[c][q] = sum_a s[32a + c] r[32a + q] (c < 32, q - c < 64) and folds each
+// product straight into per-thread diagonal sums (j = q - c), which one
+// deterministic pass over shared memory then adds up.  Operands live in shared memory in the K-major no-swizzle layout as
 // block matrices B[a'][j] = x[base + 32 a' + j] stored [j/4][a'][4]: each row
 // of a 4-column slab is 16 bytes, so the K range [32 t, 32 t + 32) of W (or V)
 // is the same matrix t rows down (descriptor start + 16 t bytes).  The
@@ -49,10 +52,12 @@ constexpr int kG2_HI = kG1_LO + kGRows * 8;
 constexpr int kG2_LO = kG2_HI + kGRows * 8;
 constexpr int kX = kG2_LO + kGRows * 8;
 constexpr int kH = kX + (kBlocks * kXPitch + 31) / 32 * 32;
-constexpr int kTotal = kH + 64;
+constexpr int kSLin = kH + 64;           // s[m0 + 4032] .. s[m0 + 4159], linear (taps of the 64 tail residuals)
+constexpr int kTotal = kSLin + 128;
+constexpr int kDiag = 18;                // diagonal sums per thread: d = 0 .. 8, two parities
 constexpr size_t kSmemBytes = 128 + (size_t)kTotal * 4;
 static_assert(kSmemBytes <= 113 * 1024, "two CTAs per SM");
-static_assert(32 * 129 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
+static_assert(8 * kDiag * 32 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
 constexpr uint32_t kTmemCols = 64;
 
 __host__ __device__ constexpr int blk_idx(int row, int j, int rows) { return ((j >> 2) * rows + row) * 4 + (j & 3); }
@@ -88,22 +93,34 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(addr));
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi/lo split of four consecutive columns into one 16-byte slab row each
+__device__ __forceinline__ void split_store4(float* hi, float* lo, int idx, float a, float b, float c, float d) {
+  float4 h4, l4;
+  tf32_split(a, h4.x, l4.x);
+  tf32_split(b, h4.y, l4.y);
+  tf32_split(c, h4.z, l4.z);
+  tf32_split(d, h4.w, l4.w);
+  *reinterpret_cast<float4*>(hi + idx) = h4;
+  *reinterpret_cast<float4*>(lo + idx) = l4;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_m16n8k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
@@ -136,7 +153,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
                                                     const float* __restrict__ h, const float* __restrict__ x,
                                                     const float* __restrict__ r_in, float* __restrict__ r_out,
                                                     float* __restrict__ grad_s, float* __restrict__ part_h, int nchunks,
-                                                    int* status) {
+                                                    int vec, int* status) {
   pdl_entry();
   extern __shared__ unsigned char dyn[];
   __shared__ __align__(8) uint64_t bar;
@@ -148,6 +165,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
   float* R_lo = sm + kR_LO;
   float* X = sm + kX;
   float* h_sm = sm + kH;
+  float* s_lin = sm + kSLin;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.y;
   const int64_t m0 = (int64_t)blockIdx.x * kChunk;
@@ -165,33 +183,73 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
   }
 
   // ---- stage h, s (hi/lo block matrix), and x (fused) or r (given) ----
+  // Vector path (vec bit 0 for s, bit 1 for r): the row is 16-byte aligned
+  // and its length a multiple of 4, so every float4 is wholly inside or
+  // wholly outside the row; a warp's 16-byte stores then cover all banks.
   if (tid < 64) h_sm[tid] = tid < K ? __ldg(h + (size_t)b * K + tid) : 0.0f;
-  {
-    const float* srow = s + (size_t)b * n;
-    constexpr int total = kSRows * kLb, U = (total + kNT - 1) / kNT;
+  const float* srow = s + (size_t)b * n;
+  const float* rrow = FUSED ? (x ? x + (size_t)b * nr : nullptr) : r_in + (size_t)b * nr;
+  constexpr int stotal = kSRows * kLb;
+  constexpr int rtotal = FUSED ? kChunk : kRNeed * kLb;
+  if (vec & 1) {
+    constexpr int U = (stotal / 4 + kNT - 1) / kNT;
+    float4 v[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = 4 * (tid + j * kNT);
+      const int64_t q = m0 - 64 + u;
+      v[j] = (u < stotal && q >= 0 && q < n) ? __ldg(reinterpret_cast<const float4*>(srow + q))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = 4 * (tid + j * kNT);
+      if (u < stotal) {
+        split_store4(S_hi, S_lo, blk_idx(u / kLb, u % kLb, kSRows), v[j].x, v[j].y, v[j].z, v[j].w);
+        if (u >= kChunk) *reinterpret_cast<float4*>(s_lin + u - kChunk) = v[j];
+      }
+    }
+  } else {
+    constexpr int U = (stotal + kNT - 1) / kNT;
     float v[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = tid + j * kNT;
       const int64_t q = m0 - 64 + u;
-      v[j] = (u < total && q >= 0 && q < n) ? __ldg(srow + q) : 0.0f;
+      v[j] = (u < stotal && q >= 0 && q < n) ? __ldg(srow + q) : 0.0f;
     }
-    const float* rrow = FUSED ? (x ? x + (size_t)b * nr : nullptr) : r_in + (size_t)b * nr;
-    constexpr int rtotal = FUSED ? kChunk : kRNeed * kLb, W = (rtotal + kNT - 1) / kNT;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = tid + j * kNT;
+      if (u < stotal) {
+        const int i = blk_idx(u / kLb, u % kLb, kSRows);
+        tf32_split(v[j], S_hi[i], S_lo[i]);
+        if (u >= kChunk) s_lin[u - kChunk] = v[j];
+      }
+    }
+  }
+  if (!FUSED && (vec & 2)) {
+    constexpr int W = (rtotal / 4 + kNT - 1) / kNT;
+    float4 w[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int u = 4 * (tid + j * kNT);
+      const int64_t q = m0 + u;
+      w[j] = (u < rtotal && q < nr) ? __ldg(reinterpret_cast<const float4*>(rrow + q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int u = 4 * (tid + j * kNT);
+      if (u < rtotal) split_store4(R_hi, R_lo, blk_idx(u / kLb, u % kLb, kRRows), w[j].x, w[j].y, w[j].z, w[j].w);
+    }
+  } else {
+    constexpr int W = (rtotal + kNT - 1) / kNT;
     float w[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       const int u = tid + j * kNT;
       const int64_t q = m0 + u;
       w[j] = (rrow && u < rtotal && q < nr) ? __ldg(rrow + q) : 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int u = tid + j * kNT;
-      if (u < total) {
-        const int i = blk_idx(u / kLb, u % kLb, kSRows);
-        tf32_split(v[j], S_hi[i], S_lo[i]);
-      }
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -223,6 +281,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
   const uint32_t base = smem_u32(sm);
+  const uint32_t tmem_warp = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's 32 lanes
   bool ok = true;
 
   if (FUSED) {
@@ -235,18 +294,16 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
     // (r rows 128 and 129): four threads per position, 16 taps each
     {
       const int e = tid >> 2, quarter = tid & 3;
-      const int p = kChunk + e;  // chunk-relative position; s[m0 + p - i] is s-array entry p + 64 - i
       float acc = 0.0f;
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int i = 16 * quarter + t;
-        const int u = p + 64 - i;
-        const int si = blk_idx(u / kLb, u % kLb, kSRows);
-        acc = fmaf(h_sm[i], S_hi[si] + S_lo[si], acc);
+        acc = fmaf(h_sm[i], s_lin[e + 64 - i], acc);  // s[m0 + 4096 + e - i]
       }
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       if (quarter == 0) {
+        const int p = kChunk + e;
         const int64_t q = m0 + p;
         float rv = 0.0f;
         if (q < nr) rv = acc - (x ? __ldg(x + (size_t)b * nr + q) : 0.0f);
@@ -260,19 +317,19 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
     ok = __syncthreads_and(ok);
     if (ok) {
       const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
+      float d[16];
+      tmem_ld16(tmem_warp + c0, d);
 #pragma unroll
-      for (int cc = 0; cc < 16; cc += 8) {
-        float d[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0 + cc, d);
+      for (int g4 = 0; g4 < 16; g4 += 4) {
+        float rv[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = c0 + cc + e;
+        for (int e = 0; e < 4; ++e) {
+          const int c = c0 + g4 + e;
           const int64_t q = m0 + kLb * a + c;
-          const float rv = q < nr ? d[e] - X[a * kXPitch + c] : 0.0f;
-          const int i = blk_idx(a, c, kRRows);
-          tf32_split(rv, R_hi[i], R_lo[i]);
-          X[a * kXPitch + c] = rv;  // for the coalesced r store
+          rv[e] = q < nr ? d[g4 + e] - X[a * kXPitch + c] : 0.0f;
+          X[a * kXPitch + c] = rv[e];  // for the coalesced r store
         }
+        split_store4(R_hi, R_lo, blk_idx(a, c0 + g4, kRRows), rv[0], rv[1], rv[2], rv[3]);
       }
     }
     fence_proxy_async();
@@ -287,68 +344,83 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
     umma_commit(&bar);
   }
   if (FUSED && ok && r_out) {
-    float* rrow = r_out + (size_t)b * nr;
+    float* rout = r_out + (size_t)b * nr;
     for (int v = tid; v < kChunk; v += kNT) {
       const int64_t q = m0 + v;
-      if (q < nr) rrow[q] = X[(v / kLb) * kXPitch + (v % kLb)];
+      if (q < nr) rout[q] = X[(v / kLb) * kXPitch + (v % kLb)];
     }
   }
 
-  // ---- grad_h partial: P[c][q] = sum_{a<128} s[32a + c] r[32a + q] (warp MMA) ----
-  // m tile mc = warp / 4 (rows c = 16 mc ..); its 10 n tiles (8 columns q
-  // each, from tile 2 mc) go 3, 3, 2, 2 to the four warps of the m tile.
+  // ---- grad_h partial (warp MMA; see the header) ----
   if (ok && part_h) {
     const int g = lane >> 2, t = lane & 3;
-    const int mc = warp >> 2, qw = warp & 3;
-    const int nq0 = 2 * mc + (qw < 2 ? 3 * qw : 2 * qw + 2);
-    const int ntiles = qw < 2 ? 3 : 2;
-    float acc[3][4];
+    float diag[kDiag];  // diag[2 d + bit]: entries with q - c = 8 d + 2 t + bit - g (d < 0 or > 8: never a lag < 64)
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[u][i] = 0.0f;
-    const int c_a = 16 * mc + g, c_b = c_a + 8;
+    for (int i = 0; i < kDiag; ++i) diag[i] = 0.0f;
 #pragma unroll 1
-    for (int kk = 0; kk < kBlocks / 8; ++kk) {
+    for (int kk = 2 * warp; kk < 2 * warp + 2; ++kk) {
       const int a0 = 8 * kk + t, a1 = a0 + 4;  // blocks; s of block a is s row a + 2
-      const int i0 = blk_idx(a0 + 2, c_a, kSRows), i1 = blk_idx(a0 + 2, c_b, kSRows);
-      const int i2 = blk_idx(a1 + 2, c_a, kSRows), i3 = blk_idx(a1 + 2, c_b, kSRows);
-      const uint32_t ah[4] = {__float_as_uint(S_hi[i0]), __float_as_uint(S_hi[i1]), __float_as_uint(S_hi[i2]),
-                              __float_as_uint(S_hi[i3])};
-      const uint32_t al[4] = {__float_as_uint(S_lo[i0]), __float_as_uint(S_lo[i1]), __float_as_uint(S_lo[i2]),
-                              __float_as_uint(S_lo[i3])};
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        if (u < ntiles) {
-          const int q = 8 * (nq0 + u) + g;  // r[32a + q]: row a + q / 32, column q % 32
-          const int j0 = blk_idx(a0 + q / kLb, q % kLb, kRRows), j1 = blk_idx(a1 + q / kLb, q % kLb, kRRows);
-          const uint32_t bh0 = __float_as_uint(R_hi[j0]), bl0 = __float_as_uint(R_lo[j0]);
-          const uint32_t bh1 = __float_as_uint(R_hi[j1]), bl1 = __float_as_uint(R_lo[j1]);
-          mma_m16n8k8(acc[u], al, bh0, bh1);
-          mma_m16n8k8(acc[u], ah, bl0, bl1);
-          mma_m16n8k8(acc[u], ah, bh0, bh1);
+      for (int mc = 0; mc < 2; ++mc) {
+        const int c_a = 16 * mc + g, c_b = c_a + 8;
+        const int i0 = blk_idx(a0 + 2, c_a, kSRows), i1 = blk_idx(a0 + 2, c_b, kSRows);
+        const int i2 = blk_idx(a1 + 2, c_a, kSRows), i3 = blk_idx(a1 + 2, c_b, kSRows);
+        ah[mc][0] = __float_as_uint(S_hi[i0]);
+        ah[mc][1] = __float_as_uint(S_hi[i1]);
+        ah[mc][2] = __float_as_uint(S_hi[i2]);
+        ah[mc][3] = __float_as_uint(S_hi[i3]);
+        al[mc][0] = __float_as_uint(S_lo[i0]);
+        al[mc][1] = __float_as_uint(S_lo[i1]);
+        al[mc][2] = __float_as_uint(S_lo[i2]);
+        al[mc][3] = __float_as_uint(S_lo[i3]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 12; ++nt) {
+        const int q = 8 * nt + g;  // r[32a + q]: row a + q / 32, column q % 32
+        const int j0 = blk_idx(a0 + q / kLb, q % kLb, kRRows), j1 = blk_idx(a1 + q / kLb, q % kLb, kRRows);
+        const uint32_t bh0 = __float_as_uint(R_hi[j0]), bl0 = __float_as_uint(R_lo[j0]);
+        const uint32_t bh1 = __float_as_uint(R_hi[j1]), bl1 = __float_as_uint(R_lo[j1]);
+#pragma unroll
+        for (int mc = 0; mc < 2; ++mc) {
+          const int u = nt - 2 * mc;  // n tile relative to the m tile's band start
+          if (u < 0 || u > 9) continue;
+          float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          mma_m16n8k8(acc, al[mc], bh0, bh1);
+          mma_m16n8k8(acc, ah[mc], bl0, bl1);
+          mma_m16n8k8(acc, ah[mc], bh0, bh1);
+          // element i: c = 16 mc + g + 8 (i >> 1), q = 8 nt + 2 t + (i & 1)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int d = u - (i >> 1);
+            if (d >= 0 && d <= 8) diag[2 * d + (i & 1)] += acc[i];
+          }
         }
       }
     }
-    __syncthreads();  // P[32][129] and the partial sums reuse the s arrays
-    float* P = S_hi;
+    __syncthreads();  // the diagonal sums and their totals reuse the s arrays
+    float* dg = S_hi;  // dg[(warp * kDiag + slot) * 32 + lane]
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
-      if (u < ntiles) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = 16 * mc + g + 8 * (i >> 1), q = 8 * (nq0 + u) + 2 * t + (i & 1);
-          P[c * 129 + q] = acc[u][i];
-        }
-      }
+    for (int i = 0; i < kDiag; ++i) dg[(warp * kDiag + i) * 32 + lane] = diag[i];
     __syncthreads();
-    float* red4 = P + 32 * 129;
+    float* red4 = dg + 8 * kDiag * 32;
     {
-      const int j = tid & 63, quarter = tid >> 6;
+      // lag j collects, from each warp, the lanes (g, t) and parities with
+      // 8 d + bit = j + g - 2 t: g = (bit - j + 2 t) mod 8
+      const int j = tid & 63, part = tid >> 6;
       float tsum = 0.0f;
 #pragma unroll
-      for (int c = 8 * quarter; c < 8 * quarter + 8; ++c) tsum += P[c * 129 + c + j];
-      red4[quarter * 64 + j] = tsum;
+      for (int w = 2 * part; w < 2 * part + 2; ++w)
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt)
+#pragma unroll
+          for (int bit = 0; bit < 2; ++bit) {
+            const int gg = (bit - j + 2 * tt) & 7;
+            const int e = j + gg - 2 * tt;  // = 8 d + bit
+            const int d = (e - bit) / 8;  // e >= 0 when j >= 0, so d in 0 .. 8
+            tsum += dg[(w * kDiag + 2 * d + bit) * 32 + gg * 4 + tt];
+          }
+      red4[part * 64 + j] = tsum;
     }
     __syncthreads();
     float* dst = part_h + ((size_t)b * nchunks + blockIdx.x) * K;
@@ -362,13 +434,10 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, const floa
     ok = __syncthreads_and(ok);  // also: the r store has finished reading X
     if (ok) {
       const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
+      float d[16];
+      tmem_ld16(tmem_warp + kLb + c0, d);
 #pragma unroll
-      for (int cc = 0; cc < 16; cc += 8) {
-        float d[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kLb + c0 + cc, d);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) X[a * kXPitch + c0 + cc + e] = d[e];
-      }
+      for (int e = 0; e < 16; ++e) X[a * kXPitch + c0 + e] = d[e];
     }
     __syncthreads();
     if (ok) {
@@ -397,10 +466,12 @@ int launch_conv_tc(int batch, int64_t n, int k, const float* s, const float* h, 
   dim3 grid(static_cast<unsigned>(nch), static_cast<unsigned>(batch));
   float* part = grad_h ? partials : nullptr;
   auto kern = r_in ? k_conv_tc<false> : k_conv_tc<true>;
+  auto aligned = [](const void* p, int64_t len) { return reinterpret_cast<uintptr_t>(p) % 16 == 0 && len % 4 == 0; };
+  const int vec = (aligned(s, n) ? 1 : 0) | (r_in && aligned(r_in, n + k - 1) ? 2 : 0);
   ADJWT_CUDA_CHECK(set_smem(kern, kSmemBytes));
   ADJWT_TRACED(r_in ? "conv_adjoint" : "conv_gradient", 0, st,
                pdl_launch(kern, grid, kNT, kSmemBytes, st, n, k, s, h, r_in ? nullptr : x, r_in,
-                          r_in ? nullptr : r_out, grad_s, part, static_cast<int>(nch), device_status_ptr()));
+                          r_in ? nullptr : r_out, grad_s, part, static_cast<int>(nch), vec, device_status_ptr()));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   if (grad_h) {
     const int64_t total = (int64_t)batch * k;
