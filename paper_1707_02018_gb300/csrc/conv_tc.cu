@@ -19,8 +19,8 @@
 // matrices B[a'][j] = x[base + 32 a' + j] stored [j/4][a'][4]: each row of a
 // 4-column slab is 16 bytes, so the K range [32 t, 32 t + 32) of W (or V) is
 // the same matrix t rows down (descriptor start + 16 t bytes).  The Toeplitz
-// factors are a band array G[rho][k'] (8 columns) of which K-step kk reads the
-// 32 rows from 88 - 8 kk; the H2 band replaces the H1 band once the first
+// factors are a band array G[rho][k'] (8 columns, rows 0 .. 119) of which
+// K-step kk reads the 32 rows from 88 - 8 kk; the H2 band replaces the H1 band once the first
 // product is done.  The 64 residuals past the chunk (read by grad_s and grad_h
 // of its last two blocks) come from the CUDA cores.  Float32 accuracy: each
 // operand is split into a TF32 high part and the float remainder, and each
@@ -46,7 +46,7 @@ constexpr int kKSteps = (kLb + 64) / 8;  // 12 K-steps of 8
 constexpr int kSRows = kBlocks + 4;      // s rows: s[m0 - 64] .. s[m0 + 4159]
 constexpr int kRNeed = kBlocks + 2;      // r rows read: r[m0] .. r[m0 + 4159]
 constexpr int kRRows = kBlocks + 4;      // r slab pitch (rows); 132 = 4 mod 8 keeps the fragment reads conflict-free
-constexpr int kGRows = 120;              // band rows: 31 + 88 + 1
+constexpr int kGRows = 124;              // band slab pitch (rows 0 .. 119 used); 124 = 4 mod 8: conflict-free stores
 constexpr int kGOff = 88;                // K-step kk reads band rows kGOff - 8 kk ..
 constexpr int kRawPitch = kLb + 4;       // raw x / r rows: 16-byte reads of a column are conflict-free
 constexpr int kOutPitch = kLb + 1;       // grad_s staging tile pitch (conflict-free column writes)
@@ -66,7 +66,7 @@ constexpr int kTotal = kSLin + 128;
 constexpr int kDiag = 18;                // diagonal sums per thread: d = 0 .. 8, two parities
 constexpr size_t kSmemBytes = 128 + (size_t)kTotal * 4;
 static_assert(kSmemBytes <= 113 * 1024, "two CTAs per SM");
-static_assert(8 * kDiag * 32 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
+static_assert(8 * kDiag * 36 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
 static_assert(kBlocks * kOutPitch <= kRRows * kLb, "grad_s staging fits in the r array");
 constexpr uint32_t kTmemCols = 64;
 
@@ -154,6 +154,15 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* st
   if (mbar_wait(bar, parity)) return true;
   record_status(status, ADJWT_ERR_TIMEOUT);
   return false;
+}
+
+// Block-wide wait for a product: thread 0 polls the barrier (bounded), the
+// others wait at the block barrier; true for every thread if it completed.
+__device__ __forceinline__ bool block_wait_product(uint64_t* bar, uint32_t parity, int* status) {
+  const bool ok = threadIdx.x == 0 ? wait_bar(bar, parity, status) : true;
+  const bool all = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return all;
 }
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src, uint32_t src_bytes) {
@@ -324,13 +333,13 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
         umma_commit(&bar);
       }
       // meanwhile the CUDA cores form r on the 64 positions past the chunk
-      // (r rows 128 and 129): four threads per position, 16 taps each
+      // (r rows 128 and 129): four threads per position, taps i = quarter mod 4
       {
         const int e = tid >> 2, quarter = tid & 3;
         float acc = 0.0f;
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-          const int i = 16 * quarter + t;
+          const int i = 4 * t + quarter;
           acc = fmaf(h_sm[i], s_lin[e + 64 - i], acc);  // s[m0 + 4096 + e - i]
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -345,10 +354,8 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
           if (last && r_out && p < kChunk + K - 1 && q < nr) r_out[(size_t)b * nr + q] = rv;
         }
       }
-      ok = wait_bar(&bar, phase, status);
+      ok = block_wait_product(&bar, phase, status);
       phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      ok = __syncthreads_and(ok);
       if (!ok) break;
       {
         const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
@@ -441,11 +448,11 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
         }
       }
       __syncthreads();  // the diagonal sums and their totals reuse the s arrays
-      float* dg = S_hi;  // dg[(warp * kDiag + slot) * 32 + lane]
+      float* dg = S_hi;  // dg[(warp * kDiag + slot) * 36 + 8 t + g]: conflict-free both ways
 #pragma unroll
-      for (int i = 0; i < kDiag; ++i) dg[(warp * kDiag + i) * 32 + lane] = diag[i];
+      for (int i = 0; i < kDiag; ++i) dg[(warp * kDiag + i) * 36 + 8 * t + g] = diag[i];
       __syncthreads();
-      float* red4 = dg + 8 * kDiag * 32;
+      float* red4 = dg + 8 * kDiag * 36;
       {
         // lag j collects, from each warp, the lanes (g, t) and parities with
         // 8 d + bit = j + g - 2 t: g = (bit - j + 2 t) mod 8
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
               const int gg = (bit - j + 2 * tt) & 7;
               const int e = j + gg - 2 * tt;  // = 8 d + bit >= 0
               const int d = (e - bit) / 8;    // 0 .. 8 for j < 64
-              tsum += dg[(w * kDiag + 2 * d + bit) * 32 + gg * 4 + tt];
+              tsum += dg[(w * kDiag + 2 * d + bit) * 36 + 8 * tt + gg];
             }
         red4[part * 64 + j] = tsum;
       }
@@ -471,10 +478,8 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
 
     // ---- grad_s out of tensor memory, staged in the (now free) r array ----
     if (grad_s) {
-      ok = wait_bar(&bar, phase, status);
+      ok = block_wait_product(&bar, phase, status);  // the barrier also ends grad_h's and the r store's reads of r
       phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      ok = __syncthreads_and(ok);  // also: grad_h and the r store are done with the r array
       if (!ok) break;
       float* out_t = R_hi;
       {
