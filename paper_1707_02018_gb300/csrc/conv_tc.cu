@@ -20,11 +20,15 @@
 // 4-column slab is 16 bytes, so the K range [32 t, 32 t + 32) of W (or V) is
 // the same matrix t rows down (descriptor start + 16 t bytes).  The Toeplitz
 // factors are a band array G[rho][k'] (8 columns, rows 0 .. 119) of which
-// K-step kk reads the 32 rows from 88 - 8 kk; the H2 band replaces the H1 band once the first
-// product is done.  The 64 residuals past the chunk (read by grad_s and grad_h
-// of its last two blocks) come from the CUDA cores.  Float32 accuracy: each
-// operand is split into a TF32 high part and the float remainder, and each
-// K-step issues lo*hi, hi*lo and hi*hi.
+// K-step kk reads the 32 rows from 88 - 8 kk; the H2 band replaces the H1
+// band once the first product is done.  The 64 residuals past the chunk (read
+// by grad_s and grad_h of its last two blocks) come from the CUDA cores.
+// Float32 accuracy: each operand is split into a TF32 high part and the float
+// remainder (x = x_hi + x_lo), and a product is A_hi B_hi + A_hi B_lo +
+// A_lo B_hi.  The band array stores the hi and lo halves of each 8-row group
+// side by side, so one N = 64 MMA forms A_hi B_hi and A_hi B_lo (columns
+// 16 (c/8) + c%8 and 16 (c/8) + 8 + c%8) and an N = 32 MMA over every other
+// group forms A_lo B_hi: two MMAs and two reads of the A tile per K-step.
 //
 // CTAs are persistent (two per SM, about 110 KB of shared memory each) and
 // walk the chunks in a grid-stride loop; cp.async brings the next chunk's raw
@@ -46,7 +50,8 @@ constexpr int kKSteps = (kLb + 64) / 8;  // 12 K-steps of 8
 constexpr int kSRows = kBlocks + 4;      // s rows: s[m0 - 64] .. s[m0 + 4159]
 constexpr int kRNeed = kBlocks + 2;      // r rows read: r[m0] .. r[m0 + 4159]
 constexpr int kRRows = kBlocks + 4;      // r slab pitch (rows); 132 = 4 mod 8 keeps the fragment reads conflict-free
-constexpr int kGRows = 124;              // band slab pitch (rows 0 .. 119 used); 124 = 4 mod 8: conflict-free stores
+constexpr int kGGroups = 15;             // band row groups of 8 (rows 0 .. 119)
+constexpr int kGSlab = 2 * kGGroups * 32 + 16;  // floats per 4-column band slab: hi, lo groups side by side; +16 spreads the banks
 constexpr int kGOff = 88;                // K-step kk reads band rows kGOff - 8 kk ..
 constexpr int kRawPitch = kLb + 4;       // raw x / r rows: 16-byte reads of a column are conflict-free
 constexpr int kOutPitch = kLb + 1;       // grad_s staging tile pitch (conflict-free column writes)
@@ -57,8 +62,7 @@ constexpr int kS_LO = kS_HI + kSRows * kLb;
 constexpr int kR_HI = kS_LO + kSRows * kLb;
 constexpr int kR_LO = kR_HI + kRRows * kLb;
 constexpr int kG_HI = kR_LO + kRRows * kLb;
-constexpr int kG_LO = kG_HI + kGRows * 8;
-constexpr int kSRaw = kG_LO + kGRows * 8;              // s[m0 - 64 .. m0 + 4160), linear
+constexpr int kSRaw = kG_HI + 2 * kGSlab;              // s[m0 - 64 .. m0 + 4160), linear
 constexpr int kXRaw = kSRaw + kSRows * kLb;            // x (or r) rows of kRawPitch
 constexpr int kH = kXRaw + (kRNeed * kRawPitch + 31) / 32 * 32;  // two tap buffers (current, next)
 constexpr int kSLin = kH + 128;          // s[m0 + 4032] .. s[m0 + 4159] (taps of the 64 tail residuals)
@@ -68,7 +72,7 @@ constexpr size_t kSmemBytes = 128 + (size_t)kTotal * 4;
 static_assert(kSmemBytes <= 113 * 1024, "two CTAs per SM");
 static_assert(8 * kDiag * 36 + 4 * 64 <= kR_HI, "grad_h scratch fits in the s arrays");
 static_assert(kBlocks * kOutPitch <= kRRows * kLb, "grad_s staging fits in the r array");
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 256;  // per product: A_hi (B_hi|B_lo) in 64 columns, A_lo B_hi in 32
 
 __host__ __device__ constexpr int blk_idx(int row, int j, int rows) { return ((j >> 2) * rows + row) * 4 + (j & 3); }
 
@@ -88,19 +92,34 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor: f32 accumulate, tf32 A and B, both K-major, N = 32, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kLb >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptors: f32 accumulate, tf32 A and B, both K-major, M = 128, N = 64 or 32
+__host__ __device__ constexpr uint32_t idesc_n(uint32_t n) { return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
@@ -113,6 +132,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The 16 product values of row a = 32 (warp % 4) + lane, columns c0 .. c0 + 15
+// (c0 = 16 (warp / 4)), of the product accumulated at tensor memory column col.
+__device__ __forceinline__ void product_row16(uint32_t tmem_warp, uint32_t col, int c0, float (&v)[16]) {
+  float both[32], lo_hi[16];
+  tmem_ld32(tmem_warp + col + 2 * c0, both);  // c in [c0, c0 + 16): columns 16 (c/8) + c%8 (+ 8 for A_hi B_lo)
+  tmem_ld16(tmem_warp + col + 64 + c0, lo_hi);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = (both[16 * (e >> 3) + 8 + (e & 7)] + lo_hi[e]) + both[16 * (e >> 3) + (e & 7)];
 }
 
 // hi/lo split of four consecutive columns into one 16-byte slab row each
@@ -133,20 +162,20 @@ __device__ __forceinline__ void mma_m16n8k8(float (&d)[4], const uint32_t (&a)[4
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One product (36 MMAs: 12 K-steps x lo*hi, hi*lo, hi*hi) into tmem_d.
-// X: block matrix with slab pitch `rows` (hi at xh, lo at xl); G: band arrays.
-__device__ __forceinline__ void issue_product(uint32_t tmem_d, uint32_t xh, uint32_t xl, int rows, uint32_t gh,
-                                              uint32_t gl) {
-  const uint32_t lbo_x = rows * 16, lbo_g = kGRows * 16;
+// One product (24 MMAs: 12 K-steps x A_hi (B_hi|B_lo), A_lo B_hi) into tensor
+// memory columns tmem_d .. + 63 and tmem_d + 64 .. + 95.  X: block matrix with
+// slab pitch `rows` (hi at xh, lo at xl); g: the interleaved band array.
+__device__ __forceinline__ void issue_product(uint32_t tmem_d, uint32_t xh, uint32_t xl, int rows, uint32_t g) {
+  const uint32_t lbo_x = rows * 16, lbo_g = kGSlab * 4;
 #pragma unroll 1
   for (int kk = 0; kk < kKSteps; ++kk) {
     const uint32_t aoff = 2 * (kk & 3) * lbo_x + 16 * (kk >> 2);
-    const uint32_t boff = (kGOff - 8 * kk) * 16;
+    const uint32_t boff = (kGOff / 8 - kk) * 256;  // hi half of row group 11 - kk
     const uint64_t ah = umma_desc(xh + aoff, lbo_x, 128), al = umma_desc(xl + aoff, lbo_x, 128);
-    const uint64_t bh = umma_desc(gh + boff, lbo_g, 128), bl = umma_desc(gl + boff, lbo_g, 128);
-    umma_tf32(tmem_d, al, bh, kk > 0);
-    umma_tf32(tmem_d, ah, bl, 1);
-    umma_tf32(tmem_d, ah, bh, 1);
+    const uint64_t b_both = umma_desc(g + boff, lbo_g, 128);  // groups hi, lo, hi, lo, ...: N = 64
+    const uint64_t b_hi = umma_desc(g + boff, lbo_g, 256);    // hi groups only: N = 32
+    umma_tf32(tmem_d, ah, b_both, idesc_n(64), kk > 0);
+    umma_tf32(tmem_d + 64, al, b_hi, idesc_n(32), kk > 0);
   }
 }
 
@@ -218,14 +247,15 @@ __device__ __forceinline__ void fetch_rows(float* x_raw, const float* row, int64
 }
 
 // Toeplitz band for product 1 (G[rho][k'] = h[rho - k' - 24]) or product 2
-// (G[rho][k'] = h[k' - rho + 88]), split hi/lo.
-__device__ __forceinline__ void build_band(float* G_hi, float* G_lo, const float* h_sm, bool second, int tid) {
-  for (int i = tid; i < kGRows * 8; i += kNT) {
+// (G[rho][k'] = h[k' - rho + 88]), split hi/lo: slab k'/4, row group rho/8
+// with its hi half at 32-float slot 2 (rho/8) and its lo half at the next slot.
+__device__ __forceinline__ void build_band(float* G, const float* h_sm, bool second, int tid) {
+  for (int i = tid; i < kGGroups * 64; i += kNT) {
     const int rho = i >> 3, kq = i & 7;
     const int ti = second ? kq - rho + kGOff : rho - kq - (kGOff - 64);
     const float g = (ti >= 0 && ti < 64) ? h_sm[ti] : 0.0f;
-    const int o = blk_idx(rho, kq, kGRows);
-    tf32_split(g, G_hi[o], G_lo[o]);
+    const int o = (kq >> 2) * kGSlab + (rho >> 3) * 64 + (rho & 7) * 4 + (kq & 3);
+    tf32_split(g, G[o], G[o + 32]);
   }
 }
 
@@ -251,8 +281,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
   float* S_lo = sm + kS_LO;
   float* R_hi = sm + kR_HI;
   float* R_lo = sm + kR_LO;
-  float* G_hi = sm + kG_HI;
-  float* G_lo = sm + kG_LO;
+  float* G = sm + kG_HI;
   float* s_raw = sm + kSRaw;
   float* x_raw = sm + kXRaw;
   float* s_lin = sm + kSLin;
@@ -316,7 +345,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
         split_store4(R_hi, R_lo, blk_idx(u / kLb, u % kLb, kRRows), v.x, v.y, v.z, v.w);
       }
     }
-    build_band(G_hi, G_lo, h_sm, !FUSED, tid);
+    build_band(G, h_sm, !FUSED, tid);
     operands_ready();
     // the raw s (and raw r) buffers are free: fetch the next chunk's
     if (has_next) {
@@ -327,9 +356,9 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
     cp_async_commit();
 
     if (FUSED) {
-      // ---- r = h * s - x: product 1 into tmem columns [0, 32) ----
+      // ---- r = h * s - x: product 1 into tmem columns [0, 96) ----
       if (tid == 0) {
-        issue_product(tmem, base + kS_HI * 4, base + kS_LO * 4, kSRows, base + kG_HI * 4, base + kG_LO * 4);
+        issue_product(tmem, base + kS_HI * 4, base + kS_LO * 4, kSRows, base + kG_HI * 4);
         umma_commit(&bar);
       }
       // meanwhile the CUDA cores form r on the 64 positions past the chunk
@@ -360,7 +389,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
       {
         const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
         float d[16];
-        tmem_ld16(tmem_warp + c0, d);
+        product_row16(tmem_warp, 0, c0, d);
 #pragma unroll
         for (int g4 = 0; g4 < 16; g4 += 4) {
           const float4 xv = *reinterpret_cast<const float4*>(x_raw + a * kRawPitch + c0 + g4);
@@ -374,15 +403,15 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
           split_store4(R_hi, R_lo, blk_idx(a, c0 + g4, kRRows), rv[0], rv[1], rv[2], rv[3]);
         }
       }
-      build_band(G_hi, G_lo, h_sm, true, tid);  // product 1 has finished reading the first band
+      build_band(G, h_sm, true, tid);  // product 1 has finished reading the first band
       operands_ready();
       if (has_next) fetch_rows(x_raw, x ? x + (size_t)nb * nr : nullptr, nr, nm0, kBlocks, vec_x, tid);
       cp_async_commit();
     }
 
-    // ---- grad_s: product 2 into tmem columns [32, 64), overlapped with grad_h ----
+    // ---- grad_s: product 2 into tmem columns [128, 224), overlapped with grad_h ----
     if (grad_s && tid == 0) {
-      issue_product(tmem + kLb, base + kR_HI * 4, base + kR_LO * 4, kRRows, base + kG_HI * 4, base + kG_LO * 4);
+      issue_product(tmem + 128, base + kR_HI * 4, base + kR_LO * 4, kRRows, base + kG_HI * 4);
       umma_commit(&bar);
     }
     if (FUSED && r_out) {
@@ -485,7 +514,7 @@ __global__ void __launch_bounds__(kNT, 2) k_conv_tc(int64_t n, int K, int batch,
       {
         const int a = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
         float d[16];
-        tmem_ld16(tmem_warp + kLb + c0, d);
+        product_row16(tmem_warp, 128, c0, d);
 #pragma unroll
         for (int e = 0; e < 16; ++e) out_t[a * kOutPitch + c0 + e] = d[e];
       }
