@@ -90,6 +90,42 @@ def test_one_gradient_only_and_empty(adj, k):
     assert gh.numel() == 0 and gs.numel() == 0
 
 
+@pytest.mark.parametrize("k", [17, 64])
+def test_fused_gradient_one_output(adj, k):
+    """conv_gradient asked for grad_h alone or grad_s alone (the tensor-core
+    kernel then skips its second product or the grad_h pass)."""
+    B, n = 3, 9000
+    p = channel_problem(B, n, k, seed=k + 5)
+    x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
+    r = oconv.conv_full(p["h_est"], p["s_est"]) - x
+    wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r)
+    gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x), grad_s=False)
+    assert gs is None
+    assert_close(gh.cpu().numpy(), wh, what=f"grad_h alone k={k}")
+    gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x), grad_h=False)
+    assert gh is None
+    assert_close(gs.cpu().numpy(), ws, what=f"grad_s alone k={k}")
+
+
+@pytest.mark.parametrize("B,n,k", [(2, 8192, 61), (2, 8190, 63), (3, 8191, 62), (2, 8189, 60)])
+def test_row_length_load_paths(adj, B, n, k):
+    """Rows of s and of x / r are fetched 16 bytes at a time when their
+    length is a multiple of 4 and 4 bytes at a time otherwise: (s, x) lengths
+    (8192, 8252) both wide, (8190, 8252) and (8191, 8252) x wide only,
+    (8189, 8248) x wide only as well; the residual r of conv_adjoint has the
+    length of x."""
+    p = channel_problem(B, n, k, seed=n + k)
+    x = oconv.conv_full(p["h"], p["s"]) + p["noise"]
+    r = oconv.conv_full(p["h_est"], p["s_est"]) - x
+    wh, ws = oconv.conv_adjoint(p["s_est"], p["h_est"], r)
+    gh, gs = adj.conv_gradient(dev(p["s_est"]), dev(p["h_est"]), dev(x))
+    assert_close(gh.cpu().numpy(), wh, what=f"fused grad_h {B}x{n}x{k}")
+    assert_close(gs.cpu().numpy(), ws, what=f"fused grad_s {B}x{n}x{k}")
+    gh, gs = adj.conv_adjoint(dev(p["s_est"]), dev(p["h_est"]), dev(r))
+    assert_close(gh.cpu().numpy(), wh, what=f"grad_h {B}x{n}x{k}")
+    assert_close(gs.cpu().numpy(), ws, what=f"grad_s {B}x{n}x{k}")
+
+
 def test_full_size_256x65536x64(adj):
     """The bench workload (256 signals of 65,536 samples, 64-tap channels), in full."""
     p = channel_problem(256, 65536, 64, seed=2)
