@@ -295,6 +295,14 @@ class Fista:
     def set_lipschitz(self, L):
         self.problem.lipschitz = float(L)
 
+    def set_observation(self, b):
+        """Point the problem at another observation image b (same plan layout);
+        later calls read it, so a caller can double-buffer its input copies."""
+        if tuple(b.shape) != tuple(self.b.shape) or b.dtype != self.b.dtype or not b.is_cuda:
+            raise ValueError("set_observation: b must match the plan's image layout")
+        self.b = b
+        self.problem.b = b.data_ptr()
+
     def reset(self, x0=None):
         self.x.zero_()
         if x0 is not None:
