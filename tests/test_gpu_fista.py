@@ -120,6 +120,23 @@ def test_objective_api(adj):
     assert abs(Fg - prob.objective(x)) <= 1e-5 * prob.objective(x)
 
 
+def test_set_observation_switches_b(adj):
+    """A problem pointed at a second observation buffer (set_observation)
+    iterates exactly like one built on it; a layout mismatch is refused."""
+    prob, wt, bl, db = _setup(adj, 96, 128, 3, "db2", "sym", 5, 1.0, 2e-3, 21)
+    _, _, _, db2 = _setup(adj, 96, 128, 3, "db2", "sym", 5, 1.0, 2e-3, 22)
+    f = adj.Fista(wt, bl, db2, 2e-3, 1.05)
+    g = adj.Fista(wt, bl, db, 2e-3, 1.05)
+    g.set_observation(db2)
+    for _ in range(4):
+        f.step()
+        g.step()
+    torch.cuda.synchronize()
+    assert torch.equal(f.x, g.x) and torch.equal(f.y, g.y)
+    with pytest.raises(ValueError):
+        g.set_observation(torch.zeros(3, 3, device="cuda"))
+
+
 def test_full_size_two_steps_sym(adj):
     """2048^2, CDF 9/7 J=5, symmetric BC, 15x15 sigma=3: two steps against the oracle."""
     rows = cols = 2048
