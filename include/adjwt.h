@@ -257,6 +257,43 @@ int adjwt_fista_objective(const adjwt_fista_problem* prob, const float* x, void*
 int adjwt_fista_lipschitz(const adjwt_fista_problem* prob, float* v, int iters, void* ws, size_t ws_bytes,
                           double* lipschitz_out, adjwt_stream_t stream);
 
+/* ------------------------------------------------------ differentiation
+ * Pieces for differentiating through the FISTA iteration (unrolled FISTA;
+ * gradients with respect to lambda, the PSF width sigma and the data b).
+ * The backward of x_{k+1} = S_tau(y_k - (1/L) A^*(A y_k - b)), A = R W
+ * (Sec. 1, Eq. 1), applies A and A^* themselves (the chain rule
+ * A^* grad l(A x) of Sec. 1, correct only with the exact adjoint) plus the
+ * elementwise steps below.  None has a counterpart in the paper beyond that.
+ *
+ * adjwt_gaussian_taps (HOST): taps[i] = e_i / sum_j e_j,
+ * e_i = exp(-(i - (k-1)/2)^2 / (2 sigma^2)), and, if dtaps_dsigma is not
+ * NULL, its derivative dtaps[i] = taps[i] (d_i^2 - sum_j taps[j] d_j^2) /
+ * sigma^3 (host arrays of k doubles).  For the separable PSF g (x) g,
+ * dR/dsigma = R[g', g] + R[g, g'] (two blur plans).  SHAPE unless k is odd
+ * and >= 1; INVALID_ARG unless sigma > 0.
+ *
+ * adjwt_axpby: out[i] = a x[i] + b y[i], i < n (device float32; out may
+ * alias x or y).
+ *
+ * adjwt_dot: *out_dev (DEVICE double) = sum over rows x cols of x y, both
+ * arrays with row pitch `pitch` floats (a coefficient vector: rows = 1,
+ * cols = pitch = length).  Float64 per-block partials, added in a fixed
+ * order (reproducible).  ws: device scratch of adjwt_reduce_workspace_size()
+ * bytes (WORKSPACE if smaller or NULL).
+ *
+ * fista_prox_vjp: vector-Jacobian product of the soft threshold
+ * x_{k+1} = S_tau(z): zbar[i] = xbar[i] if x_next[i] != 0 else 0 (S_tau(z) is
+ * zero exactly where |z| <= tau), and *sign_dot_dev (DEVICE double) =
+ * sum_i sign(x_next[i]) xbar[i], so that dl/dtau = -(*sign_dot_dev).  zbar
+ * may alias xbar.  ws as for adjwt_dot. */
+int adjwt_gaussian_taps(int k, double sigma, double* taps, double* dtaps_dsigma);
+size_t adjwt_reduce_workspace_size(void);
+int adjwt_axpby(int64_t n, float a, const float* x, float b, const float* y, float* out, adjwt_stream_t stream);
+int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* out_dev, void* ws,
+              size_t ws_bytes, adjwt_stream_t stream);
+int fista_prox_vjp(int64_t n, const float* x_next, const float* xbar, float* zbar, double* sign_dot_dev, void* ws,
+                   size_t ws_bytes, adjwt_stream_t stream);
+
 /* ------------------------------------------------------------------- tracing
  * Optional per-kernel device timing without a profiler (the paper has no
  * counterpart; it serves the measurement harness).  adjwt_trace_enable(n)

@@ -20,6 +20,8 @@ Modules
   blur       -- Gaussian PSF, R and R^* (Sec. I, the gradient after Eq. 1).
   conv       -- full convolution and its adjoints (Sec. II, Eq. 5).
   fista      -- objective, power-iteration step size and FISTA (Sec. I-B).
+  unrolled   -- unrolled FISTA and its reverse-mode derivative with respect to
+                lambda, the PSF width and b (the chain rule of Sec. I).
   layout     -- band sizes and the packed coefficient order.
 
 Every function states the passage it follows.  Functions whose result cannot
@@ -27,4 +29,4 @@ be pinned independently say "parity unpinned" in their docstring; at present
 every function has at least one independent pin in ``tests/test_oracle_*``.
 """
 
-from . import filters, extension, layout, wavelet, blur, conv, fista  # noqa: F401
+from . import filters, extension, layout, wavelet, blur, conv, fista, unrolled  # noqa: F401

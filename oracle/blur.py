@@ -31,6 +31,18 @@ def gaussian_psf(k: int, sigma: float) -> np.ndarray:
     return p / p.sum()
 
 
+def gaussian_psf_dsigma(k: int, sigma: float) -> np.ndarray:
+    """d/dsigma of gaussian_psf(k, sigma): with q_i the normalised taps and
+    d_i = i - c, dq_i/dsigma = q_i (d_i^2 - sum_j q_j d_j^2) / sigma^3
+    (quotient rule on e_i / sum e, de_i/dsigma = e_i d_i^2 / sigma^3).  The
+    separable PSF q (x) q then has derivative q' (x) q + q (x) q'; R is
+    linear in its taps, so dR/dsigma u = blur(u, q', q) + blur(u, q, q')."""
+    q = gaussian_psf(k, sigma)
+    c = (k - 1) / 2.0
+    d2 = (np.arange(k, dtype=np.float64) - c) ** 2
+    return q * (d2 - float(np.sum(q * d2))) / sigma ** 3
+
+
 def _bc(bc):
     return "sym" if bc == "sym" else ("per" if bc == "per" else "zero")
 

@@ -348,6 +348,59 @@ class Fista:
         return out.value
 
 
+# ------------------------------------------------------------ differentiation
+def gaussian_taps(k, sigma):
+    """(taps, d taps / d sigma) of the normalised k-tap Gaussian (host lists)."""
+    taps, dt = (C.c_double * k)(), (C.c_double * k)()
+    _lib.check(lib().adjwt_gaussian_taps(int(k), float(sigma), taps, dt))
+    return list(taps), list(dt)
+
+
+def axpby(a, x, b, y, out=None, stream=None):
+    """out = a x + b y (float32 device tensors of one length)."""
+    if x.numel() != y.numel():
+        raise ValueError("axpby: x and y differ in length")
+    out = torch.empty_like(x) if out is None else out
+    _need(out, x.numel(), "out")
+    _lib.check(lib().adjwt_axpby(x.numel(), float(a), _ptr(x), float(b), _ptr(y), _ptr(out), _stream(stream)))
+    return out
+
+
+_reduce_ws = {}
+
+
+def _reduce_scratch(device):
+    key = torch.device(device).index
+    if key not in _reduce_ws:
+        _reduce_ws[key] = workspace(lib().adjwt_reduce_workspace_size(), device=device)
+    return _reduce_ws[key]
+
+
+def dot(x, y, rows=1, cols=None, pitch=None, out=None, stream=None):
+    """<x, y> in float64 into a 1-element device tensor: x and y hold `rows`
+    rows of `cols` values at row pitch `pitch` (default: one flat vector)."""
+    cols = x.numel() if cols is None else cols
+    pitch = cols if pitch is None else pitch
+    _need(x, rows * pitch, "x")
+    _need(y, rows * pitch, "y")
+    out = torch.zeros(1, dtype=torch.float64, device=x.device) if out is None else out
+    ws = _reduce_scratch(x.device)
+    _lib.check(lib().adjwt_dot(rows, cols, pitch, _ptr(x), _ptr(y), _ptr(out), _ptr(ws), ws.numel(),
+                               _stream(stream)))
+    return out
+
+
+def prox_vjp(x_next, xbar, zbar=None, stream=None):
+    """(zbar, s): zbar = xbar where x_next != 0 else 0, s (1-element float64
+    device tensor) = sum sign(x_next) xbar; d loss / d tau = -s."""
+    zbar = torch.empty_like(xbar) if zbar is None else zbar
+    s = torch.zeros(1, dtype=torch.float64, device=xbar.device)
+    ws = _reduce_scratch(xbar.device)
+    _lib.check(lib().fista_prox_vjp(x_next.numel(), _ptr(x_next), _ptr(xbar), _ptr(zbar), _ptr(s), _ptr(ws),
+                                    ws.numel(), _stream(stream)))
+    return zbar, s
+
+
 def fista_step(fista, objective=False, stream=None):
     return fista.step(objective, stream)
 
