@@ -299,6 +299,33 @@ def adjoint_vs_pinv(adj, torch, pr, iters=300):
     return {"iterations": iters, "boundary": pr["bc"], "F_adjoint": fa, "F_pinv": fp, "ratio_pinv_over_adjoint": fp / fa}
 
 
+def unrolled_gradient_timing(adj, torch, pr, steps=10, reps=3):
+    """Seconds for `steps` plain FISTA iterations and for the gradient of
+    l = 1/2 ||W x_N - u||^2 with respect to (lambda, sigma, b) through them
+    (forward with checkpoints, recomputed segments, reverse mode), on the
+    2048^2 SYM problem; best of `reps`."""
+    from paper_1707_02018_gb300.unrolled import UnrolledFista
+    f = pr["fista"]
+    un = UnrolledFista(SIZE, SIZE, LEVELS, WAVELET, "sym", PSF_K, PSF_SIGMA, "sym", pr["b"], LAM,
+                       f.problem.lipschitz)
+    u_ref = pr["b"].clone()
+    un.grads(steps, u_ref)  # warm-up (plans, allocations)
+    fwd, full = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        un.solve(steps)
+        torch.cuda.synchronize()
+        fwd.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        un.grads(steps, u_ref)
+        torch.cuda.synchronize()
+        full.append(time.perf_counter() - t0)
+    return {"steps": steps, "size": SIZE, "boundary": "sym", "forward_sec": min(fwd), "gradient_sec": min(full),
+            "gradient_over_forward": min(full) / min(fwd),
+            "wrt": "lambda, sigma (Gaussian PSF width), b; checkpoints every floor(sqrt(steps)) iterations"}
+
+
 # Batched solves: independent deblurring problems of uneven sizes, depths,
 # wavelets and PSF widths (symmetric boundaries), all to the same relative
 # objective tolerance.
@@ -554,6 +581,7 @@ def ours(args):
         extra["fista_sec_to_1e-4"] = fista_time_to_tol(adj, torch, probs[1])
         extra["fista_batched_vs_plain_to_1e-4"] = batched_vs_plain(adj, torch)
         extra["fista_adjoint_vs_pinv"] = adjoint_vs_pinv(adj, torch, probs[1])
+        extra["unrolled_fista_gradient"] = unrolled_gradient_timing(adj, torch, probs[1])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
