@@ -30,6 +30,11 @@ sys.path.insert(0, ROOT)
 SIZE, LEVELS, WAVELET = 2048, 5, "cdf97"
 PSF_K, PSF_SIGMA, LAM, NOISE = 15, 3.0, 1e-3, 1e-3
 BCS = ("per", "sym", "zero")
+# bench.py --autotune measures the TMA / tiled choice per wavelet level first
+# (adjwt_wt_plan_autotune, each transform timed alone).  Off by default: the
+# serially measured choice (tiled kernels for the level-1 W^* + prox) cuts the
+# serial kernel time but makes this four-stream step slower.
+AUTOTUNE = False
 CH_B, CH_N, CH_K = 256, 65536, 64
 METRIC = "W/W* HBM GB/s; FISTA sec to 1e-4 rel objective, learned/batched vs plain"
 WORKLOAD = ("FISTA iteration on 2048x2048, 5-level CDF 9/7, PER+SYM+ZERO boundaries, 15x15 Gaussian PSF "
@@ -139,6 +144,8 @@ def build_workload(adj, torch, rank):
     for i, bc in enumerate(BCS):
         seed = 2000 + 10 * rank + i
         wt = adj.WtPlan(SIZE, SIZE, LEVELS, WAVELET, bc)
+        if AUTOTUNE:
+            wt.autotune(reps=5)  # plan-time choice of TMA / tiled kernels per level (untimed setup)
         bl = adj.BlurPlan(SIZE, SIZE, p, p, bc)
         img = wt.image(torch.as_tensor(piecewise_smooth_image(SIZE, SIZE, seed)))
         b = adj.blur(bl, img)
@@ -591,7 +598,9 @@ def ours(args):
                        "boundaries": list(BCS), "psf": [PSF_K, PSF_SIGMA], "channels": [CH_B, CH_N, CH_K],
                        "parallelism": f"replicas x{world} (independent problems per rank)",
                        "l2": "inputs larger than L2: ~540 MB touched per step vs 129 MB L2",
-                       "bytes_per_step": bytes_step},
+                       "bytes_per_step": bytes_step,
+                       "level_kernels": {pr["bc"]: {"tma": pr["wt"].tma_levels(), "autotuned": AUTOTUNE}
+                                         for pr in probs}},
             "roofline": roof, "hbm_rooflines": hbm_roofs, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps,
@@ -689,7 +698,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
+    ap.add_argument("--autotune", action="store_true", help="measure the TMA / tiled kernel choice per wavelet level")
     args = ap.parse_args()
+    global AUTOTUNE
+    AUTOTUNE = args.autotune
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -22,7 +22,9 @@
  *    floats; num_coeffs counts the padding.  Padding is ignored on input and
  *    written as 0 on output.
  *  - Plans are created once (they allocate a few KB of device tables), are
- *    immutable, and may be used concurrently from several streams.  Hot calls
+ *    immutable apart from the level-implementation switches of wavelet
+ *    plans (set before use), and may be used concurrently from several
+ *    streams.  Hot calls
  *    allocate nothing: scratch comes from a caller-provided workspace of at
  *    least *_workspace_size bytes (256-byte aligned).
  *  - Out-of-place only: an output that overlaps an input -> ADJWT_ERR_ALIAS.
@@ -116,6 +118,30 @@ int wt_synth_adjoint(const adjwt_wt_plan* plan, const float* image, float* coeff
  * The "pseudoinverse approximation" of W^* discussed in Sec. I-B. */
 int wt_analysis(const adjwt_wt_plan* plan, const float* image, float* coeffs, void* ws, size_t ws_bytes,
                 adjwt_stream_t stream);
+
+/* Level implementations.  A level of W (op 0), of W^* / W^dagger (op 1) or
+ * of W^* with the FISTA prox epilogue (op 2, a kernel of its own: it also
+ * reads and writes the iterate) runs either on the persistent TMA-staged
+ * kernel, which takes the tiles a size rule gives it (levels of at least
+ * 256 x 512; shared with the tiled kernel only from 1536 x 1536), with the
+ * tiled kernel on the rest, or on the tiled kernel alone.  Results agree
+ * within float32 rounding either way.  adjwt_wt_plan_set_tma(plan, op,
+ * level, 0) forces the tiled kernel for that level, 1 restores the rule;
+ * adjwt_wt_plan_uses_tma reports whether the TMA kernel runs there.
+ * adjwt_wt_plan_autotune measures: for every level the rule makes eligible
+ * it times `reps` whole transforms (W, W^*, then W^* with the prox on
+ * scratch iterates) with the level one way and the other, keeps the tiled
+ * kernel only if it is at least 3 % faster, and stores the choices for the
+ * plan's size class (rows, cols, levels, wavelet, boundary, current device);
+ * plans created later for that class start from them, and autotuning such a
+ * class again only applies them (*from_cache = 1; from_cache may be NULL).
+ * It allocates and frees its own device buffers and synchronises the
+ * stream.  These calls change the plan: make them before the plan is used
+ * on other streams.  Errors: INVALID_ARG (op outside 0..2, reps outside
+ * 1..1000), SHAPE (level outside 1..levels), CUDA. */
+int adjwt_wt_plan_set_tma(adjwt_wt_plan* plan, int op, int level, int enabled);
+int adjwt_wt_plan_uses_tma(const adjwt_wt_plan* plan, int op, int level, int* uses);
+int adjwt_wt_plan_autotune(adjwt_wt_plan* plan, int reps, int* from_cache, adjwt_stream_t stream);
 
 /* ---------------------------------------------------------------------- blur
  * Separable PSF p = outer(taps_r, taps_c) (float64 taps, odd lengths

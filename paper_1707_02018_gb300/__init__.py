@@ -82,6 +82,33 @@ class WtPlan:
             _lib._lib.adjwt_wt_plan_destroy(h)
             self._h = None
 
+    LEVEL_OPS = {"synth": 0, "analysis": 1, "prox": 2}
+
+    def set_tma(self, op, level, enabled):
+        """op "synth" (W), "analysis" (W^*, W^dagger) or "prox" (W^* with the
+        FISTA prox epilogue): run `level` on the TMA kernel under its size rule
+        (enabled) or on the tiled kernel alone."""
+        _lib.check(lib().adjwt_wt_plan_set_tma(self._h, self.LEVEL_OPS[op], int(level), int(enabled)))
+
+    def tma_levels(self):
+        """{"synth", "analysis", "prox": [...]}: per level 1..J, whether the TMA kernel runs."""
+        out = {}
+        for name, op in self.LEVEL_OPS.items():
+            v = C.c_int()
+            row = []
+            for j in range(1, self.levels + 1):
+                _lib.check(lib().adjwt_wt_plan_uses_tma(self._h, op, j, C.byref(v)))
+                row.append(bool(v.value))
+            out[name] = row
+        return out
+
+    def autotune(self, reps=5, stream=None):
+        """Measure the TMA / tiled choice per level (see include/adjwt.h); True
+        if the choices came from an earlier tuning of the same size class."""
+        fc = C.c_int()
+        _lib.check(lib().adjwt_wt_plan_autotune(self._h, int(reps), C.byref(fc), _stream(stream)))
+        return bool(fc.value)
+
     def filters(self):
         arrs = [(C.c_double * 10)() for _ in range(4)]
         L = C.c_int()

@@ -57,6 +57,9 @@ PROTOTYPES = {
     "bce_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, SZ, VP]),
     "fista_step_device": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, SZ, VP, VP]),
     "adjwt_fista_device_reset": (C.c_int, [C.POINTER(FistaProblem), VP, SZ, VP]),
+    "adjwt_wt_plan_set_tma": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
+    "adjwt_wt_plan_uses_tma": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "adjwt_wt_plan_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int), VP]),
     "adjwt_gaussian_taps": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "adjwt_reduce_workspace_size": (SZ, []),
     "adjwt_axpby": (C.c_int, [I64, C.c_float, VP, C.c_float, VP, VP, VP]),

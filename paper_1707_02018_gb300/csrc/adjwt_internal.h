@@ -136,6 +136,11 @@ struct adjwt_wt_plan {
   std::vector<adjwt::Level> lv;       // lv[j-1] = level j
   int64_t ll_buf_floats[2];           // ping-pong LL buffer sizes (odd / even levels)
   float* d_tables = nullptr;          // device copy of all 1/c tables
+  // per operator (0: W, 1: W^* and W^dagger, 2: W^* with the FISTA prox
+  // epilogue) and level: 1 = the level runs on the tiled kernel alone, 0 = the
+  // TMA kernel takes the tiles the size rule gives it (set by
+  // adjwt_wt_plan_set_tma / adjwt_wt_plan_autotune)
+  unsigned char tma_off[3][adjwt::kMaxLevels] = {};
 };
 
 struct adjwt_blur_plan {
@@ -172,7 +177,7 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 // Coefficient rectangle of level j computed by the persistent TMA analysis
 // kernel (W^*, optionally with the prox, or W^dagger), and its launcher;
 // *ncta receives the number of l1 partial slots it wrote.
-void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1, int* c0, int* c1);
+void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, bool prox, int* r0, int* r1, int* c0, int* c1);
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
                    float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
                    const double* beta_dev, double* l1, const float* flo, const float* fhi, const char* name,
@@ -204,6 +209,10 @@ int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b,
 // Deterministic sum of float64 partials: out[0] = scale0 * sum(a[0..na)) + scale1 * sum(b[0..nb)).
 int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,
                         double* out, cudaStream_t s);
+
+// Tuning cache: apply the stored per-level TMA choices of this plan's size
+// class (rows, cols, levels, wavelet, boundary, device), if any.
+void apply_tuning_cache(adjwt_wt_plan* p);
 
 // Convolution family.
 int launch_conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r,

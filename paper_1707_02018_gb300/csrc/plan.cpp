@@ -141,6 +141,7 @@ extern "C" int adjwt_wt_plan_create(adjwt_wt_plan** out, int rows, int cols, int
     }
     for (auto& w : where) p->lv[w.first / 2].ax[w.first % 2].winv = p->d_tables + w.second;
   }
+  apply_tuning_cache(p);
   *out = p;
   return ADJWT_OK;
 }

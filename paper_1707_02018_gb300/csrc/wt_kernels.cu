@@ -770,7 +770,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     a.tiles_c = grid.x;
     a.tiles_r = grid.y;
     int r0, r1, c0, c1;  // coefficient rectangle of the TMA kernel
-    ana_tma_rect(p, j, adjoint, &r0, &r1, &c0, &c1);
+    ana_tma_rect(p, j, adjoint, prox.x != nullptr, &r0, &r1, &c0, &c1);
     if (r1 > r0) {
       a.in_r0 = r0 / kTile;
       a.in_r1 = r1 / kTile;

@@ -296,6 +296,7 @@ int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[4], cudaStream_t s, 
 // TMA kernel (empty when the level is small); the tiled kernel skips it.
 void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1) {
   *r0 = *r1 = *c0 = *c1 = 0;
+  if (p->tma_off[0][j - 1]) return;
   const Level& L = p->lv[j - 1];
   if (L.generic_synth || L.ax[0].N < 256 || L.ax[1].N < 512) return;
   const bool weighted = L.ax[0].winv != nullptr || p->bc == kPpd;
@@ -620,8 +621,9 @@ int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, co
 
 // Coefficient rectangle [r0, r1) x [c0, c1) of level j's bands computed by
 // the TMA kernel (rows aligned to 32, columns to 64; empty for small levels).
-void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, int* r0, int* r1, int* c0, int* c1) {
+void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, bool prox, int* r0, int* r1, int* c0, int* c1) {
   *r0 = *r1 = *c0 = *c1 = 0;
+  if (p->tma_off[prox ? 2 : 1][j - 1]) return;
   const Level& L = p->lv[j - 1];
   if (L.ax[0].N < 256 || L.ax[1].N < 512) return;
   const bool weighted = adjoint && L.ax[0].winv != nullptr;
@@ -644,7 +646,7 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
                    cudaStream_t s, int* ncta) {
   *ncta = 0;
   int r0, r1, c0, c1;
-  ana_tma_rect(p, j, adjoint, &r0, &r1, &c0, &c1);
+  ana_tma_rect(p, j, adjoint, px[1] != nullptr, &r0, &r1, &c0, &c1);
   if (r1 <= r0 || c1 <= c0) return ADJWT_OK;
   const Level& L = p->lv[j - 1];
   const int Lf = p->fb.L, Lp = Lf - 1;

@@ -146,3 +146,27 @@ def test_workspace_sizes(lib):
     assert rc == 0
     assert lib.adjwt_wt_workspace_size(h) >= (1024 * 1024 + 512 * 512) * 4
     lib.adjwt_wt_plan_destroy(h)
+
+
+def test_level_implementation_switches(lib):
+    """The per-level TMA / tiled switch (host logic; no GPU needed): the size
+    rule gives level 1 of a 2048^2 PER plan to the TMA kernels, small levels
+    never; the switch and its argument checks."""
+    h = C.c_void_p()
+    assert lib.adjwt_wt_plan_create(C.byref(h), 2048, 2048, 5, 1, 3) == 0   # db2, PER
+    uses = C.c_int()
+    try:
+        for op in (0, 1, 2):
+            assert lib.adjwt_wt_plan_uses_tma(h, op, 1, C.byref(uses)) == 0 and uses.value == 1
+            assert lib.adjwt_wt_plan_uses_tma(h, op, 5, C.byref(uses)) == 0 and uses.value == 0
+            assert lib.adjwt_wt_plan_set_tma(h, op, 1, 0) == 0
+            assert lib.adjwt_wt_plan_uses_tma(h, op, 1, C.byref(uses)) == 0 and uses.value == 0
+            assert lib.adjwt_wt_plan_set_tma(h, op, 1, 1) == 0
+            assert lib.adjwt_wt_plan_uses_tma(h, op, 1, C.byref(uses)) == 0 and uses.value == 1
+        assert lib.adjwt_wt_plan_set_tma(h, 0, 6, 0) == -2     # level out of range
+        assert lib.adjwt_wt_plan_set_tma(h, 0, 0, 0) == -2
+        assert lib.adjwt_wt_plan_set_tma(h, 3, 1, 0) == -1     # unknown operator
+        assert lib.adjwt_wt_plan_uses_tma(h, 0, 1, None) == -1
+        assert lib.adjwt_wt_plan_autotune(h, 0, None, None) == -1   # reps outside 1..1000
+    finally:
+        lib.adjwt_wt_plan_destroy(h)

@@ -77,12 +77,17 @@ def test_fista_steps_other_boundaries(adj, mode):
 
 
 @pytest.mark.parametrize("mode", ["sym", "zero", "per", "ppd"])
-def test_fista_steps_large_levels(adj, mode):
+@pytest.mark.parametrize("tiled_only", [False, True])
+def test_fista_steps_large_levels(adj, mode, tiled_only):
     """1600 x 1664, db4 J=2: level 1 runs the prox in the persistent TMA
     analysis kernel (with the tiled kernel on the border tiles unless the TMA
-    tiles cover the level)."""
+    tiles cover the level), or, switched off, in the tiled kernel alone."""
     bc = "per" if mode in ("per", "ppd") else mode
     prob, wt, bl, db = _setup(adj, 1600, 1664, 2, "db4", mode, 9, 1.5, 1e-3, 21, bc=bc)
+    if tiled_only:
+        for op in ("synth", "prox"):
+            for j in (1, 2):
+                wt.set_tma(op, j, False)
     L = 1.01  # a few steps at a fixed step size: parity does not need the estimated L_f
     f = adj.Fista(wt, bl, db, 1e-3, L)
     x, y, t = np.zeros(wt.logical_size), np.zeros(wt.logical_size), 1.0

@@ -75,6 +75,49 @@ def test_large_levels_interior_and_border_kernels(adj, w, mode):
     assert adj.device_status() == 0
 
 
+@pytest.mark.parametrize("w,mode", [("cdf97", "sym"), ("db2", "per"), ("db4", "zero"), ("cdf97", "ppd")])
+def test_large_levels_tiled_only(adj, w, mode):
+    """Every level forced onto the tiled kernels (the TMA kernels switched off
+    for W and for W^* / W^dagger) on levels the size rule would give to the
+    TMA kernels: same operators within the float32 tolerance."""
+    rows, cols, J = 1600, 1664, 2
+    plan = adj.WtPlan(rows, cols, J, w, mode)
+    assert plan.tma_levels()["synth"][0] and plan.tma_levels()["analysis"][0]
+    for j in range(1, J + 1):
+        for op in ("synth", "analysis", "prox"):
+            plan.set_tma(op, j, False)
+    assert not any(any(v) for v in plan.tma_levels().values())
+    x = random_vector(plan.logical_size, 17)
+    out = adj.wt_synth(plan, plan.pack(x))
+    assert_close(to_host_image(out, rows, cols), owt.wt_synth(x, rows, cols, J, w, mode), what=f"W tiled {w} {mode}")
+    img = random_vector((rows, cols), 19)
+    got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
+    assert_close(plan.unpack(got).cpu().numpy(), owt.wt_adjoint(img, J, w, mode), what=f"W^* tiled {w} {mode}")
+    got = adj.wt_analysis(plan, image_dev(plan, img))
+    assert_close(plan.unpack(got).cpu().numpy(), owt.wt_pinv(img, J, w, mode), what=f"W^dagger tiled {w} {mode}")
+    assert adj.device_status() == 0
+
+
+def test_autotune_and_its_cache(adj):
+    """Autotuning measures every eligible level, leaves the operators exact,
+    and a later plan of the same size class starts from the stored choice."""
+    rows, cols, J, w, mode = 1600, 1664, 3, "cdf97", "sym"
+    plan = adj.WtPlan(rows, cols, J, w, mode)
+    assert plan.autotune(reps=3) is False
+    chosen = plan.tma_levels()
+    x = random_vector(plan.logical_size, 23)
+    out = adj.wt_synth(plan, plan.pack(x))
+    assert_close(to_host_image(out, rows, cols), owt.wt_synth(x, rows, cols, J, w, mode), what="W after autotune")
+    img = random_vector((rows, cols), 29)
+    got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
+    assert_close(plan.unpack(got).cpu().numpy(), owt.wt_adjoint(img, J, w, mode), what="W^* after autotune")
+    again = adj.WtPlan(rows, cols, J, w, mode)
+    assert again.tma_levels() == chosen        # applied at creation
+    assert again.autotune(reps=3) is True      # and not measured again
+    assert again.tma_levels() == chosen
+    print("\nautotune 1600x1664 J3 cdf97 sym:", chosen)
+
+
 @pytest.mark.parametrize("mode", ["sym", "per", "zero"])
 def test_full_size_cdf97_five_levels(adj, mode):
     """The 2048 x 2048, 5-level CDF 9/7 operators of the bench, compared in full."""
