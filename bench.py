@@ -210,6 +210,36 @@ def run_step(adj, probs, ch, lanes=None):
     lanes.join()
 
 
+def run_step_device(adj, probs, ch, lanes=None):
+    """The step with the momentum on the device (fista_step_device): the
+    stream sequence that is captured in the CUDA graph the timed loop
+    replays.  Without `lanes`, serially on the current stream."""
+    if lanes is None:
+        for pr in probs:
+            pr["fista"].step_device()
+        adj.conv_gradient(ch["s"], ch["h"], ch["x"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"])
+        return
+    lanes.fork()
+    for pr, st in zip(probs, lanes.streams):
+        pr["fista"].step_device(stream=st)
+    adj.conv_gradient(ch["s"], ch["h"], ch["x"], grad_h=ch["gh"], grad_s=ch["gs"], ws=ch["ws"],
+                      stream=lanes.streams[-1])
+    lanes.join()
+
+
+def capture_step(adj, torch, probs, ch, lanes):
+    """One step (three FISTA iterations on their streams + the channel
+    gradient) captured in a CUDA graph: every replay runs all of its kernels
+    again (the iterations advance; t_k lives in each problem's workspace)."""
+    for pr in probs:
+        pr["fista"].reset_device()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=torch.cuda.Stream()):
+        run_step_device(adj, probs, ch, lanes)
+    return graph
+
+
 def run_e2e(adj, torch, probs, ch, out_host, lanes, steps):
     """`steps` steps through the public API with host buffers: every step's
     inputs (the three observations b and the channel batch s, h, x) are copied
@@ -480,6 +510,13 @@ def ours(args):
         run_step(adj, probs, ch, lanes)
     torch.cuda.synchronize()
 
+    graph = None
+    if not args.no_graph:
+        graph = capture_step(adj, torch, probs, ch, lanes)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+
     traced = min(args.steps, 20)
     stream = torch.cuda.current_stream()
     clock = ClockSampler(local)
@@ -490,16 +527,23 @@ def ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
-    for k in range(args.steps):
-        if k == args.steps - traced:
-            adj.trace_enable(traced * 64)   # the traced steps run serially for clean per-kernel times
-        run_step(adj, probs, ch, None if k >= args.steps - traced else lanes)
+    for _ in range(args.steps):
+        if graph is not None:
+            graph.replay()
+        else:
+            run_step(adj, probs, ch, lanes)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     ms_local = e0.elapsed_time(e1)
     clocks = clock.stop()
+    # per-kernel times: further steps, untimed, run serially with event pairs
+    # around every kernel (the same kernels as a replayed step)
+    adj.trace_enable(traced * 64)
+    for _ in range(traced):
+        run_step_device(adj, probs, ch) if graph is not None else run_step(adj, probs, ch)
+    torch.cuda.synchronize()
     recs = adj.trace_records()
     adj.trace_enable(0)
 
@@ -598,6 +642,8 @@ def ours(args):
                        "boundaries": list(BCS), "psf": [PSF_K, PSF_SIGMA], "channels": [CH_B, CH_N, CH_K],
                        "parallelism": f"replicas x{world} (independent problems per rank)",
                        "l2": "inputs larger than L2: ~540 MB touched per step vs 129 MB L2",
+                       "issue": ("CUDA graph of the step (three fista_step_device lanes + conv_gradient), "
+                                 "replayed once per step" if graph is not None else "call by call on four streams"),
                        "bytes_per_step": bytes_step,
                        "level_kernels": {pr["bc"]: {"tma": pr["wt"].tma_levels(), "autotuned": AUTOTUNE}
                                          for pr in probs}},
@@ -699,6 +745,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline sample")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
     ap.add_argument("--autotune", action="store_true", help="measure the TMA / tiled kernel choice per wavelet level")
+    ap.add_argument("--no-graph", action="store_true", help="time the step issued call by call, not a CUDA graph")
     args = ap.parse_args()
     global AUTOTUNE
     AUTOTUNE = args.autotune
