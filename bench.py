@@ -193,6 +193,21 @@ class Lanes:
             main.wait_event(ev)
 
 
+def max_over_ranks(torch, dist, ms, world, device):
+    """The slowest rank's time (every rank gets it): ranks run independent
+    replicas, so the whole job is done when the last one is."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(bytes_per_step, steps, world, ms):
+    """GB/s of the whole job: every rank processed `steps` steps of
+    `bytes_per_step` algorithmic bytes in at most `ms` milliseconds."""
+    return bytes_per_step * steps * world / (ms * 1e-3) / 1e9
+
+
 def run_step(adj, probs, ch, lanes=None):
     """One step.  With `lanes` the four independent problems run on their own
     streams (the GPU overlaps them); without, one after the other on the
@@ -547,12 +562,9 @@ def ours(args):
     recs = adj.trace_records()
     adj.trace_enable(0)
 
-    t = torch.tensor([ms_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(torch, dist, ms_local, world, "cuda")
     bytes_step = step_bytes()
-    value = bytes_step * args.steps * world / (ms * 1e-3) / 1e9
+    value = whole_job_rate(bytes_step, args.steps, world, ms)
 
     # per-kernel device time from the traced steps
     per = {}
@@ -621,11 +633,8 @@ def ours(args):
     run_e2e(adj, torch, probs, ch, out_host, lanes, e2e_steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = bytes_step * e2e_steps * world / (float(t.item()) * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(torch, dist, e0.elapsed_time(e1), world, "cuda")
+    e2e_value = whole_job_rate(bytes_step, e2e_steps, world, e2e_ms)
 
     extra = {}
     if rank == 0 and not args.no_solve:
