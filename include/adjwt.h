@@ -82,6 +82,15 @@ int adjwt_version(void);
  * after synchronising the device, and resets it to 0 when clear != 0. */
 int adjwt_device_status(int* status_out, int clear);
 
+/* Exercises that bounded wait without any fault: one thread arms a barrier
+ * that expects one arrival and waits on it exactly as the staging kernels
+ * do.  arrive != 0: it arrives itself and the wait ends at once.  arrive == 0:
+ * nothing completes the barrier, the wait gives up after its limit (about one
+ * second) and the kernel records ADJWT_ERR_TIMEOUT in the device status word
+ * and returns; the context stays usable.  Asynchronous on `stream`; read the
+ * result with adjwt_device_status.  No counterpart in the paper. */
+int adjwt_wait_selftest(int arrive, adjwt_stream_t stream);
+
 /* ------------------------------------------------------------------ wavelets
  * Plan of a J-level 2D transform of a rows x cols image.  Band lengths per
  * level and axis: n = floor((N + 3L')/2) for ZERO/SYM/PPD (the full

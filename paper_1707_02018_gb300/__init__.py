@@ -225,6 +225,12 @@ def bce_gradient(s, h, x, lambda_tv, delta, ws=None, stream=None):
     return gh, gs
 
 
+def wait_selftest(arrive, stream=None):
+    """Launch the bounded-wait self-test (arrive=False: the wait runs out and
+    records ADJWT_ERR_TIMEOUT in the device status word); read device_status()."""
+    _lib.check(lib().adjwt_wait_selftest(int(bool(arrive)), _stream(stream)))
+
+
 def device_status(clear=True):
     """Device status word (0, or ADJWT_ERR_TIMEOUT after a bounded wait gave up); synchronises."""
     v = C.c_int()

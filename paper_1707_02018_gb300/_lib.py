@@ -29,6 +29,7 @@ PROTOTYPES = {
     "adjwt_last_error": (C.c_char_p, []),
     "adjwt_version": (C.c_int, []),
     "adjwt_device_status": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
+    "adjwt_wait_selftest": (C.c_int, [C.c_int, VP]),
     "adjwt_wt_plan_create": (C.c_int, [C.POINTER(VP), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "adjwt_wt_plan_destroy": (None, [VP]),
     "adjwt_wt_layout": (C.c_int, [VP, C.POINTER(I64), C.POINTER(I64), C.POINTER(C.c_int), C.POINTER(C.c_int),

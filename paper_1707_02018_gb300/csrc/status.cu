@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "adjwt_internal.h"
+#include "tma.cuh"
 
 namespace adjwt {
 namespace {
@@ -114,5 +115,32 @@ extern "C" int adjwt_device_status(int* status_out, int clear) {
     ADJWT_CUDA_CHECK(cudaMemcpyToSymbol(g_device_status, &zero, sizeof(int)));
   }
   *status_out = v;
+  return ADJWT_OK;
+}
+
+// Self-test of the bounded wait that every asynchronous-copy and tensor-core
+// completion wait of the library uses (mbar_wait: about one second of SM
+// cycles).  One thread arms a barrier that expects one arrival; with
+// arrive != 0 it arrives itself and the wait returns at once, otherwise
+// nothing ever completes the barrier, the wait gives up at its limit and the
+// kernel records ADJWT_ERR_TIMEOUT and returns normally.
+namespace adjwt {
+namespace {
+__global__ void k_wait_selftest(int arrive, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  if (!mbar_wait(&bar, 0)) record_status(status, ADJWT_ERR_TIMEOUT);
+}
+}  // namespace
+}  // namespace adjwt
+
+extern "C" int adjwt_wait_selftest(int arrive, adjwt_stream_t stream) {
+  int* st = device_status_ptr();
+  if (!st) return fail(ADJWT_ERR_CUDA, "adjwt_wait_selftest: no device status word");
+  k_wait_selftest<<<1, 32, 0, stream>>>(arrive, st);
+  ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
