@@ -194,18 +194,6 @@ __device__ __forceinline__ bool block_wait_product(uint64_t* bar, uint32_t parit
   return all;
 }
 
-__device__ __forceinline__ void cp_async16(float* dst, const float* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
-               "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src)),
-               "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Raw s of one chunk: s_raw[u] = s[m0 - 64 + u] (zero off the row), u < 4224.
 // vec: the row is 16-byte aligned and n a multiple of 4.

@@ -394,7 +394,13 @@ struct AG {
   static constexpr int BUF = up32(ER * BC);
   static constexpr int NW = 2 * kAP + L - 2;      // register window per thread
   static constexpr int VP = EC | 1;               // odd pitch of the column-pass output
-  static constexpr size_t smem_bytes() { return 128 + (size_t)(2 * BUF + 2 * kAR * VP) * 4; }
+  // prox variant: each row-pass thread's slot of next-tile prox state (x and y
+  // of its two bands, 8 values each), padded to 36 floats so that the 16-byte
+  // slot reads of a quarter warp fall on distinct banks
+  static constexpr int kSlot = 36;
+  static constexpr size_t smem_bytes(bool prox) {
+    return 128 + (size_t)(2 * BUF + 2 * kAR * VP + (prox ? (kAC / kAP) * 32 * kSlot : 0)) * 4;
+  }
 };
 
 struct AnaTmaArgs {
@@ -424,6 +430,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
   float* V = buf0 + 2 * G::BUF;  // [2][kAR][VP]
   const int tid = threadIdx.x;
+  float* slot = V + 2 * kAR * G::VP + tid * G::kSlot;  // prox: this thread's next-tile state (y, x per band)
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -451,35 +458,56 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
 
   float l1 = 0.0f;
   const float beta = PROX && a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
+  // row-pass thread: (vertical filter f, coefficient row kk), 8-coefficient block = warp
+  const int warp = tid >> 5, lane = tid & 31, f = lane >> 4, kk = lane & 15;
+  const bool rower = warp < kAC / kAP;
+  auto pick = [&](float* const (&arr)[4], int bnd) -> float* {
+    return bnd == 0 ? arr[0] : (bnd == 1 ? arr[1] : (bnd == 2 ? arr[2] : arr[3]));
+  };
+  float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
+  float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
+  // prox variant: a thread copies the prox state it will need for a tile
+  // (its 8 coefficients of y and x in both of its bands) into its own slot
+  // one tile ahead; only the thread itself reads the slot, so no barrier
+  auto prefetch_prox = [&](int tt) {
+    int pk0, pl0;
+    tile_origin(tt, pk0, pl0);
+    const size_t prow = (size_t)(pk0 + kk) * a.out_pitch + pl0 + kAP * warp;
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb) {
+      if (!pxs[hb]) continue;
+#pragma unroll
+      for (int q = 0; q < kAP / 4; ++q) {
+        cp_async16(slot + hb * 16 + 4 * q, pys[hb] + prow + 4 * q, 16u);
+        cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + prow + 4 * q, 16u);
+      }
+    }
+    cp_async_commit();
+  };
   int t = blockIdx.x, b = 0;
   if (t < a.ntiles) issue(t, 0);
+  if (PROX && rower && t < a.ntiles) prefetch_prox(t);
   for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
     int k0, l0;
     tile_origin(t, k0, l0);
     if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
-    // row-pass thread: (vertical filter f, coefficient row kk), 8-coefficient block = warp
-    const int warp = tid >> 5, lane = tid & 31, f = lane >> 4, kk = lane & 15;
-    const bool rower = warp < kAC / kAP;
     const size_t row = (size_t)(k0 + kk) * a.out_pitch + l0 + kAP * warp;
-    auto pick = [&](float* const (&arr)[4], int bnd) -> float* {
-      return bnd == 0 ? arr[0] : (bnd == 1 ? arr[1] : (bnd == 2 ? arr[2] : arr[3]));
-    };
-    float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
-    float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
-    // prox state of this tile: requested before the copy completes
+    // this tile's prox state from the slot, then the next tile's requested
     float yv[2][kAP], xv[2][kAP];
     if (PROX && rower) {
+      cp_async_wait_all();
 #pragma unroll
       for (int hb = 0; hb < 2; ++hb) {
         if (!pxs[hb]) continue;
 #pragma unroll
         for (int q = 0; q < kAP / 4; ++q) {
-          const float4 y4 = reinterpret_cast<const float4*>(pys[hb] + row)[q];
-          const float4 x4 = reinterpret_cast<const float4*>(pxs[hb] + row)[q];
+          const float4 y4 = reinterpret_cast<const float4*>(slot + hb * 16)[q];
+          const float4 x4 = reinterpret_cast<const float4*>(slot + hb * 16 + 8)[q];
           yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
           xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
         }
       }
+      if (t + gridDim.x < a.ntiles) prefetch_prox(t + gridDim.x);
     }
     bool ok = mbar_wait(&bar[b], (phase >> b) & 1);
     if (ok) {
@@ -490,6 +518,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
       if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
       for (int bb = 0; bb < 2; ++bb)
         if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
+      if (PROX) cp_async_wait_all();
       return;
     }
     const float* S = buf0 + b * G::BUF + a.d_c;
@@ -593,7 +622,7 @@ template <int L, bool PROX>
 int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, const char* name, int level,
                   int* ncta) {
   using G = AG<L>;
-  const size_t smem = G::smem_bytes();
+  const size_t smem = G::smem_bytes(PROX);
   auto kern = k_ana_tma<L, PROX>;
   ADJWT_CUDA_CHECK(set_smem(kern, smem));
   static int occ = 0;
