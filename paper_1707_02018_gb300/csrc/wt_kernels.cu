@@ -24,6 +24,7 @@
 
 #include "adjwt_internal.h"
 #include "device_common.cuh"
+#include "tma.cuh"
 
 namespace adjwt {
 namespace {
@@ -104,6 +105,13 @@ __device__ __forceinline__ void border_tile(int r0, int r1, int c0, int c1, int 
 // values held in registers; row pass likewise along a row (lanes on rows, odd
 // row pitch).  Both filters of a pass share the loaded window.
 constexpr int kAP = 8;
+// prox epilogue: each row-pass thread's prox state (y and x of its two bands,
+// 8 values each) is copied into its own dynamic-shared-memory slot at kernel
+// start, so the loads overlap the window gather and both passes; 36-float
+// slots put a quarter warp's 16-byte reads on distinct banks
+constexpr int kProxSlot = 36;
+constexpr int kProxRowers = 2 * (kTile / kAP) * 32;
+constexpr size_t kProxSlotBytes = (size_t)kProxRowers * kProxSlot * sizeof(float);
 
 template <int L>
 __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
@@ -122,6 +130,42 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
   border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
   const int k0 = tile_y * kTile, l0 = tile_x * kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ float prox_slots[];  // kProxSlotBytes when the launch has prox bands, else none
+  const bool rower = warp < 2 * (kTile / kAP);
+  // row pass + prox epilogue: thread = (row kk, vertical filter f, block lb)
+  const int kk = lane, f = warp & 1, lb = warp >> 1;
+  const int k = k0 + kk, lbase = l0 + kAP * lb;
+  const size_t row = (size_t)k * a.out_pitch + lbase;
+  const bool full = lbase + kAP <= a.nc;   // all eight inside the band (16-byte aligned)
+  const bool has_prox = a.px[1] != nullptr;
+  // band pointers by compile-time index (avoids dynamic indexing of the parameter block)
+  auto pick = [&](float* const (&arr)[4], int b) -> float* {
+    return b == 0 ? arr[0] : (b == 1 ? arr[1] : (b == 2 ? arr[2] : arr[3]));
+  };
+  float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
+  float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
+  float* slot = prox_slots + tid * kProxSlot;
+  if (has_prox && rower && k < a.nr && lbase < a.out_pitch) {
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb) {
+      if (!pxs[hb]) continue;
+      if (full) {
+#pragma unroll
+        for (int q = 0; q < kAP / 4; ++q) {
+          cp_async16(slot + hb * 16 + 4 * q, pys[hb] + row + 4 * q, 16u);
+          cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + row + 4 * q, 16u);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < kAP; ++p) {
+          const bool in = lbase + p < a.nc;
+          cp_async4(slot + hb * 16 + p, pys[hb] + row + (in ? p : 0), in ? 4u : 0u);
+          cp_async4(slot + hb * 16 + 8 + p, pxs[hb] + row + (in ? p : 0), in ? 4u : 0u);
+        }
+      }
+    }
+    cp_async_commit();
+  }
 
   // first extended coordinate of each axis and whether the tile reads only
   // plain interior samples (no zero, mirror, wrap or weight)
@@ -199,9 +243,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
   // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
   float l1 = 0.0f;  // per-thread float32 partial of |x_k|, float64 across the block
   const float beta = a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
-  if (warp < 2 * (kTile / kAP)) {  // the ninth warp has no row-pass item
-    const int kk = lane, f = warp & 1, lb = warp >> 1;
-    const int k = k0 + kk;
+  if (rower) {  // the ninth warp has no row-pass item
     float w[NW];
 #pragma unroll
     for (int j = 0; j < NW; ++j) w[j] = V[f][kk][2 * kAP * lb + j];
@@ -217,39 +259,20 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
       res[0][p] = lo;
       res[1][p] = hi;
     }
-    const int lbase = l0 + kAP * lb;
     if (k < a.nr && lbase < a.out_pitch) {
-      const size_t row = (size_t)k * a.out_pitch + lbase;
-      const bool full = lbase + kAP <= a.nc;   // all eight inside the band (16-byte aligned)
-      // band pointers by compile-time index (avoids dynamic indexing of the parameter block)
-      auto pick = [&](float* const (&arr)[4], int b) -> float* {
-        return b == 0 ? arr[0] : (b == 1 ? arr[1] : (b == 2 ? arr[2] : arr[3]));
-      };
-      float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
-      float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
       float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
-      // prox bands: gather y and x first (all loads in flight), then compute and store
+      // prox bands: y and x from this thread's slot (copied at kernel start)
       float yv[2][kAP], xv[2][kAP];
+      if (has_prox) cp_async_wait_all();
 #pragma unroll
       for (int hb = 0; hb < 2; ++hb) {
         if (!pxs[hb]) continue;
-        const float* __restrict__ ys = pys[hb] + row;
-        const float* __restrict__ xs = pxs[hb] + row;
-        if (full) {
 #pragma unroll
-          for (int q = 0; q < kAP / 4; ++q) {
-            const float4 y4 = reinterpret_cast<const float4*>(ys)[q];
-            const float4 x4 = reinterpret_cast<const float4*>(xs)[q];
-            yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
-            xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
-          }
-        } else {
-#pragma unroll
-          for (int p = 0; p < kAP; ++p) {
-            const bool in = lbase + p < a.nc;
-            yv[hb][p] = in ? ys[p] : 0.0f;
-            xv[hb][p] = in ? xs[p] : 0.0f;
-          }
+        for (int q = 0; q < kAP / 4; ++q) {
+          const float4 y4 = reinterpret_cast<const float4*>(slot + hb * 16)[q];
+          const float4 x4 = reinterpret_cast<const float4*>(slot + hb * 16 + 8)[q];
+          yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
+          xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
         }
       }
 #pragma unroll
@@ -784,8 +807,11 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     slot += ncta;
     const char* name = !adjoint ? "wt_analysis" : (prox.x ? "wt_adjoint_prox" : "wt_adjoint");
     if (ncta > 0) {
-      int rc = dispatch_L(fb.L, [&](auto Lc) {
-        ADJWT_TRACED(name, j, s, pdl_launch(k_analysis<decltype(Lc)::value>, grid, kAnaThreads, 0, s, a));
+      int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
+        auto kern = k_analysis<decltype(Lc)::value>;
+        const size_t dyn = prox.x ? kProxSlotBytes : 0;
+        if (dyn) ADJWT_CUDA_CHECK(set_smem(kern, dyn));
+        ADJWT_TRACED(name, j, s, pdl_launch(kern, grid, kAnaThreads, dyn, s, a));
         return ADJWT_OK;
       });
       if (rc) return rc;
