@@ -170,3 +170,18 @@ def test_level_implementation_switches(lib):
         assert lib.adjwt_wt_plan_autotune(h, 0, None, None) == -1   # reps outside 1..1000
     finally:
         lib.adjwt_wt_plan_destroy(h)
+
+
+def test_differentiation_entry_validation(lib):
+    """The differentiation entries reject bad arguments before any launch."""
+    assert lib.adjwt_axpby(-1, 1.0, None, 1.0, None, None, None) == -2
+    assert lib.adjwt_axpby(0, 1.0, None, 1.0, None, None, None) == 0        # nothing to do
+    assert lib.adjwt_axpby(4, 1.0, None, 1.0, None, None, None) == -1       # NULL buffers
+    assert lib.adjwt_dot(2, 5, 4, None, None, None, None, 0, None) == -2      # pitch < cols
+    assert lib.adjwt_dot(1, 4, 4, None, None, None, None, 0, None) == -1      # NULL buffers
+    fake = C.c_void_p(256)                                                   # never dereferenced
+    assert lib.adjwt_dot(1, 4, 4, fake, fake, fake, None, 0, None) == -7     # no workspace
+    assert lib.adjwt_dot(1, 4, 4, fake, fake, fake, fake, 8, None) == -7     # workspace too small
+    assert lib.fista_prox_vjp(-1, None, None, None, None, None, 0, None) == -2
+    assert lib.fista_prox_vjp(4, fake, fake, fake, fake, None, 0, None) == -7
+    assert lib.adjwt_reduce_workspace_size() >= 8
