@@ -183,7 +183,11 @@ int blur_normal(const adjwt_blur_plan* plan, const float* u, const float* b, flo
  * h (batch x k), r and x (batch x (n+k-1)).  Eq. 5 gradients:
  *   grad_h[b][j] = sum_{i<n} s[b][i] r[b][i+j]   (j < k)   = S^T r
  *   grad_s[b][m] = sum_{i<k} h[b][i] r[b][i+m]   (m < n)   = H^T r
- * either output may be NULL.  batch >= 0, n >= 1, k >= 1. */
+ * either output may be NULL.  batch >= 0, n >= 1, k >= 1.  Channels of
+ * 49..64 taps run on the tensor cores (TF32 operands split into high and low
+ * parts, float32-accurate); other lengths on the CUDA cores.  Setting the
+ * environment variable ADJWT_CONV_FP32 to a non-zero value before the first
+ * call sends every k <= 1024 to the CUDA-core kernel. */
 size_t adjwt_conv_adjoint_workspace_size(int batch, int64_t n, int k);
 int conv_adjoint(int batch, int64_t n, int k, const float* s, const float* h, const float* r, float* grad_h,
                  float* grad_s, void* ws, size_t ws_bytes, adjwt_stream_t stream);
