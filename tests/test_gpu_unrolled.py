@@ -115,3 +115,20 @@ def test_autograd_node(adj):
     assert float(loss.detach()) == l2
     assert float(lam_t.grad) == 2.0 * dl and float(sig_t.grad) == 2.0 * ds
     assert torch.equal(bdev.grad, adj.axpby(2.0, db, 0.0, db))
+
+
+@pytest.mark.parametrize("steps,every,bc,mode", [(1, None, "zero", "zero"), (4, 9, "sym", "sym"), (5, 2, "per", "per")])
+def test_unrolled_edge_cases(adj, steps, every, bc, mode):
+    """One iteration, checkpoints sparser than the iterations, and the ZERO
+    and PER blur boundaries, against the oracle's reverse mode."""
+    from paper_1707_02018_gb300.unrolled import UnrolledFista
+    rows = cols = 32
+    S, img, nco = _problem(adj, rows, cols, 2, "db2", mode, bc, 5, 1.1, 0.02, 61 + steps)
+    want = ounr.unrolled_grads(S, steps, img, nco)
+    wt = adj.WtPlan(rows, cols, 2, "db2", mode)
+    un = UnrolledFista(rows, cols, 2, "db2", mode, 5, 1.1, bc, wt.image(S.b), 0.02, S.L)
+    loss, dlam, dsig, db = un.grads(steps, wt.image(img), checkpoint_every=every)
+    assert abs(loss - want[0]) <= 1e-5 * abs(want[0])
+    assert abs(dlam - want[1]) <= 1e-5 * max(abs(want[1]), 1e-6)
+    assert abs(dsig - want[2]) <= 1e-5 * max(abs(want[2]), 1e-6)
+    assert rel_err(db[:, :cols].double().cpu().numpy(), want[3]) <= 1e-5
