@@ -379,7 +379,9 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 //                with both analysis filters from a register window;
 //   row pass:    lanes on (vertical filter, coefficient row), a warp per
 //                8-coefficient block; both horizontal filters, then the
-//                plain store or the prox epilogue (loads first, float4).
+//                plain store or the prox epilogue (float4 stores), whose
+//                state x, y each thread copied with cp.async into its own
+//                shared-memory slot one tile earlier.
 namespace {
 
 constexpr int kAR = 16;    // coefficient rows per tile
