@@ -351,29 +351,47 @@ def adjoint_vs_pinv(adj, torch, pr, iters=300):
     return {"iterations": iters, "boundary": pr["bc"], "F_adjoint": fa, "F_pinv": fp, "ratio_pinv_over_adjoint": fp / fa}
 
 
-def unrolled_gradient_timing(adj, torch, pr, steps=10, reps=3):
-    """Seconds for `steps` plain FISTA iterations and for the gradient of
+def unrolled_gradient_timing(adj, torch, batch=16, size=512, levels=4, wavelet="db4", steps=10, reps=2):
+    """The differentiation workload: a batch of `batch` problems of size^2,
+    `levels`-level 8-tap Daubechies, symmetric boundaries, 9x9 Gaussian PSF
+    sigma = 1.5 (the PSF of the 256^2 configuration; the workload names none),
+    lambda = 1e-3; for each, `steps` FISTA iterations and the gradient of
     l = 1/2 ||W x_N - u||^2 with respect to (lambda, sigma, b) through them
-    (forward with checkpoints, recomputed segments, reverse mode), on the
-    2048^2 SYM problem; best of `reps`."""
+    (checkpointed forward, recomputed segments, reverse mode).  Seconds for
+    the whole batch, best of `reps`, forward alone and with the gradient."""
+    from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
     from paper_1707_02018_gb300.unrolled import UnrolledFista
-    f = pr["fista"]
-    un = UnrolledFista(SIZE, SIZE, LEVELS, WAVELET, "sym", PSF_K, PSF_SIGMA, "sym", pr["b"], LAM,
-                       f.problem.lipschitz)
-    u_ref = pr["b"].clone()
-    un.grads(steps, u_ref)  # warm-up (plans, allocations)
+    k, sigma = 9, 1.5
+    p = gaussian_taps(k, sigma)
+    runs = []
+    for i in range(batch):
+        seed = 9000 + i
+        wt = adj.WtPlan(size, size, levels, wavelet, "sym")
+        bl = adj.BlurPlan(size, size, p, p, "sym")
+        img = wt.image(torch.as_tensor(piecewise_smooth_image(size, size, seed)))
+        b = adj.blur(bl, img)
+        b[:, :size] += torch.as_tensor(gaussian_noise((size, size), seed + 1, NOISE), dtype=torch.float32,
+                                       device="cuda")
+        f = adj.Fista(wt, bl, b, LAM, 1.0)
+        L = f.lipschitz(wt.pack(random_vector(wt.logical_size, seed + 2)), iters=30)
+        runs.append((UnrolledFista(size, size, levels, wavelet, "sym", k, sigma, "sym", b, LAM, L), img))
+    for un, img in runs[:1]:
+        un.grads(steps, img)  # warm-up (plans, allocations)
     fwd, full = [], []
     for _ in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        un.solve(steps)
+        for un, _ in runs:
+            un.solve(steps)
         torch.cuda.synchronize()
         fwd.append(time.perf_counter() - t0)
         t0 = time.perf_counter()
-        un.grads(steps, u_ref)
+        for un, img in runs:
+            un.grads(steps, img)
         torch.cuda.synchronize()
         full.append(time.perf_counter() - t0)
-    return {"steps": steps, "size": SIZE, "boundary": "sym", "forward_sec": min(fwd), "gradient_sec": min(full),
+    return {"batch": batch, "size": size, "levels": levels, "wavelet": wavelet, "boundary": "sym",
+            "psf": [k, sigma], "steps": steps, "forward_sec": min(fwd), "gradient_sec": min(full),
             "gradient_over_forward": min(full) / min(fwd),
             "wrt": "lambda, sigma (Gaussian PSF width), b; checkpoints every floor(sqrt(steps)) iterations"}
 
@@ -641,7 +659,7 @@ def ours(args):
         extra["fista_sec_to_1e-4"] = fista_time_to_tol(adj, torch, probs[1])
         extra["fista_batched_vs_plain_to_1e-4"] = batched_vs_plain(adj, torch)
         extra["fista_adjoint_vs_pinv"] = adjoint_vs_pinv(adj, torch, probs[1])
-        extra["unrolled_fista_gradient"] = unrolled_gradient_timing(adj, torch, probs[1])
+        extra["unrolled_fista_gradient"] = unrolled_gradient_timing(adj, torch)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

@@ -333,6 +333,31 @@ int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, const float
 int fista_prox_vjp(int64_t n, const float* x_next, const float* xbar, float* zbar, double* sign_dot_dev, void* ws,
                    size_t ws_bytes, adjwt_stream_t stream);
 
+/* One whole reverse-mode step of the FISTA iteration k (0-based) for the
+ * exact-adjoint problem (prob->gradient == ADJWT_GRAD_ADJOINT, else
+ * INVALID_ARG): the kernels of the pieces above, W, R, R^* and W^* issued in
+ * one call.  With beta = beta_k (the momentum factor that iteration used, as
+ * float32), x_next = x_{k+1}, y_k (device coefficient vectors), xbar = the
+ * adjoint of x_{k+1} collected so far and ybar = the adjoint of y_{k+1}:
+ *   X = xbar + (1 + beta) ybar;  zbar = X where x_next != 0;  u = W zbar
+ *   *dtau_dev -= sum sign(x_next) X                       (tau = lambda / L)
+ *   ybar <- zbar - (1/L) W^* R^* R u     (the adjoint of y_k)
+ *   xbar <- -beta (old ybar)              (the adjoint of x_k from y_{k+1})
+ *   db   += (1/L) R u                     (if db, a device image, is not NULL)
+ *   *dsigma_dev -= (1/L) (<R' u, R W y_k - b> + <R u, R' W y_k>)
+ * where R' = dblur_1 + dblur_2, the two plans of dR/dsigma
+ * (adjwt_gaussian_taps).  dsigma_dev NULL skips that term (and the plans may
+ * be NULL); otherwise both plans are required (INVALID_ARG) and describe the
+ * problem's image (SHAPE).  dtau_dev and dsigma_dev are DEVICE doubles that
+ * the call accumulates into (float64).  Vectors 16-byte aligned (ALIGN).
+ * ws: device scratch of adjwt_fista_vjp_workspace_size(prob) bytes, 256-byte
+ * aligned (WORKSPACE), overlapping none of the arguments.  Nothing
+ * synchronises; the call is a pure sequence of stream operations. */
+size_t adjwt_fista_vjp_workspace_size(const adjwt_fista_problem* prob);
+int fista_vjp_step(const adjwt_fista_problem* prob, const adjwt_blur_plan* dblur_1, const adjwt_blur_plan* dblur_2,
+                   const float* x_next, const float* y_k, double beta, float* xbar, float* ybar, float* db,
+                   double* dtau_dev, double* dsigma_dev, void* ws, size_t ws_bytes, adjwt_stream_t stream);
+
 /* ------------------------------------------------------------------- tracing
  * Optional per-kernel device timing without a profiler (the paper has no
  * counterpart; it serves the measurement harness).  adjwt_trace_enable(n)

@@ -374,6 +374,10 @@ class Fista:
                                                C.byref(out), _stream(stream)))
         return out.value
 
+    def vjp_workspace(self):
+        """Scratch for fista_vjp_step on this problem."""
+        return workspace(lib().adjwt_fista_vjp_workspace_size(C.byref(self.problem)), device=self.x.device)
+
     def lipschitz(self, v, iters=50, stream=None):
         out = C.c_double()
         _lib.check(lib().adjwt_fista_lipschitz(C.byref(self.problem), _ptr(v), iters, _ptr(self.ws),
@@ -432,6 +436,19 @@ def prox_vjp(x_next, xbar, zbar=None, stream=None):
     _lib.check(lib().fista_prox_vjp(x_next.numel(), _ptr(x_next), _ptr(xbar), _ptr(zbar), _ptr(s), _ptr(ws),
                                     ws.numel(), _stream(stream)))
     return zbar, s
+
+
+def fista_vjp_step(fista, dblur, x_next, y_k, beta, xbar, ybar, db, dtau, dsigma, ws, stream=None):
+    """One reverse-mode step of FISTA iteration k in a single library call:
+    xbar (adjoint of x_{k+1}) and ybar (adjoint of y_{k+1}) are replaced by
+    the adjoints of x_k (from y_{k+1}) and y_k, db (image or None) gains
+    (1/L) R W zbar, and the float64 device scalars dtau / dsigma accumulate
+    dl/dtau and dl/dsigma.  dblur: the two plans of dR/dsigma, or None with
+    dsigma None.  ws: fista.vjp_workspace()."""
+    d1, d2 = (None, None) if dblur is None else (dblur[0].handle, dblur[1].handle)
+    _lib.check(lib().fista_vjp_step(C.byref(fista.problem), d1, d2, _ptr(x_next), _ptr(y_k), float(beta), _ptr(xbar),
+                                    _ptr(ybar), None if db is None else _ptr(db), _ptr(dtau),
+                                    None if dsigma is None else _ptr(dsigma), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def fista_step(fista, objective=False, stream=None):

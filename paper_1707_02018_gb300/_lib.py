@@ -66,6 +66,9 @@ PROTOTYPES = {
     "adjwt_axpby": (C.c_int, [I64, C.c_float, VP, C.c_float, VP, VP, VP]),
     "adjwt_dot": (C.c_int, [C.c_int, I64, I64, VP, VP, VP, VP, SZ, VP]),
     "fista_prox_vjp": (C.c_int, [I64, VP, VP, VP, VP, VP, SZ, VP]),
+    "adjwt_fista_vjp_workspace_size": (SZ, [C.POINTER(FistaProblem)]),
+    "fista_vjp_step": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, VP, C.c_double, VP, VP, VP, VP, VP, VP, SZ,
+                                 VP]),
     "adjwt_fista_objective": (C.c_int, [C.POINTER(FistaProblem), VP, VP, SZ, DP, VP]),
     "adjwt_fista_lipschitz": (C.c_int, [C.POINTER(FistaProblem), VP, C.c_int, VP, SZ, DP, VP]),
     "adjwt_trace_enable": (C.c_int, [C.c_int]),

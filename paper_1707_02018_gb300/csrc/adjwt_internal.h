@@ -210,6 +210,18 @@ int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b,
 int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,
                         double* out, cudaStream_t s);
 
+// Differentiation pieces (grad.cu): out = a x + b y on rows x cols of pitched
+// arrays; float64 per-block partials of an inner product and of the soft
+// threshold's sum sign(x_next) xbar (zbar = xbar where x_next != 0), with
+// *nparts partials written (at most reduce_partials_bytes() / 8).
+int launch_axpby(int rows, int64_t cols, int64_t pitch, float a, const float* x, float b, const float* y, float* out,
+                 cudaStream_t st);
+int launch_dot_partials(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* partials,
+                        cudaStream_t st, int* nparts);
+int launch_prox_vjp_partials(int64_t n, const float* x_next, const float* xbar, float* zbar, double* partials,
+                             cudaStream_t st, int* nparts);
+size_t reduce_partials_bytes();
+
 // Tuning cache: apply the stored per-level TMA choices of this plan's size
 // class (rows, cols, levels, wavelet, boundary, device), if any.
 void apply_tuning_cache(adjwt_wt_plan* p);

@@ -23,11 +23,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs: partial slots of one inner product
 
-__global__ void __launch_bounds__(kThreads) k_axpby(int64_t n, float a, const float* __restrict__ x, float b,
+// out = a x + b y on rows x cols of arrays with row pitch `pitch` (pitch
+// columns beyond cols untouched); a flat vector is rows = 1, cols = pitch = n
+__global__ void __launch_bounds__(kThreads) k_axpby(int rows, int64_t cols, int64_t pitch, float a,
+                                                    const float* __restrict__ x, float b,
                                                     const float* __restrict__ y, float* __restrict__ out) {
   pdl_entry();
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-    out[i] = fmaf(a, x[i], b * y[i]);
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const int64_t r = i / cols, o = r * pitch + (i - r * cols);
+    out[o] = fmaf(a, x[o], b * y[o]);
+  }
 }
 
 // partials[block] = sum over the block's elements of x y (rows x cols of a pitched array)
@@ -68,21 +74,47 @@ unsigned grid_for(int64_t n) {
 }
 
 }  // namespace
+
+int launch_axpby(int rows, int64_t cols, int64_t pitch, float a, const float* x, float b, const float* y, float* out,
+                 cudaStream_t st) {
+  ADJWT_TRACED("axpby", 0, st,
+               pdl_launch(k_axpby, grid_for((int64_t)rows * cols), kThreads, 0, st, rows, cols, pitch, a, x, b, y, out));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+int launch_dot_partials(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* partials,
+                        cudaStream_t st, int* nparts) {
+  const unsigned nb = grid_for((int64_t)rows * cols);
+  ADJWT_TRACED("dot", 0, st, pdl_launch(k_dot, nb, kThreads, 0, st, rows, cols, pitch, x, y, partials));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  *nparts = static_cast<int>(nb);
+  return ADJWT_OK;
+}
+
+int launch_prox_vjp_partials(int64_t n, const float* x_next, const float* xbar, float* zbar, double* partials,
+                             cudaStream_t st, int* nparts) {
+  const unsigned nb = grid_for(n);
+  ADJWT_TRACED("prox_vjp", 0, st, pdl_launch(k_prox_vjp, nb, kThreads, 0, st, n, x_next, xbar, zbar, partials));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  *nparts = static_cast<int>(nb);
+  return ADJWT_OK;
+}
+
+size_t reduce_partials_bytes() { return (size_t)kDotBlocks * sizeof(double); }
+
 }  // namespace adjwt
 
 using namespace adjwt;
 
-extern "C" size_t adjwt_reduce_workspace_size(void) { return (size_t)kDotBlocks * sizeof(double); }
+extern "C" size_t adjwt_reduce_workspace_size(void) { return reduce_partials_bytes(); }
 
 extern "C" int adjwt_axpby(int64_t n, float a, const float* x, float b, const float* y, float* out,
                            adjwt_stream_t stream) {
   if (n < 0) return fail(ADJWT_ERR_SHAPE, "adjwt_axpby: n < 0");
   if (n == 0) return ADJWT_OK;
   if (!x || !y || !out) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_axpby: NULL pointer");
-  auto st = reinterpret_cast<cudaStream_t>(stream);
-  ADJWT_TRACED("axpby", 0, st, pdl_launch(k_axpby, grid_for(n), kThreads, 0, st, n, a, x, b, y, out));
-  ADJWT_CUDA_CHECK(cudaGetLastError());
-  return ADJWT_OK;
+  return launch_axpby(1, n, n, a, x, b, y, out, stream);
 }
 
 extern "C" int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* out_dev,
@@ -91,12 +123,11 @@ extern "C" int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, 
   if (!x || !y || !out_dev) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_dot: NULL pointer");
   if (!ws || ws_bytes < adjwt_reduce_workspace_size())
     return fail(ADJWT_ERR_WORKSPACE, "adjwt_dot: workspace of adjwt_reduce_workspace_size() bytes needed");
-  auto st = reinterpret_cast<cudaStream_t>(stream);
   auto* part = static_cast<double*>(ws);
-  const unsigned nb = grid_for((int64_t)rows * cols);
-  ADJWT_TRACED("dot", 0, st, pdl_launch(k_dot, nb, kThreads, 0, st, rows, cols, pitch, x, y, part));
-  ADJWT_CUDA_CHECK(cudaGetLastError());
-  return launch_sum_partials(part, static_cast<int>(nb), 1.0, nullptr, 0, 0.0, out_dev, st);
+  int nb = 0;
+  int rc = launch_dot_partials(rows, cols, pitch, x, y, part, stream, &nb);
+  if (rc) return rc;
+  return launch_sum_partials(part, nb, 1.0, nullptr, 0, 0.0, out_dev, stream);
 }
 
 extern "C" int fista_prox_vjp(int64_t n, const float* x_next, const float* xbar, float* zbar, double* sign_dot_dev,
@@ -105,10 +136,9 @@ extern "C" int fista_prox_vjp(int64_t n, const float* x_next, const float* xbar,
   if (!x_next || !xbar || !zbar || !sign_dot_dev) return fail(ADJWT_ERR_INVALID_ARG, "fista_prox_vjp: NULL pointer");
   if (!ws || ws_bytes < adjwt_reduce_workspace_size())
     return fail(ADJWT_ERR_WORKSPACE, "fista_prox_vjp: workspace of adjwt_reduce_workspace_size() bytes needed");
-  auto st = reinterpret_cast<cudaStream_t>(stream);
   auto* part = static_cast<double*>(ws);
-  const unsigned nb = grid_for(n);
-  ADJWT_TRACED("prox_vjp", 0, st, pdl_launch(k_prox_vjp, nb, kThreads, 0, st, n, x_next, xbar, zbar, part));
-  ADJWT_CUDA_CHECK(cudaGetLastError());
-  return launch_sum_partials(part, static_cast<int>(nb), 1.0, nullptr, 0, 0.0, sign_dot_dev, st);
+  int nb = 0;
+  int rc = launch_prox_vjp_partials(n, x_next, xbar, zbar, part, stream, &nb);
+  if (rc) return rc;
+  return launch_sum_partials(part, nb, 1.0, nullptr, 0, 0.0, sign_dot_dev, stream);
 }

@@ -17,15 +17,17 @@ x_{k+1} collected so far, Y: adjoint of y_{k+1}):
     dl/dsigma -= (1/L) (<R' u, R W y_k - b> + <R u, R' W y_k>)
 and dl/dlambda = dl/dtau / L.  L is held fixed.  Every vector step is one of
 the library's kernels (W, W^*, R, R^*, the soft-threshold VJP, a x + b y,
-float64 inner products); the iterates are kept at checkpoints only and the
+float64 inner products); by default one backward iteration is one library
+call (fista_vjp_step) that issues them all, with dl/dtau and dl/dsigma
+accumulated on the device.  The iterates are kept at checkpoints only and the
 segments between them recomputed during the backward pass.
 """
 import math
 
 import torch
 
-from . import (BlurPlan, Fista, WtPlan, axpby, blur, blur_adjoint, dot, gaussian_taps, prox_vjp, wt_synth,
-               wt_synth_adjoint)
+from . import (BlurPlan, Fista, WtPlan, axpby, blur, blur_adjoint, dot, fista_vjp_step, gaussian_taps, prox_vjp,
+               wt_synth, wt_synth_adjoint)
 
 
 class UnrolledFista:
@@ -42,6 +44,7 @@ class UnrolledFista:
         self.b = b
         self.lam, self.L = float(lam), float(L)
         self.fista = Fista(self.wt, self.R, b, self.lam, self.L)
+        self._vjp_ws = None
 
     # --------------------------------------------------------------- helpers
     def _img_dot(self, x, y):
@@ -75,9 +78,28 @@ class UnrolledFista:
         self._run(0, n_steps, keep=False)
         return self.fista.x.clone()
 
-    def grads(self, n_steps, u_ref, checkpoint_every=None):
+    def _back_pieces(self, k, beta, x_next, y_k, Xp, Y, db, tau_terms, sigma_terms):
+        """Backward iteration k from the library's separate pieces; returns (Xp, Y)."""
+        inv_l = 1.0 / self.L
+        X = axpby(1.0, Xp, 1.0 + beta, Y)
+        zbar, sd = prox_vjp(x_next, X)
+        tau_terms.append(sd)
+        u = wt_synth(self.wt, zbar)
+        Ru = blur(self.R, u)
+        q = wt_synth_adjoint(self.wt, blur_adjoint(self.R, Ru))
+        Y_k = axpby(1.0, zbar, -inv_l, q)
+        Xp = axpby(-beta, Y, 0.0, Y)
+        axpby(1.0, db, inv_l, Ru, out=db)
+        Wy = wt_synth(self.wt, y_k)
+        r = axpby(1.0, blur(self.R, Wy), -1.0, self.b)
+        sigma_terms.append(-inv_l * self._img_dot(self._dR(u), r))
+        sigma_terms.append(-inv_l * self._img_dot(Ru, self._dR(Wy)))
+        return Xp, Y_k
+
+    def grads(self, n_steps, u_ref, checkpoint_every=None, fused=True):
         """(loss, dl/dlambda, dl/dsigma, dl/db) for l = 1/2 ||W x_N - u_ref||^2;
-        u_ref and the returned dl/db are (rows, image_pitch) device images."""
+        u_ref and the returned dl/db are (rows, image_pitch) device images.
+        fused=False runs each backward iteration as separate library calls."""
         every = checkpoint_every or max(1, int(math.isqrt(n_steps)))
         f = self.fista
         f.reset()
@@ -97,7 +119,11 @@ class UnrolledFista:
         Xp = wt_synth_adjoint(self.wt, e)
         Y = torch.zeros_like(Xp)
         db = torch.zeros_like(self.b)
-        tau_terms, sigma_terms = [], []
+        dev = Xp.device
+        acc = torch.zeros(2, dtype=torch.float64, device=dev)  # dl/dtau, dl/dsigma
+        tau_terms, sigma_terms = [acc[0:1]], [acc[1:2]]
+        if fused and self._vjp_ws is None:
+            self._vjp_ws = f.vjp_workspace()
         inv_l = 1.0 / self.L
         for s in sorted(ckpt, reverse=True):
             stop = min(s + every, n_steps)
@@ -107,23 +133,14 @@ class UnrolledFista:
             f.state.t, f.state.k = t0, s
             xs, ys = self._run(s, stop, keep=True)  # xs[i] = x_{s+i}
             for k in range(stop - 1, s - 1, -1):
-                beta = betas[k]
-                X = axpby(1.0, Xp, 1.0 + beta, Y)
-                zbar, sd = prox_vjp(xs[k + 1 - s], X)
-                tau_terms.append(sd)
-                u = wt_synth(self.wt, zbar)
-                Ru = blur(self.R, u)
-                q = wt_synth_adjoint(self.wt, blur_adjoint(self.R, Ru))
-                Y_k = axpby(1.0, zbar, -inv_l, q)
-                Xp = axpby(-beta, Y, 0.0, Y)
-                axpby(1.0, db, inv_l, Ru, out=db)
-                Wy = wt_synth(self.wt, ys[k - s])
-                r = axpby(1.0, blur(self.R, Wy), -1.0, self.b)
-                sigma_terms.append(self._img_dot(self._dR(u), r))
-                sigma_terms.append(self._img_dot(Ru, self._dR(Wy)))
-                Y = Y_k
-        dtau = -sum(float(v) for v in tau_terms)
-        dsigma = -inv_l * sum(float(v) for v in sigma_terms)
+                if fused:
+                    fista_vjp_step(f, self.dR, xs[k + 1 - s], ys[k - s], betas[k], Xp, Y, db, acc[0:1], acc[1:2],
+                                   self._vjp_ws)
+                else:
+                    Xp, Y = self._back_pieces(k, betas[k], xs[k + 1 - s], ys[k - s], Xp, Y, db, tau_terms,
+                                              sigma_terms)
+        dtau = -sum(float(v) for v in tau_terms[1:]) + float(acc[0])
+        dsigma = sum(float(v) for v in sigma_terms)
         return loss, dtau * inv_l, dsigma, db
 
 

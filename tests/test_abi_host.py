@@ -185,3 +185,43 @@ def test_differentiation_entry_validation(lib):
     assert lib.fista_prox_vjp(-1, None, None, None, None, None, 0, None) == -2
     assert lib.fista_prox_vjp(4, fake, fake, fake, fake, None, 0, None) == -7
     assert lib.adjwt_reduce_workspace_size() >= 8
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="fake-pointer validation runs on the host only")
+def test_vjp_step_validation(lib):
+    """fista_vjp_step rejects bad problems, pointers and workspaces before any
+    launch; its workspace holds at least the seven images and three coefficient
+    vectors it uses.  Fake device addresses are never dereferenced; a zeroed
+    host buffer stands in for a blur plan of an empty image (blur plans hold
+    device taps and cannot be created without a GPU)."""
+    from paper_1707_02018_gb300._lib import FistaProblem
+    rc, wt = _plan(lib, 64, 48, 2, 1, 3)   # db2, PER: no boundary tables to upload
+    assert rc == 0
+    zero_plan = (C.c_char * 4096)()
+    R = C.cast(zero_plan, C.c_void_p)
+    a, ws = 0x10000000, 0x30000000
+    prob = FistaProblem(wt, R, a, 0.01, 2.0, 0)
+    try:
+        need = lib.adjwt_fista_vjp_workspace_size(C.byref(prob))
+        assert need >= 7 * 64 * 48 * 4 + 3 * 64 * 48 * 4
+        assert lib.adjwt_fista_vjp_workspace_size(None) == 0
+
+        def call(x=a, dsig=None, d1=None, d2=None, w=ws, nbytes=need):
+            return lib.fista_vjp_step(C.byref(prob), d1, d2, x, a, 0.5, a, a, None, a, dsig, w, nbytes, None)
+
+        assert lib.fista_vjp_step(None, None, None, a, a, 0.5, a, a, None, a, None, ws, need, None) == -1
+        assert call(x=None) == -1                     # NULL x_next
+        assert call(x=a + 4) == -3                    # misaligned vector
+        assert call(dsig=a) == -1                     # dsigma without the dR plans
+        assert call(w=None) == -7                     # no workspace
+        assert call(w=ws + 16) == -7                  # misaligned workspace
+        assert call(nbytes=need - 1) == -7            # small workspace
+        assert call() == -2                           # blur plan of another (empty) image
+        prob.gradient = 1
+        assert call() == -1                           # W^dagger iteration: not differentiable
+        prob.gradient, prob.lipschitz = 0, 0.0
+        assert call() == -1                           # L = 0
+        prob.lipschitz, prob.blur = 2.0, None
+        assert call() == -1                           # no blur plan
+    finally:
+        lib.adjwt_wt_plan_destroy(wt)

@@ -95,6 +95,13 @@ def test_unrolled_gradients_match_oracle(adj, wavelet, mode, bc):
     once = un.grads(steps, wt.image(img), checkpoint_every=steps)
     for other in (again, once):
         assert other[0] == loss and other[1] == dlam and other[2] == dsig and torch.equal(other[3], db)
+    # the one-call backward step (fista_vjp_step) against the same step built
+    # from the separate library calls: the same kernels, so the same values up
+    # to the order of the float64 accumulation of dl/dtau and dl/dsigma
+    lp, dlp, dsp, dbp = un.grads(steps, wt.image(img), checkpoint_every=3, fused=False)
+    assert lp == loss
+    assert abs(dlp - dlam) <= 1e-9 * abs(dlam) and abs(dsp - dsig) <= 1e-9 * abs(dsig)
+    assert rel_err(dbp[:, :cols].double().cpu().numpy(), db_np) <= 1e-6
     assert adj.device_status() == 0
 
 
