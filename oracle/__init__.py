@@ -23,10 +23,13 @@ Modules
   unrolled   -- unrolled FISTA and its reverse-mode derivative with respect to
                 lambda, the PSF width and b (the chain rule of Sec. I).
   layout     -- band sizes and the packed coefficient order.
+  cnn        -- the learned warm start x_0 = W^dagger u_hat for FISTA (Sec. I-B
+                starts from zero; the 8-layer 3x3 network that computes u_hat
+                from b is not in the paper), its loss gradient and Adam.
 
 Every function states the passage it follows.  Functions whose result cannot
 be pinned independently say "parity unpinned" in their docstring; at present
 every function has at least one independent pin in ``tests/test_oracle_*``.
 """
 
-from . import filters, extension, layout, wavelet, blur, conv, fista, unrolled  # noqa: F401
+from . import filters, extension, layout, wavelet, blur, conv, fista, unrolled, cnn  # noqa: F401

@@ -16,6 +16,10 @@ with the same structure:
   decaying channels of Sec. II), plus a perturbed estimate (h_est, s_est) at
   which gradients are taken, and observation noise of std 0.005 (Sec. II);
 * `random_vector`: N(0,1) start vectors (power iteration) and test vectors.
+* `he_normal_params`: initial weights of a stack of 3x3 convolution layers,
+  N(0, 2 / (9 Cin)) per weight (He et al.'s fan-in scaling for ReLU), the last
+  layer scaled by `last_scale`, biases 0, concatenated layer by layer as
+  (weights in (Cout, Cin, 3, 3) order, then Cout biases).
 
 Every draw uses numpy's PCG64 generator seeded by the caller.
 """
@@ -74,3 +78,15 @@ def channel_problem(batch: int, n: int, k: int, seed: int, noise_std: float = 0.
     h_est = h + perturb * g.standard_normal((batch, k)) * np.exp(-np.arange(k) / tau)[None, :]
     noise = noise_std * g.standard_normal((batch, n + k - 1))
     return {"s": s, "h": h, "noise": noise, "s_est": s_est, "h_est": h_est}
+
+
+def he_normal_params(shapes, seed: int, last_scale: float = 0.1) -> np.ndarray:
+    """Flat initial parameters for 3x3 layers of (Cout, Cin) `shapes`."""
+    g = rng(seed)
+    parts = []
+    for i, (co, ci) in enumerate(shapes):
+        w = g.standard_normal(co * ci * 9) * np.sqrt(2.0 / (9 * ci))
+        if i == len(shapes) - 1:
+            w *= last_scale
+        parts += [w, np.zeros(co)]
+    return np.concatenate(parts)
