@@ -67,6 +67,17 @@ PROTOTYPES = {
     "adjwt_dot": (C.c_int, [C.c_int, I64, I64, VP, VP, VP, VP, SZ, VP]),
     "fista_prox_vjp": (C.c_int, [I64, VP, VP, VP, VP, VP, SZ, VP]),
     "adjwt_fista_vjp_workspace_size": (SZ, [C.POINTER(FistaProblem)]),
+    "adjwt_cnn_param_count": (SZ, []),
+    "adjwt_cnn_packed_bytes": (SZ, []),
+    "adjwt_cnn_activation_bytes": (SZ, [C.c_int, C.c_int, C.c_int]),
+    "adjwt_cnn_workspace_size": (SZ, [C.c_int, C.c_int, C.c_int]),
+    "adjwt_cnn_wgrad_workspace_size": (SZ, []),
+    "cnn_pack": (C.c_int, [VP, VP, VP]),
+    "cnn_forward": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, I64, VP, VP, VP, VP, VP]),
+    "cnn_backward": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, I64, VP, VP, VP, VP, VP, VP, SZ, VP]),
+    "cnn_adam": (C.c_int, [I64, VP, VP, VP, VP, I64, C.c_double, C.c_double, C.c_double, C.c_double, VP]),
+    "cnn_conv32": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, C.c_int, VP, VP, VP]),
+    "cnn_conv32_wgrad": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, SZ, VP]),
     "fista_vjp_step": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, VP, C.c_double, VP, VP, VP, VP, VP, VP, SZ,
                                  VP]),
     "adjwt_fista_objective": (C.c_int, [C.POINTER(FistaProblem), VP, VP, SZ, DP, VP]),

@@ -30,7 +30,8 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    import glob
+    text = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?(?:int|void|size_t|char)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
@@ -225,3 +226,30 @@ def test_vjp_step_validation(lib):
         assert call() == -1                           # no blur plan
     finally:
         lib.adjwt_wt_plan_destroy(wt)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="fake-pointer validation runs on the host only")
+def test_cnn_entry_validation(lib):
+    """The learned-warm-start entries reject bad sizes, pointers and
+    workspaces before any launch (fake addresses are never dereferenced)."""
+    a = 0x10000000
+    assert lib.adjwt_cnn_param_count() == 56097
+    assert lib.adjwt_cnn_packed_bytes() == 6 * 2 * 18 * 1024
+    assert lib.adjwt_cnn_activation_bytes(2, 8, 8) == 7 * 2 * 8 * 8 * 32 * 2
+    assert lib.adjwt_cnn_activation_bytes(-1, 8, 8) == 0
+    assert lib.adjwt_cnn_workspace_size(2, 8, 8) >= 2 * 8 * 8 * (4 + 2 * 64)
+    assert lib.cnn_forward(-1, 8, 8, a, 8, a, a, a, a, None) == -2
+    assert lib.cnn_forward(0, 8, 8, None, 8, None, None, None, None, None) == 0     # empty batch
+    assert lib.cnn_forward(1, 8, 8, a, 4, a, a, a, a, None) == -2                    # pitch < cols
+    assert lib.cnn_forward(1, 8, 8, a, 8, None, a, a, a, None) == -1                 # no params
+    assert lib.cnn_forward(1, 8, 8, a + 4, 8, a, a, a, a, None) == -3                # misaligned b
+    assert lib.cnn_backward(1, 8, 8, a, a, a, 8, a, a, a, a, a, None, 0, None) == -7  # no workspace
+    assert lib.cnn_backward(1, 8, 8, a, a, a, 8, a, a, a, a, a, a + 16, 1 << 30, None) == -7  # misaligned
+    assert lib.cnn_adam(10, a, a, a, a, 0, 1e-3, 0.9, 0.999, 1e-8, None) == -1      # step 0
+    assert lib.cnn_adam(10, a, a, a, a, 1, 1e-3, 1.0, 0.999, 1e-8, None) == -1      # beta1 = 1
+    assert lib.cnn_adam(10, a, a, a, a, 1, 1e-3, 0.9, 0.999, 0.0, None) == -1       # eps = 0
+    assert lib.cnn_adam(0, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 0
+    assert lib.cnn_conv32(1, 4, 4, a, a, None, 1, None, a + 16, None) == -4          # out overlaps in
+    assert lib.cnn_conv32(1, 4, 4, a, None, None, 1, None, a + 4096, None) == -1
+    assert lib.cnn_conv32_wgrad(1, 4, 4, a, a, a, a, None, 0, None) == -7
+    assert lib.cnn_pack(None, a, None) == -1

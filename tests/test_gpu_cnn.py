@@ -1,0 +1,182 @@
+"""The learned warm start on the GPU against the float64 oracle (oracle/cnn.py):
+the tensor-core 32 -> 32 layer (forward, and the data gradient with the ReLU
+mask), its weight gradient, the whole network's forward and loss gradient,
+Adam, training, and the warm start itself.
+
+Tolerances.  A 32 -> 32 output is a float32 sum of 288 bf16 x bf16 products
+rounded once to bf16: |got - exact| <= 2^-8 |exact| (the rounding) +
+2^-20 sum |terms| (float32 accumulation, 288 terms).  Whole-network values
+compare with the oracle's bf16 storage emulation; they differ where the
+float32 and float64 sums round to neighbouring bf16 values, which moves a
+few elements by one bf16 ulp, so those compare in relative L2 norm.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn as ocnn
+from synthetic_inputs import he_normal_params, piecewise_smooth_image, random_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    import paper_1707_02018_gb300 as adj
+    from paper_1707_02018_gb300 import warmstart
+    adj.lib()
+    return warmstart
+
+
+def _bf16_dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).cuda().contiguous()
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _params(seed, last_scale=0.1):
+    return he_normal_params(ocnn.layer_shapes(), seed, last_scale)
+
+
+def _check_layer(got, exact, bound, what):
+    err = np.abs(got - exact)
+    tol = 2.0 ** -8 * np.abs(exact) + 2.0 ** -20 * bound + 1e-30
+    bad = err > tol
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} outside, worst {np.max(err / tol):.2f}x"
+
+
+@pytest.mark.parametrize("n,rows,cols", [(2, 10, 200), (1, 3, 128), (1, 1, 1), (3, 5, 37)])
+def test_conv32_forward_matches_oracle(ws, n, rows, cols):
+    """Tiles of 4 x 128 with ragged rows and columns, a single pixel, a
+    partial tile smaller than the MMA."""
+    theta = _params(1)
+    net = ws.WarmStartNet(theta)
+    layer = 3
+    w, c = ocnn.unflatten(theta)[layer]
+    x = ocnn.round_bf16(np.maximum(random_vector((n, rows, cols, 32), 2), -0.5))
+    got = _np(ws.conv32(n, rows, cols, _bf16_dev(x), ws.packed_layer(net, layer, 0),
+                        bias=net.params[ocnn.flat_offsets()[0][layer][1]:][:32], relu=True))
+    wb = ocnn.round_bf16(w)
+    exact = np.maximum(ocnn.conv3x3(x, wb, c), 0.0)
+    bound = ocnn.conv3x3(np.abs(x), np.abs(wb), np.abs(c))
+    _check_layer(got, exact, bound, "conv32 forward")
+
+
+@pytest.mark.parametrize("n,rows,cols", [(2, 9, 140), (1, 4, 5)])
+def test_conv32_data_gradient_matches_oracle(ws, n, rows, cols):
+    """The data-gradient block applies the layer's adjoint (flipped taps,
+    swapped channels) and the mask [a > 0] of the layer below."""
+    theta = _params(3)
+    net = ws.WarmStartNet(theta)
+    layer = 5
+    w, _ = ocnn.unflatten(theta)[layer]
+    wb = ocnn.round_bf16(w)
+    dz = ocnn.round_bf16(random_vector((n, rows, cols, 32), 4) * 1e-3)
+    a_below = ocnn.round_bf16(np.maximum(random_vector((n, rows, cols, 32), 5), 0.0))
+    got = _np(ws.conv32(n, rows, cols, _bf16_dev(dz), ws.packed_layer(net, layer, 1), mask=_bf16_dev(a_below)))
+    dx, _, _ = ocnn.conv3x3_backward(np.zeros((n, rows, cols, 32)), wb, dz)
+    exact = dx * (a_below > 0)
+    bound, _, _ = ocnn.conv3x3_backward(np.zeros((n, rows, cols, 32)), np.abs(wb), np.abs(dz))
+    _check_layer(got, exact, bound, "conv32 data gradient")
+    assert np.all(got[a_below <= 0] == 0.0)
+
+
+@pytest.mark.parametrize("n,rows,cols", [(2, 10, 200), (1, 1, 3)])
+def test_conv32_weight_gradient_matches_oracle(ws, n, rows, cols):
+    x = ocnn.round_bf16(np.maximum(random_vector((n, rows, cols, 32), 6), 0.0))
+    dz = ocnn.round_bf16(random_vector((n, rows, cols, 32), 7))
+    gw, gb = ws.conv32_wgrad(n, rows, cols, _bf16_dev(x), _bf16_dev(dz))
+    _, dw, db = ocnn.conv3x3_backward(x, np.zeros((32, 32, 3, 3)), dz)
+    _, bw, bb = ocnn.conv3x3_backward(np.abs(x), np.zeros((32, 32, 3, 3)), np.abs(dz))
+    # exact bf16 products, float32 sums over <= 4 x 128 pixels per CTA, float64 across CTAs
+    assert np.all(np.abs(_np(gw) - dw) <= 1e-5 * bw + 1e-30)
+    assert np.all(np.abs(_np(gb) - db) <= 1e-5 * bb + 1e-30)
+
+
+def _images(n, rows, cols, seed):
+    """(b, u): clean images u and their observations b = R u + noise (9 x 9
+    Gaussian, sigma 1.5, symmetric boundary)."""
+    from oracle import blur as oblur
+    from synthetic_inputs import gaussian_noise
+    q = oblur.gaussian_psf(9, 1.5)
+    u = np.stack([piecewise_smooth_image(rows, cols, seed + i) for i in range(n)])
+    b = np.stack([oblur.blur(u[i], q, q, "sym") + gaussian_noise((rows, cols), seed + 50 + i, 1e-2)
+                  for i in range(n)])
+    return b, u
+
+
+def _dev_images(a, pitch):
+    n, rows, cols = a.shape
+    t = torch.zeros(n, rows, pitch, dtype=torch.float32)
+    t[:, :, :cols] = torch.tensor(a, dtype=torch.float32)
+    return t.cuda()
+
+
+def test_network_forward_and_gradient_match_oracle(ws):
+    n, rows, cols, pitch = 2, 12, 136, 140
+    theta = _params(8, last_scale=1.0)
+    b, u = _images(n, rows, cols, 30)
+    b = b.astype(np.float32).astype(np.float64)
+    u = u.astype(np.float32).astype(np.float64)
+    net = ws.WarmStartNet(theta)
+    bd, ud = _dev_images(b, pitch), _dev_images(u, pitch)
+    uh = net.forward(bd, rows, cols)
+    want_u, _ = ocnn.forward(theta, b, bf16=True)
+    got_u = uh[:, :, :cols].double().cpu().numpy()
+    r_u = np.linalg.norm((got_u - b) - (want_u - b)) / np.linalg.norm(want_u - b)
+    net.backward(bd, uh, ud, rows, cols)
+    want_l, want_g = ocnn.backward(theta, b, u, bf16=True)
+    got_g = net.grad.double().cpu().numpy()
+    got_l = float(net.loss)
+    offs, _ = ocnn.flat_offsets()
+    print(f"\nnet(b) rel L2 {r_u:.2e}; loss {got_l:.8e} vs {want_l:.8e}")
+    # one-ulp bf16 flips of a few activations: observed ~1e-4 relative
+    assert r_u <= 2e-3
+    assert abs(got_l - want_l) <= 2e-3 * want_l
+    for layer, (ow, oc) in enumerate(offs):
+        end = offs[layer + 1][0] if layer + 1 < len(offs) else got_g.size
+        r = np.linalg.norm(got_g[ow:end] - want_g[ow:end]) / np.linalg.norm(want_g[ow:end])
+        print(f"layer {layer}: gradient rel L2 {r:.2e}")
+        assert r <= 2e-2, f"layer {layer}"
+    assert torch.equal(net.forward(bd, rows, cols), uh)  # deterministic
+
+
+def test_adam_matches_oracle(ws):
+    theta = _params(9)
+    net = ws.WarmStartNet(theta)
+    g = random_vector(theta.size, 10) * 1e-3
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    t = theta.copy()
+    net.grad.copy_(torch.tensor(g, dtype=torch.float32))
+    gf = net.grad.double().cpu().numpy()
+    for step in range(1, 4):
+        net.adam(lr=1e-2)
+        t, m, v = ocnn.adam_step(t, gf, m, v, step, lr=1e-2)
+    got = net.params.double().cpu().numpy()
+    assert np.allclose(got, t, rtol=1e-5, atol=1e-6)
+
+
+def test_training_reduces_loss_and_warm_start(ws):
+    import paper_1707_02018_gb300 as adj
+    rows = cols = 64
+    b, u = _images(4, rows, cols, 50)
+    wt = adj.WtPlan(rows, cols, 3, "db2", "sym")
+    pitch = wt.image_pitch
+    bd, ud = _dev_images(b, pitch), _dev_images(u, pitch)
+    net = ws.WarmStartNet(_params(11))
+    losses = [float(net.train_step(bd, ud, rows, cols, lr=1e-3)) for _ in range(30)]
+    print("\nlosses", [f"{v:.3e}" for v in losses[::5]])
+    assert losses[-1] < losses[0] and min(losses) < 0.95 * losses[0], losses
+    x0 = net.warm_start(wt, bd[0])
+    uh = net.forward(bd[:1], rows, cols)[0]
+    assert torch.equal(x0, adj.wt_analysis(wt, uh.contiguous()))
+    assert adj.device_status() == 0
+
+
+def test_empty_batch_is_a_no_op(ws):
+    net = ws.WarmStartNet(_params(12))
+    b = torch.zeros(0, 8, 8, device="cuda")
+    assert net.forward(b, 8, 8).numel() == 0
