@@ -404,6 +404,128 @@ BATCH_SIZES = (128, 256, 384, 512, 768, 1024)
 BATCH_WAVELETS = ("db2", "db4", "cdf97")
 
 
+def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=48, n_test=4, target_iters=500,
+                       batch=8, train_steps=600, lr=1e-3, tol=1e-4, check_every=10, ref_iters=3000, max_iters=3000):
+    """The learned-warm-start workload: seeded size^2 problems (piecewise-smooth
+    image, 9x9 Gaussian sigma 1.5 with symmetric boundaries, N(0, 1e-3) noise,
+    `levels`-level CDF 9/7 with symmetric boundaries, lambda = 1e-3).  Targets:
+    the images W x_500 of 500-iteration GPU FISTA solutions; the network is
+    trained on them with the library's kernels (Adam, `train_steps` steps of
+    `batch` images cycling over n_train problems); then, on n_test held-out
+    problems, seconds and iterations of FISTA to (F - F*)/F* <= tol from zero
+    and from x_0 = W^dagger u_hat (inference and W^dagger inside the timed
+    region), F* the smallest objective of a ref_iters run.  The network and its
+    training set are smaller than a production one (20,000 images): this
+    measures the mechanism, not a tuned predictor."""
+    from paper_1707_02018_gb300 import warmstart
+    from synthetic_inputs import gaussian_noise, he_normal_params, piecewise_smooth_image, random_vector
+    p = gaussian_taps(9, 1.5)
+    wt = adj.WtPlan(size, size, levels, wavelet, "sym")
+    bl = adj.BlurPlan(size, size, p, p, "sym")
+    pitch = wt.image_pitch
+    total = n_train + n_test
+    B = torch.zeros(total, size, pitch, dtype=torch.float32, device="cuda")
+    U = torch.zeros_like(B)
+    t0 = time.perf_counter()
+    L = None
+    for i in range(total):
+        seed = 11000 + i
+        img = wt.image(torch.as_tensor(piecewise_smooth_image(size, size, seed)))
+        adj.blur(bl, img, out=B[i])
+        B[i, :, :size] += torch.as_tensor(gaussian_noise((size, size), seed + 1, NOISE), dtype=torch.float32,
+                                          device="cuda")
+        f = adj.Fista(wt, bl, B[i], LAM, 1.0)
+        if L is None:  # the same operator A = R W for every problem
+            L = f.lipschitz(wt.pack(random_vector(wt.logical_size, 12000)), iters=30)
+        f.set_lipschitz(L)
+        f.reset()
+        for _ in range(target_iters):
+            f.step()
+        adj.wt_synth(wt, f.x, image=U[i])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    net = warmstart.WarmStartNet(he_normal_params(warmstart.LAYER_SHAPES, 13000))
+    nb = n_train // batch
+    losses = []
+    for k in range(3):  # warm-up (allocations, first launches)
+        net.forward(B[:batch], size, size)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(train_steps):
+        j = k % nb
+        loss = net.train_step(B[j * batch:(j + 1) * batch], U[j * batch:(j + 1) * batch], size, size, lr=lr)
+        if k % 100 == 0 or k == train_steps - 1:
+            losses.append(float(loss))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # one traced step: per-kernel device times
+    adj.trace_enable(512)
+    adj.trace_reset()
+    net.train_step(B[:batch], U[:batch], size, size, lr=0.0)
+    torch.cuda.synchronize()
+    recs = adj.trace_records()
+    adj.trace_enable(0)
+    per = {}
+    for name, _, ms in recs:
+        c, t = per.get(name, (0, 0.0))
+        per[name] = (c + 1, t + ms)
+    px = batch * size * size
+    fwd = per.get("cnn_conv32_tc", (1, float("nan")))
+    bwd = per.get("cnn_conv32_tc_bwd", (1, float("nan")))
+    wgr = per.get("cnn_conv32_wgrad", (1, float("nan")))
+    flop = 2.0 * 288 * 32 * px
+    kern = {name: {"launches": c, "ms_total": t} for name, (c, t) in sorted(per.items())}
+    conv = {"forward_us": 1e3 * fwd[1] / fwd[0], "data_grad_us": 1e3 * bwd[1] / bwd[0],
+            "weight_grad_us": 1e3 * wgr[1] / wgr[0],
+            "forward_GBps": 128.0 * px / (fwd[1] / fwd[0] * 1e-3) / 1e9,
+            "data_grad_GBps": 192.0 * px / (bwd[1] / bwd[0] * 1e-3) / 1e9,
+            "forward_TFLOPs": flop / (fwd[1] / fwd[0] * 1e-3) / 1e12,
+            "weight_grad_TFLOPs": flop / (wgr[1] / wgr[0] * 1e-3) / 1e12,
+            "bytes_per_pixel": {"forward": 128, "data_grad": 192}}
+
+    def time_to_tol(f, x0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if x0 is not None:
+            x0 = x0()
+        f.reset(x0)
+        it, reached = 0, False
+        while it < max_iters:
+            it += 1
+            val = f.step(objective=(it % check_every == 0))
+            if val is not None and (val - fstar) / fstar <= tol:
+                reached = True
+                break
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, it, reached
+
+    tests = []
+    for i in range(n_train, total):
+        f = adj.Fista(wt, bl, B[i], LAM, L)
+        f.reset()
+        fstar = float("inf")
+        for k in range(1, ref_iters + 1):
+            val = f.step(objective=(k % 50 == 0 or k == ref_iters))
+            if val is not None:
+                fstar = min(fstar, val)
+        f0 = f.objective(torch.zeros_like(f.x))
+        xw = net.warm_start(wt, B[i])
+        fw = f.objective(xw)
+        zs, zi, zr = time_to_tol(f, None)
+        ws_, wi, wr = time_to_tol(f, lambda: net.warm_start(wt, B[i]))
+        tests.append({"F_star": fstar, "rel_F_at_zero": (f0 - fstar) / fstar, "rel_F_at_warm": (fw - fstar) / fstar,
+                      "zero_start": {"seconds": zs, "iterations": zi, "reached": zr},
+                      "warm_start": {"seconds": ws_, "iterations": wi, "reached": wr}})
+    zsum = sum(t["zero_start"]["seconds"] for t in tests)
+    wsum = sum(t["warm_start"]["seconds"] for t in tests)
+    return {"size": size, "levels": levels, "wavelet": wavelet, "train_images": n_train, "test_images": n_test,
+            "target_iterations": target_iters, "targets_sec": gen_s, "batch": batch, "train_steps": train_steps,
+            "train_sec": train_s, "train_images_per_sec": train_steps * batch / train_s,
+            "loss_every_100_steps": losses, "conv32": conv, "train_step_kernels": kern, "held_out": tests,
+            "zero_start_sec_total": zsum, "warm_start_sec_total": wsum, "speedup": zsum / wsum}
+
+
 def batch_problems(adj, torch, seed=7000):
     from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
     rng = np.random.default_rng(seed)
@@ -660,6 +782,7 @@ def ours(args):
         extra["fista_batched_vs_plain_to_1e-4"] = batched_vs_plain(adj, torch)
         extra["fista_adjoint_vs_pinv"] = adjoint_vs_pinv(adj, torch, probs[1])
         extra["unrolled_fista_gradient"] = unrolled_gradient_timing(adj, torch)
+        extra["learned_warm_start"] = learned_warm_start(adj, torch)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

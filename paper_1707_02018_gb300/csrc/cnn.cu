@@ -64,7 +64,7 @@ constexpr int kWgSmem = kInBytes + kDzBytes + 128;
 constexpr int kWgStride = 9 * kC * kC + kC;   // floats of one CTA's partial
 constexpr int kWgMaxGrid = 320;
 constexpr int kThinStride = 9 * kC + kC + 1;  // 321
-constexpr int kThinMaxGrid = 640;
+constexpr int kThinMaxGrid = 2432;
 constexpr int kThinThreads = 256;             // 16 channel pairs x 16 row segments
 constexpr int kLossBlocks = 1024;
 
@@ -181,17 +181,19 @@ __global__ void __launch_bounds__(kFwdThreads) k_conv32_tc(int H, int W, int til
   const uint32_t tmem = tmem_holder;
 
   if (tid == 0) {
-    const uint32_t wb = smem_u32(win), bb = smem_u32(wsm);
-#pragma unroll 1
+    // A: 128 pixels (8-row groups 128 bytes apart) x 16 channels (two groups kPlane apart);
+    // B: 32 output channels (8-row groups 128 bytes apart) x 16 channels (two groups 512 apart).
+    // Every operand address stays below 2^18 bytes, so the descriptor at byte offset o is the
+    // base descriptor plus o / 16 (the 14-bit start field never carries): the 72 MMAs issue
+    // with one add each.
+    const uint64_t a0 = umma_desc(smem_u32(win), kPlane, 128), b0 = umma_desc(smem_u32(wsm), 512, 128);
+#pragma unroll
     for (int r = 0; r < kTH; ++r) {
-#pragma unroll 1
+#pragma unroll
       for (int s = 0; s < kKSteps; ++s) {
         const int t = s >> 1, h = s & 1, dy = t / 3, dx = t - 3 * dy;
-        // A: 128 pixels (8-row groups 128 bytes apart) x 16 channels (two groups kPlane apart)
-        const uint64_t a = umma_desc(wb + (r + dy) * kInRow + 2 * h * kPlane + dx * 16, kPlane, 128);
-        // B: 32 output channels (8-row groups 128 bytes apart) x 16 channels (two groups 512 apart)
-        const uint64_t b = umma_desc(bb + s * 1024, 512, 128);
-        umma_bf16(tmem + r * 32, a, b, s > 0);
+        umma_bf16(tmem + r * 32, a0 + (uint64_t)(((r + dy) * kInRow + 2 * h * kPlane + dx * 16) >> 4),
+                  b0 + (uint64_t)(s * 64), s > 0);
       }
     }
     umma_commit(&bar);
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv32_wgrad(int N, int H, in
                                                                 float* __restrict__ part) {
   pdl_entry();
   extern __shared__ unsigned char dyn[];
-  __shared__ float dbred[128];
+  __shared__ float dbred[128][8];
   unsigned char* sm = align128(dyn);
   unsigned char* win = sm;
   unsigned char* dzs = sm + kInBytes;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv32_wgrad(int N, int H, in
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-  float dbacc = 0.0f;
+  float dbacc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   const int64_t tiles = (int64_t)N * tiles_y * tiles_x;
   const uint32_t wb = smem_u32(win), zb = smem_u32(dzs);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -299,10 +301,16 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv32_wgrad(int N, int H, in
           for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], a[mt], b[nt][0], b[nt][1]);
       }
     }
-    if (tid < 128) {  // bias gradient: thread (row, channel)
-      const int r = tid >> 5, ch = tid & 31;
-      const __nv_bfloat16* col = reinterpret_cast<const __nv_bfloat16*>(dzs + r * kDzRow + (ch >> 3) * kDzPlane) + (ch & 7);
-      for (int q = 0; q < kTW; ++q) dbacc += __bfloat162float(col[q * 8]);
+    if (tid < 128) {  // bias gradient: thread (row, channel group, pixel slice) adds 16-byte groups
+      const int r = tid >> 5, g = (tid >> 3) & 3, qq = tid & 7;
+      const uint4* grp = reinterpret_cast<const uint4*>(dzs + r * kDzRow + g * kDzPlane);
+#pragma unroll 4
+      for (int q = qq; q < kTW; q += 8) {
+        float v[8];
+        unpack8(grp[q], v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dbacc[e] += v[e];
+      }
     }
     __syncthreads();
   }
@@ -319,9 +327,17 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_conv32_wgrad(int N, int H, in
       o[(co + 8) * kC + ci] = acc[mt][nt][2];
       o[(co + 8) * kC + ci + 1] = acc[mt][nt][3];
     }
-  if (tid < 128) dbred[tid] = dbacc;
+  if (tid < 128)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) dbred[tid][e] = dbacc[e];
   __syncthreads();
-  if (tid < kC) base[9 * kC * kC + tid] = dbred[tid] + dbred[32 + tid] + dbred[64 + tid] + dbred[96 + tid];
+  if (tid < kC) {  // channel c = 8 g + e: rows r and slices qq of thread r 32 + g 8 + qq
+    const int g = tid >> 3, e = tid & 7;
+    float t = 0.0f;
+    for (int r = 0; r < kTH; ++r)
+      for (int qq = 0; qq < 8; ++qq) t += dbred[r * 32 + g * 8 + qq][e];
+    base[9 * kC * kC + tid] = t;
+  }
 }
 
 // Thin-layer weight gradient: part[cta][t * 32 + c] = sum over image pixels p
@@ -407,46 +423,75 @@ __global__ void __launch_bounds__(kThinThreads) k_thin_wgrad(int N, int H, int W
   }
 }
 
-// out_w[c * 9 + t] = sum_g part[g][t * C + c]; out_b[j] = sum_g part[g][boff + j] (float64 sums, fixed order)
-__global__ void k_reduce_wgrad(int nparts, int stride, const float* __restrict__ part, int C, float* __restrict__ out_w,
-                               int boff, int nb, float* __restrict__ out_b) {
+// out_w[c * 9 + t] = sum_g part[g][t * C + c]; out_b[j] = sum_g part[g][boff + j]
+// (float64 sums in a fixed order).  A block takes 32 consecutive outputs;
+// its eight warps sum the parts g = warp (mod 8), then warp 0 adds the eight.
+__global__ void __launch_bounds__(256) k_reduce_wgrad(int nparts, int stride, const float* __restrict__ part, int C,
+                                                      float* __restrict__ out_w, int boff, int nb,
+                                                      float* __restrict__ out_b) {
   pdl_entry();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double red[8][32];
+  const int j = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + j;
   const int nw = 9 * C;
-  if (i >= nw + nb) return;
-  const int src = i < nw ? i : boff + (i - nw);
+  const bool valid = i < nw + nb;
   double acc = 0.0;
-  for (int g = 0; g < nparts; ++g) acc += part[(int64_t)g * stride + src];
-  if (i < nw)
-    out_w[(i % C) * 9 + i / C] = static_cast<float>(acc);
-  else
-    out_b[i - nw] = static_cast<float>(acc);
+  if (valid) {
+    const int src = i < nw ? i : boff + (i - nw);
+    for (int g = sl; g < nparts; g += 8) acc += part[(int64_t)g * stride + src];
+  }
+  red[sl][j] = acc;
+  __syncthreads();
+  if (sl == 0 && valid) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][j];
+    if (i < nw)
+      out_w[(i % C) * 9 + i / C] = static_cast<float>(t);
+    else
+      out_b[i - nw] = static_cast<float>(t);
+  }
 }
 
 // ------------------------------------------------------------- thin layers
+// The thin layers keep their 32 x 9 weights in shared memory transposed to
+// [tap][channel] and read them as float4 (broadcast: every thread of a warp
+// reads the same address), four channels per load.
 __global__ void __launch_bounds__(256) k_conv_in(int N, int H, int W, const float* __restrict__ img, int64_t pitch,
                                                  const float* __restrict__ p, __nv_bfloat16* __restrict__ out) {
   pdl_entry();
-  __shared__ float w[320];  // w_1 (32 x 9), then c_1
-  for (int i = threadIdx.x; i < 320; i += blockDim.x) w[i] = p[i];
+  __shared__ __align__(16) float wt[9 * kC + kC];  // wt[t][c] = w_1[c][t], then c_1
+  for (int i = threadIdx.x; i < 9 * kC; i += blockDim.x) wt[(i % 9) * kC + i / 9] = p[i];
+  if (threadIdx.x < kC) wt[9 * kC + threadIdx.x] = p[288 + threadIdx.x];
   __syncthreads();
+  const float4* w4 = reinterpret_cast<const float4*>(wt);
   const int64_t total = (int64_t)N * H * W;
   for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < total; pix += (int64_t)gridDim.x * blockDim.x) {
     const int x = static_cast<int>(pix % W), y = static_cast<int>((pix / W) % H), n = static_cast<int>(pix / ((int64_t)W * H));
-    float s[9];
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 c4 = w4[9 * 8 + q];
+      v[4 * q] = c4.x;
+      v[4 * q + 1] = c4.y;
+      v[4 * q + 2] = c4.z;
+      v[4 * q + 3] = c4.w;
+    }
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
       const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      s[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(img + ((int64_t)n * H + yy) * pitch + xx) : 0.0f;
-    }
-    float v[32];
+      const float st = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(img + ((int64_t)n * H + yy) * pitch + xx) : 0.0f;
 #pragma unroll
-    for (int c = 0; c < kC; ++c) {
-      float a = w[288 + c];
-#pragma unroll
-      for (int t = 0; t < 9; ++t) a = fmaf(w[c * 9 + t], s[t], a);
-      v[c] = fmaxf(a, 0.0f);
+      for (int q = 0; q < 8; ++q) {
+        const float4 wv = w4[t * 8 + q];
+        v[4 * q] = fmaf(wv.x, st, v[4 * q]);
+        v[4 * q + 1] = fmaf(wv.y, st, v[4 * q + 1]);
+        v[4 * q + 2] = fmaf(wv.z, st, v[4 * q + 2]);
+        v[4 * q + 3] = fmaf(wv.w, st, v[4 * q + 3]);
+      }
     }
+#pragma unroll
+    for (int c = 0; c < kC; ++c) v[c] = fmaxf(v[c], 0.0f);
     store_pixel(out + pix * kC, v);
   }
 }
@@ -455,14 +500,16 @@ __global__ void __launch_bounds__(256) k_conv_out(int N, int H, int W, const __n
                                                   const float* __restrict__ p, const float* __restrict__ src,
                                                   int64_t pitch, float* __restrict__ out) {
   pdl_entry();
-  __shared__ float w[289];  // w_8 (32 x 9), then c_8
-  for (int i = threadIdx.x; i < 289; i += blockDim.x) w[i] = p[i];
+  __shared__ __align__(16) float wt[9 * kC];  // wt[t][ci] = w_8[ci][t]
+  for (int i = threadIdx.x; i < 9 * kC; i += blockDim.x) wt[(i % 9) * kC + i / 9] = p[i];
   __syncthreads();
+  const float bias = p[288];
+  const float4* w4 = reinterpret_cast<const float4*>(wt);
   const int64_t total = (int64_t)N * H * W;
   for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < total; pix += (int64_t)gridDim.x * blockDim.x) {
     const int x = static_cast<int>(pix % W), y = static_cast<int>((pix / W) % H), n = static_cast<int>(pix / ((int64_t)W * H));
-    float acc = w[288];
-#pragma unroll 1
+    float acc = bias;
+#pragma unroll 3
     for (int t = 0; t < 9; ++t) {
       const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
       if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
@@ -471,8 +518,15 @@ __global__ void __launch_bounds__(256) k_conv_out(int N, int H, int W, const __n
       for (int g = 0; g < 4; ++g) {
         float v[8];
         unpack8(__ldg(q + g), v);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc = fmaf(w[(8 * g + e) * 9 + t], v[e], acc);
+        const float4 wa = w4[t * 8 + 2 * g], wb = w4[t * 8 + 2 * g + 1];
+        acc = fmaf(wa.x, v[0], acc);
+        acc = fmaf(wa.y, v[1], acc);
+        acc = fmaf(wa.z, v[2], acc);
+        acc = fmaf(wa.w, v[3], acc);
+        acc = fmaf(wb.x, v[4], acc);
+        acc = fmaf(wb.y, v[5], acc);
+        acc = fmaf(wb.z, v[6], acc);
+        acc = fmaf(wb.w, v[7], acc);
       }
     }
     const int64_t o = ((int64_t)n * H + y) * pitch + x;
@@ -485,32 +539,37 @@ __global__ void __launch_bounds__(256) k_conv_out_bwd(int N, int H, int W, const
                                                       const float* __restrict__ p, const __nv_bfloat16* __restrict__ a,
                                                       __nv_bfloat16* __restrict__ dz) {
   pdl_entry();
-  __shared__ float w[288];
-  for (int i = threadIdx.x; i < 288; i += blockDim.x) w[i] = p[i];
+  __shared__ __align__(16) float wt[9 * kC];  // wt[t][ci] = w_8[ci][8 - t]: pairs with dout[p + offset_t]
+  for (int i = threadIdx.x; i < 9 * kC; i += blockDim.x) wt[(8 - i % 9) * kC + i / 9] = p[i];
   __syncthreads();
+  const float4* w4 = reinterpret_cast<const float4*>(wt);
   const int64_t total = (int64_t)N * H * W;
   for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < total; pix += (int64_t)gridDim.x * blockDim.x) {
     const int x = static_cast<int>(pix % W), y = static_cast<int>((pix / W) % H), n = static_cast<int>(pix / ((int64_t)W * H));
-    float s[9];
+    float v[32];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {  // s[t] = dout[p + offset_t] pairs with w[8 - t]
+    for (int c = 0; c < kC; ++c) v[c] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
       const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      s[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(dout + ((int64_t)n * H + yy) * W + xx) : 0.0f;
+      const float st = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(dout + ((int64_t)n * H + yy) * W + xx) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 wv = w4[t * 8 + q];
+        v[4 * q] = fmaf(wv.x, st, v[4 * q]);
+        v[4 * q + 1] = fmaf(wv.y, st, v[4 * q + 1]);
+        v[4 * q + 2] = fmaf(wv.z, st, v[4 * q + 2]);
+        v[4 * q + 3] = fmaf(wv.w, st, v[4 * q + 3]);
+      }
     }
     const uint4* mq = reinterpret_cast<const uint4*>(a + pix * kC);
-    float v[32];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       float m[8];
       unpack8(__ldg(mq + g), m);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int c = 8 * g + e;
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + 8 - t], s[t], acc);
-        v[c] = m[e] > 0.0f ? acc : 0.0f;
-      }
+      for (int e = 0; e < 8; ++e)
+        if (!(m[e] > 0.0f)) v[8 * g + e] = 0.0f;
     }
     store_pixel(dz + pix * kC, v);
   }
@@ -618,7 +677,7 @@ int launch_reduce(int nparts, int stride, const float* part, int C, float* out_w
                   cudaStream_t st) {
   const int count = 9 * C + nb;
   ADJWT_TRACED("cnn_reduce_wgrad", 0, st,
-               ADJWT_CUDA_CHECK(pdl_launch(k_reduce_wgrad, dim3((count + 255) / 256), dim3(256), 0, st, nparts, stride,
+               ADJWT_CUDA_CHECK(pdl_launch(k_reduce_wgrad, dim3((count + 31) / 32), dim3(256), 0, st, nparts, stride,
                                            part, C, out_w, boff, nb, out_b)));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;

@@ -85,6 +85,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, uint32_t
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// All but the newest `N` committed groups of this thread are complete.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Record a device-side failure code (first writer wins).
 __device__ __forceinline__ void record_status(int* status, int code) {

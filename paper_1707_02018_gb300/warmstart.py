@@ -20,6 +20,10 @@ import torch
 from . import _lib, _ptr, _stream, lib, workspace, wt_analysis
 
 
+# (Cout, Cin) of the eight 3x3 layers
+LAYER_SHAPES = [(32, 1)] + [(32, 32)] * 6 + [(1, 32)]
+
+
 def param_count():
     return int(lib().adjwt_cnn_param_count())
 
@@ -125,3 +129,42 @@ def packed_layer(net, layer, direction=0):
     block = 18432
     off = ((layer - 1) * 2 + direction) * block
     return net.packed[off:off + block]
+
+
+def _main():
+    """Train the network for a few steps on seeded blurred images
+    (python -m paper_1707_02018_gb300.warmstart --batch 8 --size 512 --steps 5):
+    observations R u + noise of piecewise-smooth images u (9 x 9 Gaussian,
+    sigma 1.5, symmetric boundary), targets u.  Prints the losses."""
+    import argparse
+
+    from synthetic_inputs import gaussian_noise, he_normal_params, piecewise_smooth_image
+
+    from . import BlurPlan, blur
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args()
+    n, size = args.batch, args.size
+    g = [float(v) for v in torch.exp(-0.5 * (torch.arange(9, dtype=torch.float64) - 4) ** 2 / 1.5 ** 2)]
+    g = [v / sum(g) for v in g]
+    bl = BlurPlan(size, size, g, g, "sym")
+    pitch = bl.image_pitch
+    b = torch.zeros(n, size, pitch, dtype=torch.float32, device="cuda")
+    u = torch.zeros_like(b)
+    for i in range(n):
+        u[i, :, :size] = torch.as_tensor(piecewise_smooth_image(size, size, 500 + i), dtype=torch.float32)
+        blur(bl, u[i], out=b[i])
+        b[i, :, :size] += torch.as_tensor(gaussian_noise((size, size), 600 + i, 1e-3), dtype=torch.float32,
+                                          device="cuda")
+    net = WarmStartNet(he_normal_params(LAYER_SHAPES, 700))
+    losses = [float(net.train_step(b, u, size, size, lr=args.lr)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    print("losses", " ".join(f"{v:.4e}" for v in losses))
+
+
+if __name__ == "__main__":
+    _main()

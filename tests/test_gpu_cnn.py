@@ -114,7 +114,18 @@ def _dev_images(a, pitch):
     return t.cuda()
 
 
+def _rel(a, b, scale):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(scale))
+
+
 def test_network_forward_and_gradient_match_oracle(ws):
+    """Two bfloat16 pipelines that add in different orders round a few sums
+    to neighbouring bf16 values, and the one-ulp differences spread through
+    the later layers.  So the whole network compares in relative L2: the GPU
+    must sit much closer to the oracle's bf16 emulation than bf16 storage
+    itself moves the network from exact float64 (1.9 % on u_hat - b, 0.7 to
+    3.5 % per layer's gradient in this case; the GPU measured 0.2 %), and its
+    own distance to the exact network must match the emulation's."""
     n, rows, cols, pitch = 2, 12, 136, 140
     theta = _params(8, last_scale=1.0)
     b, u = _images(n, rows, cols, 30)
@@ -123,24 +134,30 @@ def test_network_forward_and_gradient_match_oracle(ws):
     net = ws.WarmStartNet(theta)
     bd, ud = _dev_images(b, pitch), _dev_images(u, pitch)
     uh = net.forward(bd, rows, cols)
-    want_u, _ = ocnn.forward(theta, b, bf16=True)
     got_u = uh[:, :, :cols].double().cpu().numpy()
-    r_u = np.linalg.norm((got_u - b) - (want_u - b)) / np.linalg.norm(want_u - b)
+    emu_u, _ = ocnn.forward(theta, b, bf16=True)
+    ex_u, _ = ocnn.forward(theta, b, bf16=False)
+    storage = _rel(emu_u, ex_u, ex_u - b)
+    r_emu, r_ex = _rel(got_u, emu_u, emu_u - b), _rel(got_u, ex_u, ex_u - b)
+    print(f"\nnet(b): gpu vs emulation {r_emu:.2e}, gpu vs exact {r_ex:.2e}, emulation vs exact {storage:.2e}")
+    assert r_emu <= 0.25 * storage and r_ex <= 1.5 * storage
     net.backward(bd, uh, ud, rows, cols)
-    want_l, want_g = ocnn.backward(theta, b, u, bf16=True)
+    emu_l, emu_g = ocnn.backward(theta, b, u, bf16=True)
+    ex_l, ex_g = ocnn.backward(theta, b, u, bf16=False)
     got_g = net.grad.double().cpu().numpy()
     got_l = float(net.loss)
+    print(f"loss {got_l:.8e}, emulation {emu_l:.8e}, exact {ex_l:.8e}")
+    assert abs(got_l - emu_l) <= 2e-3 * emu_l
     offs, _ = ocnn.flat_offsets()
-    print(f"\nnet(b) rel L2 {r_u:.2e}; loss {got_l:.8e} vs {want_l:.8e}")
-    # one-ulp bf16 flips of a few activations: observed ~1e-4 relative
-    assert r_u <= 2e-3
-    assert abs(got_l - want_l) <= 2e-3 * want_l
-    for layer, (ow, oc) in enumerate(offs):
+    for layer, (ow, _) in enumerate(offs):
         end = offs[layer + 1][0] if layer + 1 < len(offs) else got_g.size
-        r = np.linalg.norm(got_g[ow:end] - want_g[ow:end]) / np.linalg.norm(want_g[ow:end])
-        print(f"layer {layer}: gradient rel L2 {r:.2e}")
-        assert r <= 2e-2, f"layer {layer}"
-    assert torch.equal(net.forward(bd, rows, cols), uh)  # deterministic
+        sl = slice(ow, end)
+        storage = _rel(emu_g[sl], ex_g[sl], ex_g[sl])
+        r_emu, r_ex = _rel(got_g[sl], emu_g[sl], emu_g[sl]), _rel(got_g[sl], ex_g[sl], ex_g[sl])
+        print(f"layer {layer}: gradient gpu vs emulation {r_emu:.2e}, vs exact {r_ex:.2e}, storage {storage:.2e}")
+        assert r_emu <= 0.25 * storage and r_ex <= 1.5 * storage, f"layer {layer}"
+    again = net.forward(bd, rows, cols)  # deterministic (the pad columns are not written)
+    assert torch.equal(again[:, :, :cols], uh[:, :, :cols])
 
 
 def test_adam_matches_oracle(ws):
