@@ -414,7 +414,9 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
     `batch` images cycling over n_train problems); then, on n_test held-out
     problems, seconds and iterations of FISTA to (F - F*)/F* <= tol from zero
     and from x_0 = W^dagger u_hat (inference and W^dagger inside the timed
-    region), F* the smallest objective of a ref_iters run.  The network and its
+    region), F* the smallest objective of a ref_iters run; and the first
+    checked zero-start iteration whose objective is at or below F(x_0) (the
+    iterations the prediction stands for).  The network and its
     training set are smaller than a production one (20,000 images): this
     measures the mechanism, not a tuned predictor."""
     from paper_1707_02018_gb300 import warmstart
@@ -484,21 +486,24 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
             "weight_grad_TFLOPs": flop / (wgr[1] / wgr[0] * 1e-3) / 1e12,
             "bytes_per_pixel": {"forward": 128, "data_grad": 192}}
 
-    def time_to_tol(f, x0):
+    def time_to_tol(f, x0, match=None):
+        """(seconds, iterations, reached, first checked iteration with F <= match)."""
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if x0 is not None:
             x0 = x0()
         f.reset(x0)
-        it, reached = 0, False
+        it, reached, matched = 0, False, None
         while it < max_iters:
             it += 1
             val = f.step(objective=(it % check_every == 0))
+            if val is not None and match is not None and matched is None and val <= match:
+                matched = it
             if val is not None and (val - fstar) / fstar <= tol:
                 reached = True
                 break
         torch.cuda.synchronize()
-        return time.perf_counter() - t0, it, reached
+        return time.perf_counter() - t0, it, reached, matched
 
     tests = []
     for i in range(n_train, total):
@@ -512,9 +517,10 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
         f0 = f.objective(torch.zeros_like(f.x))
         xw = net.warm_start(wt, B[i])
         fw = f.objective(xw)
-        zs, zi, zr = time_to_tol(f, None)
-        ws_, wi, wr = time_to_tol(f, lambda: net.warm_start(wt, B[i]))
+        zs, zi, zr, zm = time_to_tol(f, None, match=fw)
+        ws_, wi, wr, _ = time_to_tol(f, lambda: net.warm_start(wt, B[i]))
         tests.append({"F_star": fstar, "rel_F_at_zero": (f0 - fstar) / fstar, "rel_F_at_warm": (fw - fstar) / fstar,
+                      "zero_start_iterations_to_F_warm": zm,
                       "zero_start": {"seconds": zs, "iterations": zi, "reached": zr},
                       "warm_start": {"seconds": ws_, "iterations": wi, "reached": wr}})
     zsum = sum(t["zero_start"]["seconds"] for t in tests)
