@@ -79,7 +79,9 @@ def channel_bytes():
 
 # DRAM bytes (read + write) of one launch of the bench workload, measured by ncu on the current kernels
 # (an entry is removed whenever its kernel changes, until it is captured again)
-NCU_TRAFFIC = {"conv_gradient": 134448896 + 35901440}
+NCU_TRAFFIC = {"conv_gradient": 134448896 + 35901440,
+               # k_conv32_tc<false>, 8 x 512^2 (one ncu capture: dram read + write bytes per launch)
+               "cnn_conv32_tc": 134286848 + 84610304}
 
 
 def step_bytes():
@@ -485,6 +487,12 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
             "forward_TFLOPs": flop / (fwd[1] / fwd[0] * 1e-3) / 1e12,
             "weight_grad_TFLOPs": flop / (wgr[1] / wgr[0] * 1e-3) / 1e12,
             "bytes_per_pixel": {"forward": 128, "data_grad": 192}}
+    pk = peaks()
+    fwd_gbs = 128.0 * px / (fwd[1] / fwd[0] * 1e-3) / 1e9
+    conv["roofline"] = {"kernel": "cnn_conv32_tc (forward)", "bound": "hbm", "achieved": fwd_gbs,
+                        "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": fwd_gbs / pk["hbm_gbs"],
+                        "traffic": NCU_TRAFFIC["cnn_conv32_tc"], "peak_source": pk["source"],
+                        "algorithmic_bytes": 128 * px}
 
     def time_to_tol(f, x0, match=None):
         """(seconds, iterations, reached, first checked iteration with F <= match)."""

@@ -139,3 +139,37 @@ def test_unrolled_edge_cases(adj, steps, every, bc, mode):
     assert abs(dlam - want[1]) <= 1e-5 * max(abs(want[1]), 1e-6)
     assert abs(dsig - want[2]) <= 1e-5 * max(abs(want[2]), 1e-6)
     assert rel_err(db[:, :cols].double().cpu().numpy(), want[3]) <= 1e-5
+
+
+def test_vjp_step_argument_errors(adj):
+    """fista_vjp_step rejects, before any launch, a derivative plan of another
+    image, dsigma without the plans, a small workspace and the W^dagger
+    iteration (its backward would not be the chain rule's A^*)."""
+    rows = cols = 32
+    S, img, nco = _problem(adj, rows, cols, 2, "db2", "sym", "sym", 5, 1.1, 0.02, 71)
+    wt = adj.WtPlan(rows, cols, 2, "db2", "sym")
+    g, dg = adj.gaussian_taps(5, 1.1)
+    R = adj.BlurPlan(rows, cols, g, g, "sym")
+    dR = (adj.BlurPlan(rows, cols, dg, g, "sym"), adj.BlurPlan(rows, cols, g, dg, "sym"))
+    other = (adj.BlurPlan(rows, 16, dg, g, "sym"), adj.BlurPlan(rows, 16, g, dg, "sym"))
+    b = wt.image(S.b)
+    f = adj.Fista(wt, R, b, 0.02, S.L)
+    ws = f.vjp_workspace()
+    v = [torch.zeros(wt.num_coeffs, device="cuda") for _ in range(4)]
+    acc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.fista_vjp_step(f, other, v[0], v[1], 0.5, v[2], v[3], None, acc[0:1], acc[1:2], ws)
+    assert e.value.code == -2
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.fista_vjp_step(f, None, v[0], v[1], 0.5, v[2], v[3], None, acc[0:1], acc[1:2], ws)
+    assert e.value.code == -1
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.fista_vjp_step(f, dR, v[0], v[1], 0.5, v[2], v[3], None, acc[0:1], acc[1:2], ws[:-256])
+    assert e.value.code == -7
+    fp = adj.Fista(wt, R, b, 0.02, S.L, gradient="pinv")
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.fista_vjp_step(fp, dR, v[0], v[1], 0.5, v[2], v[3], None, acc[0:1], acc[1:2], fp.vjp_workspace())
+    assert e.value.code == -1
+    # the valid call goes through and leaves finite accumulators
+    adj.fista_vjp_step(f, dR, v[0], v[1], 0.5, v[2], v[3], None, acc[0:1], acc[1:2], ws)
+    assert torch.isfinite(acc).all()
