@@ -131,3 +131,57 @@ def test_adam_first_step_closed_form():
         t_new, m, v = cnn.adam_step(t, g, m, v, k, lr=0.01)
         assert np.allclose(t - t_new, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-9)
         t = t_new
+
+
+def test_zero_last_layer_is_the_residual_identity():
+    """With the last layer's weights zero, u_hat = b + c_8 exactly, whatever
+    the hidden layers compute; d loss / d c_8 is then the mean of
+    u_hat - u_ref, and every earlier parameter has zero gradient (the
+    hidden activations do not reach the output)."""
+    theta = he_normal_params(cnn.layer_shapes(), 31, last_scale=1.0)
+    params = cnn.unflatten(theta)
+    params[-1] = (np.zeros_like(params[-1][0]), np.array([0.25]))
+    theta = cnn.flatten(params)
+    b = random_vector((2, 7, 9), 32)
+    u = random_vector((2, 7, 9), 33)
+    u_hat, _ = cnn.forward(theta, b)
+    assert np.array_equal(u_hat, b + 0.25)
+    _, g = cnn.backward(theta, b, u)
+    offs, _ = cnn.flat_offsets()
+    assert np.isclose(g[-1], np.mean(u_hat - u), rtol=1e-13)
+    assert np.all(g[:offs[-1][0]] == 0.0)
+
+
+def test_first_layer_gradient_matches_its_own_definition():
+    """Layer 1's weight gradient is sum_p dz_1[p][o] b[p + offset]: rebuilt
+    here from the forward's activations and an independent backward through
+    the last layers with scipy's correlation, on a tiny network whose
+    middle layers are identities (one centre tap per channel)."""
+    rng = np.random.default_rng(34)
+    params = []
+    for i, (co, ci) in enumerate(cnn.layer_shapes()):
+        w = np.zeros((co, ci, 3, 3))
+        if 0 < i < cnn.LAYERS - 1:
+            for o in range(co):
+                w[o, o, 1, 1] = 1.0        # identity on each channel
+        else:
+            w[...] = rng.standard_normal(w.shape) * 0.3
+        params.append((w, np.zeros(co)))
+    theta = cnn.flatten(params)
+    b = np.abs(random_vector((1, 6, 8), 35)) + 0.1
+    u = random_vector((1, 6, 8), 36)
+    u_hat, acts = cnn.forward(theta, b)
+    _, g = cnn.backward(theta, b, u)
+    # middle layers pass a_1 through unchanged where it is positive, so
+    # d l / d a_1 = [a_1 > 0] conv_8^T(d l / d u_hat); then dz_1 = that masked again
+    dout = (u_hat - u)[0] / u_hat.size
+    w8 = params[-1][0][0]                              # (32, 3, 3)
+    a1 = acts[0][0]
+    dz1 = np.stack([scipy.signal.convolve2d(dout, w8[c], mode="same") for c in range(32)], axis=-1) * (a1 > 0)
+    bp = np.pad(b[0], 1)
+    want = np.zeros((32, 3, 3))
+    for dy in range(3):
+        for dx in range(3):
+            want[:, dy, dx] = np.einsum("ijo,ij->o", dz1, bp[dy:dy + 6, dx:dx + 8])
+    offs, _ = cnn.flat_offsets()
+    assert np.allclose(g[offs[0][0]:offs[0][1]].reshape(32, 3, 3), want, rtol=1e-10, atol=1e-14)
