@@ -253,3 +253,17 @@ def test_cnn_entry_validation(lib):
     assert lib.cnn_conv32(1, 4, 4, a, None, None, 1, None, a + 4096, None) == -1
     assert lib.cnn_conv32_wgrad(1, 4, 4, a, a, a, a, None, 0, None) == -7
     assert lib.cnn_pack(None, a, None) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libadjwt.so the binding raises: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = ("from paper_1707_02018_gb300 import _lib\n"
+            "_lib._lib = None\n"
+            "try:\n"
+            f"    _lib.load({str(tmp_path / 'libadjwt.so')!r})\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'no CPU fallback' in str(e))\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
