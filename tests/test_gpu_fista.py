@@ -185,3 +185,27 @@ def test_pinv_gradient_variant(adj, w, mode, bc):
         assert Fp > 1.1 * Fe
     else:
         assert abs(Fp - Fe) <= 1e-5 * Fe
+
+
+def test_nonfinite_observation_is_reported(adj):
+    """Fault injected on the host: a NaN in the observation b reaches the
+    float64 objective through the residual, and the call returns
+    ADJWT_ERR_NONFINITE instead of a number; the device status word stays
+    clear and the context keeps computing."""
+    rows = cols = 32
+    wt = adj.WtPlan(rows, cols, 2, "db2", "per")
+    taps = list(oblur.gaussian_psf(5, 1.0))
+    bl = adj.BlurPlan(rows, cols, taps, taps, "per")
+    b = wt.image(piecewise_smooth_image(rows, cols, 81))
+    b[5, 7] = float("nan")
+    f = adj.Fista(wt, bl, b, 1e-3, 1.0)
+    with pytest.raises(adj.AdjwtError) as e:
+        f.step(objective=True)
+    assert e.value.code == -6
+    with pytest.raises(adj.AdjwtError) as e:
+        f.objective(torch.zeros_like(f.x))
+    assert e.value.code == -6
+    b[5, 7] = 0.5
+    f.reset()
+    assert np.isfinite(f.step(objective=True))
+    assert adj.device_status() == 0
