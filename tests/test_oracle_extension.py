@@ -80,3 +80,43 @@ def test_one_third_weights_appear():
     assert 3 in ext.copy_counts(4, 3, "sym")
     assert 3 in ext.copy_counts(4, 3, "ppd")
     assert max(ext.copy_counts(7, 3, "sym")) == 2
+
+
+@pytest.mark.parametrize("N", list(range(1, 14)))
+@pytest.mark.parametrize("Lp", [1, 3, 8, 9, 16, 31])
+def test_ext_map_matches_numpy_pad(N, Lp):
+    """The index maps against numpy's own padding of arange(N): half-point
+    symmetric ('symmetric', which repeats the reflection when the pad is wider
+    than the signal), periodic ('wrap') and zero ('constant').  This pins the
+    repeated-reflection branch used for L' >= N (Sec. I-A, reading C1) to a
+    source that shares nothing with the oracle."""
+    idx = np.arange(N)
+    assert np.array_equal(ext.ext_map(N, Lp, "sym"), np.pad(idx, Lp, mode="symmetric"))
+    assert np.array_equal(ext.ext_map(N, Lp, "ppd"), np.pad(idx, Lp, mode="wrap"))
+    assert np.array_equal(ext.ext_map(N, Lp, "zero"), np.pad(idx, Lp, mode="constant", constant_values=-1))
+
+
+# Half-point symmetric extension by L' = 3 of [a], [a b], [a b c], written out by
+# hand: the signal mirrored about each end, the mirror image mirrored again.
+_SYM_TABLE_LP3 = {
+    1: "a a a | a | a a a",
+    2: "b b a | a b | b a a",
+    3: "c b a | a b c | c b a",
+}
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_ext_map_sym_hand_table(N):
+    want = [ord(ch) - ord("a") for ch in _SYM_TABLE_LP3[N].split() if ch != "|"]
+    assert ext.ext_map(N, 3, "sym").tolist() == want
+
+
+def test_ext_map_sym_whole_point_would_fail():
+    """A whole-point reflection (y[-1] = y[1]) or an off-by-one in the repeated
+    branch changes the map at N = 2, L' = 9 (so the pins above would catch it)."""
+    N, Lp = 2, 9
+    got = ext.ext_map(N, Lp, "sym")
+    whole = np.pad(np.arange(N), Lp, mode="reflect")
+    assert not np.array_equal(got, whole)
+    shifted = np.pad(np.arange(N), (Lp - 1, Lp + 1), mode="symmetric")
+    assert not np.array_equal(got, shifted)
