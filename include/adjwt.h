@@ -212,10 +212,13 @@ int conv_gradient(int batch, int64_t n, int k, const float* s, const float* h, c
  * batch * ceil(n / c) * k <= 2^20 with the chunk
  * c = 16 * floor((4097 - 16 * ceil(k / 16)) / 16) for k <= 1024 (c = 4032 at
  * k = 64, 3072 at k = 1024) and c = 1024 above, else
- * ADJWT_ERR_WORKSPACE and nothing runs.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
+ * ADJWT_ERR_WORKSPACE and nothing runs.  (For 49 <= k <= 64 the tensor-core
+ * kernel runs with 4096-sample chunks and so uses no more than this bound.)
+ * The first call in a context looks up the array's device address (with the
+ * device current) and caches it under the context's process-unique id: the
+ * address is tied to the context, and a new context (after cudaDeviceReset,
+ * or a non-primary context made current) gets its own lookup.  Make the first
+ * call in each context before any stream capture.  All calls share the array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.
  * Results equal conv_adjoint's; arguments, layouts and errors as there. */
 int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s, const float* h, const float* r,
@@ -270,6 +273,12 @@ size_t adjwt_fista_workspace_size(const adjwt_fista_problem* prob);
  * synchronises the stream; a non-finite value returns ADJWT_ERR_NONFINITE. */
 int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* ws, size_t ws_bytes,
                double* objective_out, adjwt_stream_t stream);
+
+/* FISTA's momentum as fista_step applies it (HOST, no device work):
+ * t_next = (1 + sqrt(1 + 4 t^2))/2 and beta = (t - 1)/t_next rounded to
+ * float32, the weight of y_{k+1} = x_k + beta (x_k - x_{k-1}).  t >= 1 and
+ * finite, pointers non-NULL (INVALID_ARG). */
+int adjwt_fista_momentum(double t, double* t_next, float* beta);
 
 /* The same iteration with the momentum t_k resident in the workspace (no
  * counterpart in the paper: it makes an iteration a pure sequence of stream

@@ -386,6 +386,14 @@ class Fista:
 
 
 # ------------------------------------------------------------ differentiation
+def fista_momentum(t):
+    """(beta_k, t_{k+1}) of FISTA's momentum as fista_step applies it; beta_k is
+    the float32 weight of y_{k+1} = x_k + beta_k (x_k - x_{k-1})."""
+    t1, beta = C.c_double(), C.c_float()
+    _lib.check(lib().adjwt_fista_momentum(float(t), C.byref(t1), C.byref(beta)))
+    return float(beta.value), float(t1.value)
+
+
 def gaussian_taps(k, sigma):
     """(taps, d taps / d sigma) of the normalised k-tap Gaussian (host lists)."""
     taps, dt = (C.c_double * k)(), (C.c_double * k)()

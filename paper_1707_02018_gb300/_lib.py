@@ -62,6 +62,7 @@ PROTOTYPES = {
     "adjwt_wt_plan_uses_tma": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "adjwt_wt_plan_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int), VP]),
     "adjwt_gaussian_taps": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "adjwt_fista_momentum": (C.c_int, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "adjwt_reduce_workspace_size": (SZ, []),
     "adjwt_axpby": (C.c_int, [I64, C.c_float, VP, C.c_float, VP, VP, VP]),
     "adjwt_dot": (C.c_int, [C.c_int, I64, I64, VP, VP, VP, VP, SZ, VP]),

@@ -1,8 +1,9 @@
 """Builds libadjwt.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
 Every translation unit under csrc/ is compiled in parallel into _build/ and
-linked as a shared library next to this file.  Used by __graft_entry__.build()
-and by the Python binding when the library is missing.
+linked as a shared library next to this file.  Run by __graft_entry__.build()
+(and by `python -m paper_1707_02018_gb300.build_ext`); the Python binding does
+not build: it raises when the library is missing.
 """
 import concurrent.futures as cf
 import os

@@ -244,6 +244,7 @@ int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* 
 // unless ADJWT_CONV_FP32 is set to a non-zero value in the environment.  Its
 // grad_h partials need at most as many slots as the register-blocked kernel's.
 bool conv_tc_supported(int k);
+void fista_momentum(double t, double* t_next, float* beta);
 int64_t conv_tc_nchunks(int64_t n);
 int launch_conv_tc(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
                    float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st);

@@ -217,8 +217,10 @@ extern "C" int conv_adjoint_noalloc(int batch, int64_t n, int k, const float* s,
   if (batch == 0 || (!grad_h && !grad_s)) return ADJWT_OK;
   if (grad_h && conv_partial_floats(batch, n, k) > conv_static_scratch_floats())
     return fail(ADJWT_ERR_WORKSPACE,
-                "conv_adjoint_noalloc: batch * ceil(n/1024) * k = " + std::to_string(conv_partial_floats(batch, n, k)) +
-                    " exceeds the fixed scratch of " + std::to_string(conv_static_scratch_floats()) +
+                "conv_adjoint_noalloc: grad_h needs batch * ceil(n / c) * k = " +
+                    std::to_string(conv_partial_floats(batch, n, k)) +
+                    " partial sums (c = the kernel's chunk: 16 * floor((4097 - 16 * ceil(k / 16)) / 16) for k <= 1024, "
+                    "1024 above), more than the fixed scratch of " + std::to_string(conv_static_scratch_floats()) +
                     " floats; use conv_adjoint with a workspace");
   int rc = check_ptr(r, "r");
   if (!rc && grad_h) rc = check_ptr(s, "s");
@@ -416,4 +418,11 @@ extern "C" int adjwt_fista_lipschitz(const adjwt_fista_problem* pr, float* v, in
   rc = check_ws(ws, ws_bytes, fista_workspace_bytes(pr), "fista_lipschitz");
   if (rc) return rc;
   return fista_lipschitz_impl(pr, v, iters, ws, lipschitz_out, stream);
+}
+
+extern "C" int adjwt_fista_momentum(double t, double* t_next, float* beta) {
+  if (!t_next || !beta) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_momentum: t_next and beta must be non-NULL");
+  if (!(t >= 1.0) || !std::isfinite(t)) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_momentum: need finite t >= 1");
+  fista_momentum(t, t_next, beta);
+  return ADJWT_OK;
 }

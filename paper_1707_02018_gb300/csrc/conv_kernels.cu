@@ -8,6 +8,8 @@
 // K-1 tail), s and h in shared memory, writes grad_s for its chunk and a
 // partial grad_h over its chunk to workspace; a second pass sums the partials
 // of each row in a fixed order (deterministic, no atomics).
+#include <cuda.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -189,22 +191,61 @@ __device__ __align__(256) float g_conv_static_scratch[kStaticScratchFloats];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-float* g_static_ptr[kMaxDevices] = {};
+struct StaticSlot {
+  unsigned long long ctx_id;  // unique for the life of the process (cuCtxGetId)
+  float* ptr;
+};
+StaticSlot g_static_slot[kMaxDevices] = {};
 
-// Device address of the array on the current device.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <class F>
+F driver_fn(const char* name, int version) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(p);
+}
+
+// Identifier of the context current on this thread (0 if none is current yet).
+int current_ctx_id(unsigned long long* id) {
+  static const CtxGetCurrentFn get_ctx = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 2000);
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+  if (!get_ctx || !get_id) return fail(ADJWT_ERR_CUDA, "conv_adjoint_noalloc: cuCtxGetCurrent/cuCtxGetId unavailable");
+  CUcontext ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS) return fail(ADJWT_ERR_CUDA, "conv_adjoint_noalloc: cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return fail(ADJWT_ERR_CUDA, "conv_adjoint_noalloc: cuCtxGetId failed");
+  return ADJWT_OK;
+}
+
+// Device address of the array in the current context.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, the first time a context uses
+// the entry point, and cached under that context's process-unique id: a new
+// context (after cudaDeviceReset, or a non-primary context made current) loads
+// the module again, possibly elsewhere, and gets its own lookup.
 int static_scratch(float** out) {
   int dev = 0;
   ADJWT_CUDA_CHECK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(ADJWT_ERR_INVALID_ARG, "conv_adjoint_noalloc: device index above 63");
+  unsigned long long id = 0;
+  int rc = current_ctx_id(&id);
+  if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  StaticSlot& slot = g_static_slot[dev];
+  if (id == 0 || slot.ctx_id != id || !slot.ptr) {
     void* p = nullptr;
-    ADJWT_CUDA_CHECK(cudaGetSymbolAddress(&p, g_conv_static_scratch));
-    g_static_ptr[dev] = static_cast<float*>(p);
+    ADJWT_CUDA_CHECK(cudaGetSymbolAddress(&p, g_conv_static_scratch));  // makes the primary context current if none was
+    rc = current_ctx_id(&id);
+    if (rc) return rc;
+    slot.ctx_id = id;
+    slot.ptr = static_cast<float*>(p);
   }
-  *out = g_static_ptr[dev];
+  *out = slot.ptr;
   return ADJWT_OK;
 }
 

@@ -146,6 +146,15 @@ int launch_sum_partials(const double* a, int na, double sa, const double* b, int
 
 size_t fista_workspace_bytes(const adjwt_fista_problem* pr) { return layout_ws(pr, nullptr).bytes; }
 
+// FISTA's momentum (the method cited in Sec. I-B): t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2
+// and the extrapolation weight beta_k = (t_k - 1)/t_{k+1}, rounded to float32
+// as the prox epilogue applies it.
+void fista_momentum(double t, double* t_next, float* beta) {
+  const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+  *t_next = t1;
+  *beta = static_cast<float>((t - 1.0) / t1);
+}
+
 int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, double* objective_out,
                     cudaStream_t s) {
   const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
@@ -153,14 +162,15 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
   if (rc) return rc;
   rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr);
   if (rc) return rc;
-  const double t = st->t;
-  const double t1 = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+  double t1 = 0.0;
+  float beta = 0.0f;
+  fista_momentum(st->t, &t1, &beta);
   ProxArgs prox{};
   prox.x = st->x;
   prox.y = st->y;
   prox.step = static_cast<float>(1.0 / pr->lipschitz);
   prox.thresh = static_cast<float>(pr->lambda / pr->lipschitz);
-  prox.beta = static_cast<float>((t - 1.0) / t1);
+  prox.beta = beta;
   prox.l1_partials = objective_out ? W.part_a : nullptr;
   int l1_slots = 0;
   rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0, W.ll1, s, &l1_slots);

@@ -26,8 +26,8 @@ import math
 
 import torch
 
-from . import (BlurPlan, Fista, WtPlan, axpby, blur, blur_adjoint, dot, fista_vjp_step, gaussian_taps, prox_vjp,
-               wt_synth, wt_synth_adjoint)
+from . import (BlurPlan, Fista, WtPlan, axpby, blur, blur_adjoint, dot, fista_momentum, fista_vjp_step,
+               gaussian_taps, prox_vjp, wt_synth, wt_synth_adjoint)
 
 
 class UnrolledFista:
@@ -52,12 +52,6 @@ class UnrolledFista:
 
     def _dR(self, u):
         return axpby(1.0, blur(self.dR[0], u), 1.0, blur(self.dR[1], u))
-
-    @staticmethod
-    def _beta(t):
-        """(beta_k as the library's prox epilogue uses it, t_{k+1})."""
-        t1 = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
-        return float(torch.tensor((t - 1.0) / t1, dtype=torch.float32)), t1
 
     def _run(self, start, stop, keep):
         """Iterations start .. stop-1 from the state already in self.fista;
@@ -108,7 +102,7 @@ class UnrolledFista:
         for k in range(n_steps):
             if k % every == 0:
                 ckpt[k] = (f.x.clone(), f.y.clone(), t)
-            beta, t1 = self._beta(t)
+            beta, t1 = fista_momentum(t)
             betas.append(beta)
             f.step()
             t = t1

@@ -140,7 +140,7 @@ def _main():
 
     from synthetic_inputs import gaussian_noise, he_normal_params, piecewise_smooth_image
 
-    from . import BlurPlan, blur
+    from . import BlurPlan, blur, gaussian_taps
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--batch", type=int, default=8)
@@ -149,8 +149,7 @@ def _main():
     ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()
     n, size = args.batch, args.size
-    g = [float(v) for v in torch.exp(-0.5 * (torch.arange(9, dtype=torch.float64) - 4) ** 2 / 1.5 ** 2)]
-    g = [v / sum(g) for v in g]
+    g, _ = gaussian_taps(9, 1.5)
     bl = BlurPlan(size, size, g, g, "sym")
     pitch = bl.image_pitch
     b = torch.zeros(n, size, pitch, dtype=torch.float32, device="cuda")

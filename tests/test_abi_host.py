@@ -137,6 +137,32 @@ def test_call_validation_before_launch(lib):
     lib.adjwt_wt_plan_destroy(h)
 
 
+def test_conv_adjoint_noalloc_validation(lib):
+    """The allocation-free channel gradient checks sizes, pointers and aliasing
+    on the host before it looks up its fixed array or launches anything."""
+    a, b, c = 0x10000000, 0x20000000, 0x30000000
+    f = lib.conv_adjoint_noalloc
+    assert f(-1, 5, 3, a, b, c, None, None, None) == -2                 # negative batch
+    assert f(4, 0, 3, a, b, c, None, None, None) == -2                  # empty rows
+    assert f(4, 5, 0, a, b, c, None, None, None) == -2                  # no taps
+    assert f(65536, 5, 3, a, b, c, None, None, None) == -2              # batch above 65535
+    assert f(0, 5, 3, None, None, None, None, None, None) == 0          # empty batch: nothing to do
+    assert f(2, 5, 3, None, None, None, None, None, None) == 0          # no output requested
+    # 1025 rows x 1 chunk (3072 samples) x 1024 lags = 1,049,600 partial sums > 2^20
+    assert f(1025, 3072, 1024, None, None, None, c, None, None) == -7
+    assert b"more than the fixed scratch" in lib.adjwt_last_error()
+    # 1024 rows fit exactly (2^20); the call then fails only on its NULL inputs
+    assert f(1024, 3072, 1024, None, None, None, c, None, None) == -1
+    # 17 chunks of 4032 samples at k = 64: 1000 x 17 x 64 = 1,088,000 > 2^20
+    assert f(1000, 65536, 64, a, b, c, 0x40000000, None, None) == -7
+    # without grad_h no scratch is used, so the same sizes pass the size check
+    assert f(1000, 65536, 64, a, b, c, None, 0x40000000 + 4, None) == -3   # misaligned grad_s
+    assert f(2, 5, 3, a, b, c, a, None, None) == -4                     # grad_h over s
+    assert f(2, 5, 3, a, b, c, c + 16, None, None) == -4                # grad_h over r
+    assert f(2, 5, 3, a, b, c, None, c, None) == -4                     # grad_s over r
+    assert f(2, 5, 3, a, b, c, None, b, None) == -4                     # grad_s over h
+
+
 def test_workspace_sizes(lib):
     # one partial grad_h per (row, chunk) with chunks of 32*floor((4097-k)/32) = 4032 samples at k = 64
     assert lib.adjwt_conv_adjoint_workspace_size(256, 65536, 64) >= 256 * 17 * 64 * 4
@@ -267,3 +293,20 @@ def test_missing_library_fails_loudly(tmp_path):
             "    print('raised', 'no CPU fallback' in str(e))\n")
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
+def test_fista_momentum_matches_oracle(lib):
+    """The momentum fista_step applies (host routine, no device work) follows
+    the oracle's t-update; beta is its float32 rounding."""
+    from oracle import fista as ofista
+    t = 1.0
+    for _ in range(50):
+        t1, beta = C.c_double(), C.c_float()
+        assert lib.adjwt_fista_momentum(t, C.byref(t1), C.byref(beta)) == 0
+        want_t1 = ofista.t_next(t)
+        assert abs(t1.value - want_t1) <= 1e-15 * want_t1
+        assert beta.value == np.float32((t - 1.0) / want_t1)
+        t = t1.value
+    assert lib.adjwt_fista_momentum(0.5, C.byref(C.c_double()), C.byref(C.c_float())) == -1
+    assert lib.adjwt_fista_momentum(float("nan"), C.byref(C.c_double()), C.byref(C.c_float())) == -1
+    assert lib.adjwt_fista_momentum(1.0, None, C.byref(C.c_float())) == -1
