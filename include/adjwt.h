@@ -152,6 +152,22 @@ int adjwt_wt_plan_set_tma(adjwt_wt_plan* plan, int op, int level, int enabled);
 int adjwt_wt_plan_uses_tma(const adjwt_wt_plan* plan, int op, int level, int* uses);
 int adjwt_wt_plan_autotune(adjwt_wt_plan* plan, int reps, int* from_cache, adjwt_stream_t stream);
 
+/* Level chain (no counterpart in the paper: a launch schedule).  The deepest
+ * run of at least two levels that the TMA kernel does not share (for W also
+ * none on the per-pixel gather path, and never under PPD) runs as ONE launch
+ * instead of one launch per level: its tiles are items handed out level by
+ * level in the order of the recursion (Eq. 2 / Eq. 4: W^* from level 1 down,
+ * W from level J up), and a tile starts once every tile of the level it reads
+ * is done.  Its counters live in the workspace and are zeroed on the stream
+ * before each launch; waits are bounded (ADJWT_ERR_TIMEOUT in the device
+ * status word).  Results are identical to the per-level launches.
+ * adjwt_wt_plan_set_level_chain(plan, 0) switches it off (1: on, the
+ * default); adjwt_wt_plan_chain_start gives the chain's first level for op 0
+ * (W), 1 (W^*) or 2 (W^* with the prox), 0 when that transform has none.
+ * Errors: INVALID_ARG (NULL, op outside 0..2). */
+int adjwt_wt_plan_set_level_chain(adjwt_wt_plan* plan, int enabled);
+int adjwt_wt_plan_chain_start(const adjwt_wt_plan* plan, int op, int* first_level);
+
 /* ---------------------------------------------------------------------- blur
  * Separable PSF p = outer(taps_r, taps_c) (float64 taps, odd lengths
  * kr, kc <= 65) applied as R u = C_valid(E_r u) under bc in {ZERO, SYM, PER}

@@ -102,6 +102,20 @@ class WtPlan:
             out[name] = row
         return out
 
+    def set_level_chain(self, enabled):
+        """Run the deepest tiled-only levels as one launch (True, the default)
+        or one launch per level (False)."""
+        _lib.check(lib().adjwt_wt_plan_set_level_chain(self._h, int(bool(enabled))))
+
+    def chain_start(self):
+        """{"synth", "analysis", "prox": first level of the level chain, 0 = none}."""
+        out = {}
+        for name, op in self.LEVEL_OPS.items():
+            v = C.c_int()
+            _lib.check(lib().adjwt_wt_plan_chain_start(self._h, op, C.byref(v)))
+            out[name] = int(v.value)
+        return out
+
     def autotune(self, reps=5, stream=None):
         """Measure the TMA / tiled choice per level (see include/adjwt.h); True
         if the choices came from an earlier tuning of the same size class."""

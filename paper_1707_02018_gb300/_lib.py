@@ -60,6 +60,8 @@ PROTOTYPES = {
     "adjwt_fista_device_reset": (C.c_int, [C.POINTER(FistaProblem), VP, SZ, VP]),
     "adjwt_wt_plan_set_tma": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
     "adjwt_wt_plan_uses_tma": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "adjwt_wt_plan_set_level_chain": (C.c_int, [VP, C.c_int]),
+    "adjwt_wt_plan_chain_start": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int)]),
     "adjwt_wt_plan_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int), VP]),
     "adjwt_gaussian_taps": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "adjwt_fista_momentum": (C.c_int, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_float)]),

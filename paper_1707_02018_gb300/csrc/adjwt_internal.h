@@ -18,6 +18,7 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxTaps = 10;     // longest filter array (CDF 9/7 in a length-10 array)
 constexpr int kMaxBlurRadius = 32;
 constexpr int kSynthTile = 32;   // output tile side of the tiled reconstruction kernel
+constexpr int kChainCounterFloats = 64;  // level-chain counters at the tail of the second LL buffer
 
 enum Mode : int { kZero = 0, kSym = 1, kPpd = 2, kPer = 3 };
 
@@ -141,6 +142,9 @@ struct adjwt_wt_plan {
   // TMA kernel takes the tiles the size rule gives it (set by
   // adjwt_wt_plan_set_tma / adjwt_wt_plan_autotune)
   unsigned char tma_off[3][adjwt::kMaxLevels] = {};
+  // the deepest run of tiled-only levels runs as one level-chain launch
+  // unless switched off (adjwt_wt_plan_set_level_chain)
+  bool chain_off = false;
 };
 
 struct adjwt_blur_plan {
@@ -169,6 +173,11 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
 int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs, bool adjoint,
                        const ProxArgs& prox, float* llbuf0, float* llbuf1, cudaStream_t s, int* l1_slots_used);
 int wt_l1_partial_slots(const adjwt_wt_plan* p);
+// First level of the level chain (levels j0..J in one launch) of the
+// analysis direction (W^*, W^dagger; prox: W^* with the FISTA prox) and of
+// the reconstruction W; levels + 1 when the transform has none.
+int ana_chain_start(const adjwt_wt_plan* p, bool adjoint, bool prox);
+int syn_chain_start(const adjwt_wt_plan* p);
 // Interior rectangle of level j's output reconstructed by the persistent TMA
 // kernel (empty for small levels), and its launcher.
 void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1);
@@ -205,6 +214,9 @@ bool tiled_blur_supported(const adjwt_blur_plan* p);
 int tiled_blur_grid_slots(const adjwt_blur_plan* p);
 int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b, float* out, double* partials,
                       cudaStream_t s);
+
+// FISTA momentum: t_{k+1} and the float32 extrapolation weight beta_k.
+void fista_momentum(double t, double* t_next, float* beta);
 
 // Deterministic sum of float64 partials: out[0] = scale0 * sum(a[0..na)) + scale1 * sum(b[0..nb)).
 int launch_sum_partials(const double* a, int na, double scale_a, const double* b, int nb, double scale_b,
@@ -244,7 +256,6 @@ int launch_conv_fused(int batch, int64_t n, int k, const float* s, const float* 
 // unless ADJWT_CONV_FP32 is set to a non-zero value in the environment.  Its
 // grad_h partials need at most as many slots as the register-blocked kernel's.
 bool conv_tc_supported(int k);
-void fista_momentum(double t, double* t_next, float* beta);
 int64_t conv_tc_nchunks(int64_t n);
 int launch_conv_tc(int batch, int64_t n, int k, const float* s, const float* h, const float* x, const float* r_in,
                    float* r_out, float* grad_h, float* grad_s, float* partials, cudaStream_t st);

@@ -9,6 +9,7 @@
 // partial grad_h over its chunk to workspace; a second pass sums the partials
 // of each row in a fixed order (deterministic, no atomics).
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <mutex>
@@ -197,8 +198,6 @@ struct StaticSlot {
 };
 StaticSlot g_static_slot[kMaxDevices] = {};
 
-using CtxGetCurrentFn = CUresult (*)(CUcontext*);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
 template <class F>
 F driver_fn(const char* name, int version) {
@@ -212,8 +211,8 @@ F driver_fn(const char* name, int version) {
 
 // Identifier of the context current on this thread (0 if none is current yet).
 int current_ctx_id(unsigned long long* id) {
-  static const CtxGetCurrentFn get_ctx = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 2000);
-  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+  static const auto get_ctx = driver_fn<PFN_cuCtxGetCurrent_v4000>("cuCtxGetCurrent", 4000);
+  static const auto get_id = driver_fn<PFN_cuCtxGetId_v12000>("cuCtxGetId", 12000);
   if (!get_ctx || !get_id) return fail(ADJWT_ERR_CUDA, "conv_adjoint_noalloc: cuCtxGetCurrent/cuCtxGetId unavailable");
   CUcontext ctx = nullptr;
   if (get_ctx(&ctx) != CUDA_SUCCESS) return fail(ADJWT_ERR_CUDA, "conv_adjoint_noalloc: cuCtxGetCurrent failed");

@@ -117,6 +117,9 @@ extern "C" int adjwt_wt_plan_create(adjwt_wt_plan** out, int rows, int cols, int
     int64_t sz = static_cast<int64_t>(L.ax[0].n) * L.band_pitch;
     p->ll_buf_floats[j % 2] = std::max(p->ll_buf_floats[j % 2], sz);
   }
+  // transforms of two or more levels may run a level chain, whose counters
+  // sit past the LL data of the second buffer
+  if (levels >= 2) p->ll_buf_floats[1] = round_up(p->ll_buf_floats[1], 64) + kChainCounterFloats;
 
   // 1/c tables for the weighted extension (E^dagger)^* and the fold E^dagger
   std::vector<float> host;

@@ -100,6 +100,20 @@ extern "C" int adjwt_wt_plan_uses_tma(const adjwt_wt_plan* p, int op, int level,
   return ADJWT_OK;
 }
 
+extern "C" int adjwt_wt_plan_set_level_chain(adjwt_wt_plan* p, int enabled) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_set_level_chain: plan is NULL");
+  p->chain_off = !enabled;
+  return ADJWT_OK;
+}
+
+extern "C" int adjwt_wt_plan_chain_start(const adjwt_wt_plan* p, int op, int* first_level) {
+  if (!p || !first_level) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_chain_start: NULL argument");
+  if (op < 0 || op >= kOps) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_chain_start: op must be 0, 1 or 2");
+  const int j0 = op == 0 ? syn_chain_start(p) : ana_chain_start(p, true, op == 2);
+  *first_level = j0 <= p->levels ? j0 : 0;
+  return ADJWT_OK;
+}
+
 extern "C" int adjwt_wt_plan_autotune(adjwt_wt_plan* p, int reps, int* from_cache, adjwt_stream_t stream) {
   if (!p) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_autotune: plan is NULL");
   if (reps < 1 || reps > 1000) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_autotune: reps must be in 1..1000");

@@ -113,9 +113,23 @@ constexpr int kProxSlot = 36;
 constexpr int kProxRowers = 2 * (kTile / kAP) * 32;
 constexpr size_t kProxSlotBytes = (size_t)kProxRowers * kProxSlot * sizeof(float);
 
-template <int L>
-__global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
-  pdl_entry();
+// Loads of a level's input.  Inputs written before the launch take the
+// read-only path; the level chain (below) reads LL bands that other CTAs of
+// the same launch wrote, so it loads them at L2 (ld.global.cg), never from a
+// possibly stale L1 or read-only cache line.
+template <bool CG>
+__device__ __forceinline__ float ld_level(const float* p) {
+  if constexpr (CG) {
+    return __ldcg(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
+// One kTile x kTile coefficient tile (tile_y, tile_x) of the four bands of
+// one level; adds this thread's |x_k| to l1 when the prox runs.
+template <int L, bool CG>
+__device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int tile_x, float& l1) {
   constexpr int Lp = L - 1;
   constexpr int E = 2 * kTile + L - 2;  // extended samples feeding one tile
   constexpr int EP = E | 1;
@@ -124,10 +138,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
   __shared__ float V[2][kTile][EP];
   __shared__ int s_src[2][E];
   __shared__ float s_w[2][E];
-  __shared__ double red[kAnaThreads / 32];
 
-  int tile_y, tile_x;
-  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
   const int k0 = tile_y * kTile, l0 = tile_x * kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ float prox_slots[];  // kProxSlotBytes when the launch has prox bands, else none
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
         E * E,
         [&](int i) {
           const int er = i / E;
-          return __ldg(src + (size_t)er * a.in_pitch + (i - er * E));
+          return ld_level<CG>(src + (size_t)er * a.in_pitch + (i - er * E));
         },
         [&](int i, float v) {
           const int er = i / E;
@@ -211,7 +222,8 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
         [&](int i) {
           const int er = i / E, ec = i - er * E;
           const int sr = s_src[0][er], sc = s_src[1][ec];
-          return (sr >= 0 && sc >= 0) ? s_w[0][er] * s_w[1][ec] * __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+          return (sr >= 0 && sc >= 0) ? s_w[0][er] * s_w[1][ec] * ld_level<CG>(a.in + (size_t)sr * a.in_pitch + sc)
+                                      : 0.0f;
         },
         [&](int i, float v) {
           const int er = i / E;
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
   __syncthreads();
 
   // row pass + store / prox epilogue: thread = (row kk, vertical filter f, block lb)
-  float l1 = 0.0f;  // per-thread float32 partial of |x_k|, float64 across the block
+  // (l1: per-thread float32 partial of |x_k|, float64 across the block)
   const float beta = a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
   if (rower) {  // the ninth warp has no row-pass item
     float w[NW];
@@ -321,9 +333,19 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
       }
     }
   }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kAnaThreads, 2) k_analysis(const AnaArgs a) {
+  pdl_entry();
+  __shared__ double red[kAnaThreads / 32];
+  int tile_y, tile_x;
+  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
+  float l1 = 0.0f;
+  analysis_tile<L, false>(a, tile_y, tile_x, l1);
   if (a.l1) {
     const double tot = block_sum<kAnaThreads>((double)l1, red);
-    if (tid == 0) a.l1[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.l1[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 }
 
@@ -384,9 +406,9 @@ __device__ __forceinline__ void pair_block(const float (&c0)[SynGeo<L>::NC], con
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
-  pdl_entry();
+// One kTile x kTile output tile (tile_y, tile_x) of one level.
+template <int L, bool CG>
+__device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int tile_x) {
   using G = SynGeo<L>;
   constexpr int Lp = L - 1;
   __shared__ float C[4][G::KM][G::KP];
@@ -396,8 +418,6 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   static_assert(kTile * G::YP <= 2 * G::XM * G::KP, "Y must fit in H");
 
   const int tid = threadIdx.x;
-  int tile_y, tile_x;
-  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
   const int t0r = tile_y * kTile, t0c = tile_x * kTile;
   const bool sym = a.mode == 1;
   float g0[L], g1[L];
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
         const int kk = half + 2 * r;
-        v[r] = (kk < nk[0] && lane < nk[1]) ? __ldg(src + (size_t)(2 * r) * a.band_pitch) : 0.0f;
+        v[r] = (kk < nk[0] && lane < nk[1]) ? ld_level<CG>(src + (size_t)(2 * r) * a.band_pitch) : 0.0f;
       }
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
@@ -527,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
         } else if (k < 0 || k >= a.nr || l < 0 || l >= a.nc) {
           return 0.0f;
         }
-        return __ldg(a.band[b] + (size_t)k * a.band_pitch + l);
+        return ld_level<CG>(a.band[b] + (size_t)k * a.band_pitch + l);
       },
       [&](int i, float v) {
         const int b = i / KK, rem = i - b * KK;
@@ -641,6 +661,14 @@ __global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
   }
 }
 
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_synthesis(const SynArgs a) {
+  pdl_entry();
+  int tile_y, tile_x;
+  border_tile(a.in_r0, a.in_r1, a.in_c0, a.in_c1, a.tiles_r, a.tiles_c, &tile_y, &tile_x);
+  synthesis_tile<L, false>(a, tile_y, tile_x);
+}
+
 // Per-pixel gather of W = E^dagger S for pixels with copies anywhere in the
 // extended domain (periodic-extension borders, tiny images).
 template <int L>
@@ -713,6 +741,148 @@ __global__ void __launch_bounds__(kThreads) k_synthesis_gather(const SynArgs a, 
   a.out[(size_t)tr * a.out_pitch + tc] = acc;
 }
 
+// ---------------------------------------------------------------- level chain
+// The deep levels of a transform move little data (LL_1 of a 2048^2 image is
+// 4.3 MB and everything below it fits in L2), so one launch per level leaves
+// them bound by launch latency and a dependent global round trip per level.
+// The level chain runs a run of consecutive levels in one launch.  An item is
+// one tile of one level; items are numbered level by level in the order the
+// recursion needs them (W^*: j ascending, W: j descending).  A CTA takes the
+// next item number from a counter, waits until every tile of the item's
+// preceding level is done, runs the tile and counts it done.  A CTA only ever
+// waits on items handed out before its own, to CTAs that are running, so the
+// launch needs no co-residency and cannot deadlock with kernels of other
+// streams.  Waits are bounded (kWaitCycles): a CTA that gives up records
+// ADJWT_ERR_TIMEOUT in the device status word and stops taking items.
+//
+// Counters (ints, zeroed on the stream before each launch): [0] next item,
+// [kChainDone + i] tiles of chain level i done.
+constexpr int kChainDone = 4;
+
+struct AnaChainArgs {
+  AnaArgs lv[kMaxLevels];       // chain levels, shallowest first
+  int first_item[kMaxLevels + 1];
+  int nlev;
+  int* counters;
+  int* status;
+  double* l1;                   // one float64 partial per CTA (null = none)
+};
+
+struct SynChainArgs {
+  SynArgs lv[kMaxLevels];       // chain levels, deepest first
+  int first_item[kMaxLevels + 1];
+  int nlev;
+  int* counters;
+  int* status;
+};
+
+// Bounded wait (one thread) until *ctr >= target, with acquire semantics.
+__device__ __forceinline__ bool chain_wait(const int* ctr, int target) {
+  const long long t0 = clock64();
+  for (;;) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+    __nanosleep(100);
+  }
+}
+
+// Thread 0 takes the next item and waits for its level's inputs; every thread
+// returns (item, level) or item = -1 when the chain is finished or a wait gave
+// up.  The caller's next __syncthreads() must come after its last read of the
+// shared words.
+__device__ __forceinline__ void chain_next(const int* first_item, int nlev, int* counters, int* status, int* s_word,
+                                           int* item_out, int* lev_out) {
+  if (threadIdx.x == 0) {
+    int item = atomicAdd(&counters[0], 1);
+    int lev = 0;
+    while (lev + 1 < nlev && item >= first_item[lev + 1]) ++lev;
+    if (item >= first_item[nlev]) {
+      item = -1;
+    } else if (lev > 0 && !chain_wait(&counters[kChainDone + lev - 1], first_item[lev] - first_item[lev - 1])) {
+      record_status(status, ADJWT_ERR_TIMEOUT);
+      item = -1;
+    }
+    __threadfence();
+    s_word[0] = item;
+    s_word[1] = lev;
+  }
+  __syncthreads();
+  *item_out = s_word[0];
+  *lev_out = s_word[1];
+}
+
+// Every write of the finished tile happens before the count is published
+// (block barrier, then a device-scope fence by the counting thread).
+__device__ __forceinline__ void chain_done(int* counters, int lev) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&counters[kChainDone + lev], 1);
+  }
+}
+
+// Copy one level's argument block from the launch parameters into shared
+// memory (the level index is only known at run time).
+template <typename T, int NT>
+__device__ __forceinline__ void copy_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += NT) d[i] = s[i];
+}
+
+template <int L>
+__global__ void __launch_bounds__(kAnaThreads, 2) k_analysis_chain(const __grid_constant__ AnaChainArgs c) {
+  pdl_entry();
+  __shared__ AnaArgs s_a;
+  __shared__ int s_word[2];
+  __shared__ double red[kAnaThreads / 32];
+  float l1 = 0.0f;
+  int cur = -1;
+  for (;;) {
+    int item, lev;
+    chain_next(c.first_item, c.nlev, c.counters, c.status, s_word, &item, &lev);
+    if (item < 0) break;
+    if (lev != cur) {
+      copy_args<AnaArgs, kAnaThreads>(&s_a, &c.lv[lev]);
+      __syncthreads();
+      cur = lev;
+    }
+    const int local = item - c.first_item[lev];
+    const int ty = local / s_a.tiles_c;
+    analysis_tile<L, true>(s_a, ty, local - ty * s_a.tiles_c, l1);
+    chain_done(c.counters, lev);
+  }
+  if (c.l1) {
+    const double tot = block_sum<kAnaThreads>((double)l1, red);
+    if (threadIdx.x == 0) c.l1[blockIdx.x] = tot;
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_synthesis_chain(const __grid_constant__ SynChainArgs c) {
+  pdl_entry();
+  __shared__ SynArgs s_a;
+  __shared__ int s_word[2];
+  int cur = -1;
+  for (;;) {
+    int item, lev;
+    chain_next(c.first_item, c.nlev, c.counters, c.status, s_word, &item, &lev);
+    if (item < 0) break;
+    if (lev != cur) {
+      copy_args<SynArgs, kThreads>(&s_a, &c.lv[lev]);
+      __syncthreads();
+      cur = lev;
+    }
+    const int local = item - c.first_item[lev];
+    const int ty = local / s_a.tiles_c;
+    synthesis_tile<L, true>(s_a, ty, local - ty * s_a.tiles_c);
+    chain_done(c.counters, lev);
+  }
+}
+
 template <typename Fn>
 int dispatch_L(int L, Fn&& fn) {
   switch (L) {
@@ -729,7 +899,73 @@ int analysis_grid(const Level& L, dim3* g) {
   return static_cast<int>(g->x * g->y);
 }
 
+// Arguments of the tiled reconstruction of level j (LL_j from the ping-pong
+// buffer below level J, LL_{j-1} into the other buffer or the image).
+SynArgs synth_args(const adjwt_wt_plan* p, int j, const float* coeffs, float* image, float* const llbuf[2]) {
+  const Level& L = p->lv[j - 1];
+  const FilterBank& fb = p->fb;
+  SynArgs a{};
+  for (int b = 0; b < 4; ++b) a.band[b] = (b == 0 && j < p->levels) ? llbuf[j % 2] : coeffs + L.off_band[b];
+  a.band_pitch = L.band_pitch;
+  a.out = (j == 1) ? image : llbuf[(j - 1) % 2];
+  a.out_pitch = L.in_pitch;
+  a.Nr = L.ax[0].N;
+  a.Nc = L.ax[1].N;
+  a.nr = L.ax[0].n;
+  a.nc = L.ax[1].n;
+  a.mode = p->bc;
+  a.winv_r = L.ax[0].winv;
+  a.winv_c = L.ax[1].winv;
+  for (int t = 0; t < fb.L; ++t) {
+    a.g[0][t] = static_cast<float>(fb.rec_lo[t]);
+    a.g[1][t] = static_cast<float>(fb.rec_hi[t]);
+  }
+  return a;
+}
+
+template <typename K>
+int resident_per_sm(K kernel, int threads, size_t dyn) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, dyn) != cudaSuccess) nb = 1;
+  return std::max(1, nb);
+}
+
+// Counters of the level chain: the tail of the second LL buffer (reserved by
+// the plan for transforms of two or more levels).
+constexpr size_t kChainCounterBytes = (kChainDone + kMaxLevels) * sizeof(int);
+int* chain_counters(const adjwt_wt_plan* p, float* llbuf1) {
+  return reinterpret_cast<int*>(llbuf1 + p->ll_buf_floats[1] - kChainCounterFloats);
+}
+
 }  // namespace
+
+// First level of the analysis-direction chain: the deepest run of levels
+// (at least two) that no TMA kernel shares; levels + 1 when there is none.
+int ana_chain_start(const adjwt_wt_plan* p, bool adjoint, bool prox) {
+  if (p->chain_off) return p->levels + 1;
+  int j0 = p->levels + 1;
+  for (int j = p->levels; j >= 1; --j) {
+    int r0, r1, c0, c1;
+    ana_tma_rect(p, j, adjoint, prox, &r0, &r1, &c0, &c1);
+    if (r1 > r0) break;
+    j0 = j;
+  }
+  return p->levels - j0 + 1 >= 2 ? j0 : p->levels + 1;
+}
+
+// The same for the reconstruction: levels without a TMA rectangle, the
+// per-pixel gather path or the redundant-periodic border pass.
+int syn_chain_start(const adjwt_wt_plan* p) {
+  if (p->chain_off || p->bc == kPpd) return p->levels + 1;
+  int j0 = p->levels + 1;
+  for (int j = p->levels; j >= 1; --j) {
+    int r0, r1, c0, c1;
+    synth_tma_rect(p, j, &r0, &r1, &c0, &c1);
+    if (r1 > r0 || p->lv[j - 1].generic_synth) break;
+    j0 = j;
+  }
+  return p->levels - j0 + 1 >= 2 ? j0 : p->levels + 1;
+}
 
 // Per level: the tiled kernel's CTAs plus the TMA kernel's (at most one per
 // 16 x 64 coefficient tile, which is no more than the 32 x 32 tile count).
@@ -747,6 +983,8 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
   float* llbuf[2] = {llbuf0, llbuf1};
   const FilterBank& fb = p->fb;
   int slot = 0;
+  const int j0 = ana_chain_start(p, adjoint, prox.x != nullptr);
+  AnaChainArgs chain{};
   for (int j = 1; j <= p->levels; ++j) {
     const Level& L = p->lv[j - 1];
     AnaArgs a{};
@@ -792,6 +1030,14 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     int ncta = analysis_grid(L, &grid);
     a.tiles_c = grid.x;
     a.tiles_r = grid.y;
+    if (j >= j0) {  // a level of the chain: its tiles become items of one launch
+      const int i = j - j0;
+      chain.lv[i] = a;
+      // the tile code only tests l1 for null; the chain writes one partial per CTA
+      chain.lv[i].l1 = (prox.x && prox.l1_partials) ? prox.l1_partials : nullptr;
+      chain.first_item[i + 1] = chain.first_item[i] + ncta;
+      continue;
+    }
     int r0, r1, c0, c1;  // coefficient rectangle of the TMA kernel
     ana_tma_rect(p, j, adjoint, prox.x != nullptr, &r0, &r1, &c0, &c1);
     if (r1 > r0) {
@@ -827,6 +1073,26 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       slot += used;
     }
   }
+  if (j0 <= p->levels) {
+    chain.nlev = p->levels - j0 + 1;
+    chain.counters = chain_counters(p, llbuf1);
+    chain.status = device_status_ptr();
+    ADJWT_CUDA_CHECK(cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
+    const char* name = !adjoint ? "wt_analysis_chain" : (prox.x ? "wt_adjoint_prox_chain" : "wt_adjoint_chain");
+    int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
+      auto kern = k_analysis_chain<decltype(Lc)::value>;
+      const size_t dyn = prox.x ? kProxSlotBytes : 0;
+      if (dyn) ADJWT_CUDA_CHECK(set_smem(kern, dyn));
+      static const int per_sm = resident_per_sm(kern, kAnaThreads, kProxSlotBytes);
+      const int ncta = std::max(1, std::min(chain.first_item[chain.nlev], per_sm * sm_count()));
+      chain.l1 = (prox.x && prox.l1_partials) ? prox.l1_partials + slot : nullptr;
+      slot += ncta;
+      ADJWT_TRACED(name, j0, s, pdl_launch(kern, dim3(ncta), kAnaThreads, dyn, s, chain));
+      return ADJWT_OK;
+    });
+    if (rc) return rc;
+    ADJWT_CUDA_CHECK(cudaGetLastError());
+  }
   if (l1_slots_used) *l1_slots_used = slot;
   return ADJWT_OK;
 }
@@ -836,25 +1102,34 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
   float* llbuf[2] = {llbuf0, llbuf1};
   const FilterBank& fb = p->fb;
   const int Lp = fb.L - 1;
-  for (int j = p->levels; j >= 1; --j) {
-    const Level& L = p->lv[j - 1];
-    SynArgs a{};
-    for (int b = 0; b < 4; ++b)
-      a.band[b] = (b == 0 && j < p->levels) ? llbuf[j % 2] : coeffs + L.off_band[b];
-    a.band_pitch = L.band_pitch;
-    a.out = (j == 1) ? image : llbuf[(j - 1) % 2];
-    a.out_pitch = L.in_pitch;
-    a.Nr = L.ax[0].N;
-    a.Nc = L.ax[1].N;
-    a.nr = L.ax[0].n;
-    a.nc = L.ax[1].n;
-    a.mode = p->bc;
-    a.winv_r = L.ax[0].winv;
-    a.winv_c = L.ax[1].winv;
-    for (int t = 0; t < fb.L; ++t) {
-      a.g[0][t] = static_cast<float>(fb.rec_lo[t]);
-      a.g[1][t] = static_cast<float>(fb.rec_hi[t]);
+  const int j0 = syn_chain_start(p);
+  if (j0 <= p->levels) {  // levels J .. j0 in one launch
+    SynChainArgs chain{};
+    chain.nlev = p->levels - j0 + 1;
+    for (int j = p->levels; j >= j0; --j) {
+      const int i = p->levels - j;
+      chain.lv[i] = synth_args(p, j, coeffs, image, llbuf);
+      SynArgs& a = chain.lv[i];
+      a.tiles_c = (a.Nc + kTile - 1) / kTile;
+      a.tiles_r = (a.Nr + kTile - 1) / kTile;
+      chain.first_item[i + 1] = chain.first_item[i] + a.tiles_c * a.tiles_r;
     }
+    chain.counters = chain_counters(p, llbuf1);
+    chain.status = device_status_ptr();
+    ADJWT_CUDA_CHECK(cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
+    int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
+      auto kern = k_synthesis_chain<decltype(Lc)::value>;
+      static const int per_sm = resident_per_sm(kern, kThreads, 0);
+      const int ncta = std::max(1, std::min(chain.first_item[chain.nlev], per_sm * sm_count()));
+      ADJWT_TRACED("wt_synth_chain", j0, s, pdl_launch(kern, dim3(ncta), kThreads, 0, s, chain));
+      return ADJWT_OK;
+    });
+    if (rc) return rc;
+    ADJWT_CUDA_CHECK(cudaGetLastError());
+  }
+  for (int j = std::min(p->levels, j0 - 1); j >= 1; --j) {
+    const Level& L = p->lv[j - 1];
+    SynArgs a = synth_args(p, j, coeffs, image, llbuf);
     int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
       constexpr int LL = decltype(Lc)::value;
       if (L.generic_synth) {

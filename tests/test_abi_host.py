@@ -310,3 +310,33 @@ def test_fista_momentum_matches_oracle(lib):
     assert lib.adjwt_fista_momentum(0.5, C.byref(C.c_double()), C.byref(C.c_float())) == -1
     assert lib.adjwt_fista_momentum(float("nan"), C.byref(C.c_double()), C.byref(C.c_float())) == -1
     assert lib.adjwt_fista_momentum(1.0, None, C.byref(C.c_float())) == -1
+
+
+def test_level_chain_range(lib):
+    """Which levels run as one level-chain launch (plans without 1/c tables,
+    so nothing touches a device): 2048^2 CDF 9/7 J=5 chains 2..5 under ZERO
+    (level 1 is the TMA kernels'), and under PER W chains 4..5 (levels 1-3 are
+    whole TMA levels) while W^* chains 2..5;
+    a small ZERO image chains every level; one level has no chain; switching the
+    chain off reports none."""
+    def starts(h):
+        out = []
+        for op in range(3):
+            v = C.c_int(-1)
+            assert lib.adjwt_wt_plan_chain_start(h, op, C.byref(v)) == 0
+            out.append(v.value)
+        return out
+    for (rows, J, bc, want) in [(2048, 5, 0, [2, 2, 2]), (2048, 5, 3, [4, 2, 2]), (256, 3, 0, [1, 1, 1]),
+                                (256, 1, 0, [0, 0, 0])]:
+        rc, h = _plan(lib, rows, rows, J, WAV["cdf97"], bc)
+        assert rc == 0, lib.adjwt_last_error()
+        assert starts(h) == want, (rows, J, bc)
+        assert lib.adjwt_wt_plan_set_level_chain(h, 0) == 0
+        assert starts(h) == [0, 0, 0]
+        assert lib.adjwt_wt_plan_set_level_chain(h, 1) == 0
+        assert starts(h) == want
+        lib.adjwt_wt_plan_destroy(h)
+    assert lib.adjwt_wt_plan_chain_start(None, 0, C.byref(C.c_int())) == -1
+    rc, h = _plan(lib, 64, 64, 2, WAV["db2"], 0)
+    assert lib.adjwt_wt_plan_chain_start(h, 3, C.byref(C.c_int())) == -1
+    lib.adjwt_wt_plan_destroy(h)

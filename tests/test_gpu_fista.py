@@ -209,3 +209,22 @@ def test_nonfinite_observation_is_reported(adj):
     f.reset()
     assert np.isfinite(f.step(objective=True))
     assert adj.device_status() == 0
+
+
+@pytest.mark.parametrize("rows,J,w,mode", [(256, 3, "db2", "sym"), (2048, 5, "cdf97", "sym"), (2048, 5, "cdf97", "per")])
+def test_level_chain_fista_steps(adj, rows, J, w, mode):
+    """FISTA with the prox epilogue in the level chain and without it: the
+    iterates are bit-identical; the objective (whose |x| partials are summed
+    over a different CTA split) agrees to float64 rounding."""
+    prob, wt, bl, db = _setup(adj, rows, rows, J, w, mode, 9, 1.5, 1e-3, 3, bc="sym" if mode == "per" else None)
+    res = []
+    for chain in (True, False):
+        wt.set_level_chain(chain)
+        f = adj.Fista(wt, bl, db, 1e-3, 2.0)
+        Fs = [f.step(objective=(k % 2 == 1)) for k in range(4)]
+        torch.cuda.synchronize()
+        res.append((f.x.clone(), f.y.clone(), [v for v in Fs if v is not None]))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    for a, b in zip(res[0][2], res[1][2]):
+        assert abs(a - b) <= 1e-12 * abs(b)
+    assert adj.device_status() == 0

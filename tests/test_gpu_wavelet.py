@@ -174,3 +174,44 @@ def test_errors_reach_python(adj):
     assert e.value.code == -4
     with pytest.raises(adj.AdjwtError):
         adj.WtPlan(12, 16, 3, "db2", "per")
+
+
+@pytest.mark.parametrize("rows,cols,J,w,mode", [
+    (2048, 2048, 5, "cdf97", "sym"), (2048, 2048, 5, "cdf97", "per"), (2048, 2048, 5, "cdf97", "zero"),
+    (256, 256, 3, "db2", "sym"), (300, 211, 4, "db4", "zero"), (70, 45, 3, "haar", "per"),
+    (64, 48, 2, "cdf97", "ppd"), (5, 7, 2, "db2", "sym")])
+def test_level_chain_equals_per_level_launches(adj, rows, cols, J, w, mode):
+    """The deep levels run as one level-chain launch by default.  The chain runs
+    the same tile code as the per-level launches, so W, W^* and W^dagger are
+    bit-identical with the chain on and off, and still match the oracle."""
+    if mode == "per":
+        rows, cols = rows + (-rows) % 2 ** J, cols + (-cols) % 2 ** J
+    plan = adj.WtPlan(rows, cols, J, w, mode)
+    starts = plan.chain_start()
+    x = plan.pack(random_vector(plan.logical_size, rows + 5 * cols))
+    img = image_dev(plan, random_vector((rows, cols), 3 * rows + cols))
+    on = [adj.wt_synth(plan, x).clone(), adj.wt_synth_adjoint(plan, img).clone(), adj.wt_analysis(plan, img).clone()]
+    plan.set_level_chain(False)
+    assert plan.chain_start() == {"synth": 0, "analysis": 0, "prox": 0}
+    off = [adj.wt_synth(plan, x), adj.wt_synth_adjoint(plan, img), adj.wt_analysis(plan, img)]
+    torch.cuda.synchronize()
+    for name, a, b in zip(("W", "W^*", "W^dagger"), on, off):
+        assert torch.equal(a, b), f"{name} {rows}x{cols} J{J} {w} {mode}: chain differs from per-level launches"
+    if rows * cols <= 300 * 300:
+        assert_close(plan.unpack(on[1]).cpu().numpy(), owt.wt_adjoint(img[:, :cols].double().cpu().numpy(), J, w, mode),
+                     what=f"W^* chain {w} {mode}")
+    assert adj.device_status() == 0
+    print(f"\nchain start {rows}x{cols} J{J} {w} {mode}: {starts}")
+
+
+def test_level_chain_is_where_the_rule_puts_it(adj):
+    """2048^2, 5 levels: levels 2..5 chained under SYM and ZERO (level 1 runs
+    on the TMA kernels); PER hands levels 1-3 to the TMA kernels and chains
+    4..5 of W (W^* runs level 1 alone on them, so it chains 2..5); PPD
+    reconstruction has no chain; small images chain every level."""
+    for mode, want in (("sym", (2, 2)), ("zero", (2, 2)), ("per", (4, 2))):
+        s = adj.WtPlan(2048, 2048, 5, "cdf97", mode).chain_start()
+        assert s == {"synth": want[0], "analysis": want[1], "prox": want[1]}, (mode, s)
+    assert adj.WtPlan(512, 512, 4, "cdf97", "ppd").chain_start()["synth"] == 0
+    assert adj.WtPlan(256, 256, 3, "db2", "sym").chain_start() == {"synth": 1, "analysis": 1, "prox": 1}
+    assert adj.WtPlan(256, 256, 1, "db2", "sym").chain_start() == {"synth": 0, "analysis": 0, "prox": 0}
