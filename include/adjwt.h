@@ -396,6 +396,10 @@ int adjwt_trace_enable(int capacity);
 int adjwt_trace_reset(void);
 int adjwt_trace_count(void);
 int adjwt_trace_get(int i, const char** name, int* tag, float* ms);
+/* Device milliseconds from the start of trace record `first` to the end of
+ * record `last` (first <= last, same stream): one multi-kernel call, launch
+ * gaps included.  INVALID_ARG for indices outside the records. */
+int adjwt_trace_span(int first, int last, float* ms);
 
 #ifdef __cplusplus
 }

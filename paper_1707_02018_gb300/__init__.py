@@ -486,6 +486,13 @@ def trace_reset():
     _lib.check(lib().adjwt_trace_reset())
 
 
+def trace_span(first, last):
+    """Device milliseconds from the start of trace record `first` to the end of `last`."""
+    ms = C.c_float()
+    _lib.check(lib().adjwt_trace_span(int(first), int(last), C.byref(ms)))
+    return float(ms.value)
+
+
 def trace_records():
     """[(kernel name, tag, milliseconds)] of the armed trace (waits for each record)."""
     out = []

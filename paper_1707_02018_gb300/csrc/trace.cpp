@@ -77,3 +77,14 @@ extern "C" int adjwt_trace_get(int i, const char** name, int* tag, float* ms) {
   if (ms) *ms = t;
   return ADJWT_OK;
 }
+
+// Device time from the start of record `first` to the end of record `last`
+// (both on one stream, first <= last): a whole multi-kernel operator call,
+// launch gaps included.
+extern "C" int adjwt_trace_span(int first, int last, float* ms) {
+  if (first < 0 || last < first || last >= g_used || !ms)
+    return fail(ADJWT_ERR_INVALID_ARG, "adjwt_trace_span: indices out of range or ms NULL");
+  ADJWT_CUDA_CHECK(cudaEventSynchronize(g_pool[last].b));
+  ADJWT_CUDA_CHECK(cudaEventElapsedTime(ms, g_pool[first].a, g_pool[last].b));
+  return ADJWT_OK;
+}

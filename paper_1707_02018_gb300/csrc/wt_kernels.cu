@@ -1077,8 +1077,12 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     chain.nlev = p->levels - j0 + 1;
     chain.counters = chain_counters(p, llbuf1);
     chain.status = device_status_ptr();
-    ADJWT_CUDA_CHECK(cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
     const char* name = !adjoint ? "wt_analysis_chain" : (prox.x ? "wt_adjoint_prox_chain" : "wt_adjoint_chain");
+    const char* rname =
+        !adjoint ? "wt_analysis_chain_reset" : (prox.x ? "wt_adjoint_prox_chain_reset" : "wt_adjoint_chain_reset");
+    cudaError_t me = cudaSuccess;
+    ADJWT_TRACED(rname, j0, s, me = cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
+    ADJWT_CUDA_CHECK(me);
     int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
       auto kern = k_analysis_chain<decltype(Lc)::value>;
       const size_t dyn = prox.x ? kProxSlotBytes : 0;
@@ -1116,7 +1120,9 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
     }
     chain.counters = chain_counters(p, llbuf1);
     chain.status = device_status_ptr();
-    ADJWT_CUDA_CHECK(cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
+    cudaError_t me = cudaSuccess;
+    ADJWT_TRACED("wt_synth_chain_reset", j0, s, me = cudaMemsetAsync(chain.counters, 0, kChainCounterBytes, s));
+    ADJWT_CUDA_CHECK(me);
     int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
       auto kern = k_synthesis_chain<decltype(Lc)::value>;
       static const int per_sm = resident_per_sm(kern, kThreads, 0);
