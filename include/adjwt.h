@@ -383,6 +383,13 @@ int fista_vjp_step(const adjwt_fista_problem* prob, const adjwt_blur_plan* dblur
                    const float* x_next, const float* y_k, double beta, float* xbar, float* ybar, float* db,
                    double* dtau_dev, double* dsigma_dev, void* ws, size_t ws_bytes, adjwt_stream_t stream);
 
+/* Measured float32 FMA rate of the current device in TFLOP/s (no
+ * counterpart in the paper; it gives the blur and channel-gradient rooflines
+ * their float32 ceiling): independent FMA chains on every SM, no memory
+ * traffic, best of five timed launches.  Synchronises the stream; allocates
+ * nothing.  INVALID_ARG (NULL), CUDA. */
+int adjwt_fp32_fma_peak(double* tflops, adjwt_stream_t stream);
+
 /* ------------------------------------------------------------------- tracing
  * Optional per-kernel device timing without a profiler (the paper has no
  * counterpart; it serves the measurement harness).  adjwt_trace_enable(n)

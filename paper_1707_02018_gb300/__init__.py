@@ -486,6 +486,13 @@ def trace_reset():
     _lib.check(lib().adjwt_trace_reset())
 
 
+def fp32_fma_peak(stream=None):
+    """Measured float32 FMA rate of the current device, TFLOP/s."""
+    v = C.c_double()
+    _lib.check(lib().adjwt_fp32_fma_peak(C.byref(v), _stream(stream)))
+    return float(v.value)
+
+
 def trace_span(first, last):
     """Device milliseconds from the start of trace record `first` to the end of `last`."""
     ms = C.c_float()
