@@ -510,7 +510,6 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
     net.train_step(B[:batch], U[:batch], size, size, lr=0.0)
     torch.cuda.synchronize()
     recs = adj.trace_records()
-    spans = whole_operator_spans(adj, recs)
     adj.trace_enable(0)
     per = {}
     for name, _, ms in recs:
@@ -756,6 +755,7 @@ def ours(args):
         run_step_device(adj, probs, ch) if graph is not None else run_step(adj, probs, ch)
     torch.cuda.synchronize()
     recs = adj.trace_records()
+    spans = whole_operator_spans(adj, recs)
     adj.trace_enable(0)
 
     ms = max_over_ranks(torch, dist, ms_local, world, "cuda")

@@ -839,7 +839,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis_chain(const __grid_
   __shared__ AnaArgs s_a;
   __shared__ int s_word[2];
   __shared__ double red[kAnaThreads / 32];
-  float l1 = 0.0f;
+  double l1 = 0.0;  // float32 within a tile (as the per-level kernel), float64 across tiles
   int cur = -1;
   for (;;) {
     int item, lev;
@@ -852,11 +852,13 @@ __global__ void __launch_bounds__(kAnaThreads, 2) k_analysis_chain(const __grid_
     }
     const int local = item - c.first_item[lev];
     const int ty = local / s_a.tiles_c;
-    analysis_tile<L, true>(s_a, ty, local - ty * s_a.tiles_c, l1);
+    float l1_tile = 0.0f;
+    analysis_tile<L, true>(s_a, ty, local - ty * s_a.tiles_c, l1_tile);
+    l1 += l1_tile;
     chain_done(c.counters, lev);
   }
   if (c.l1) {
-    const double tot = block_sum<kAnaThreads>((double)l1, red);
+    const double tot = block_sum<kAnaThreads>(l1, red);
     if (threadIdx.x == 0) c.l1[blockIdx.x] = tot;
   }
 }

@@ -214,8 +214,9 @@ def test_nonfinite_observation_is_reported(adj):
 @pytest.mark.parametrize("rows,J,w,mode", [(256, 3, "db2", "sym"), (2048, 5, "cdf97", "sym"), (2048, 5, "cdf97", "per")])
 def test_level_chain_fista_steps(adj, rows, J, w, mode):
     """FISTA with the prox epilogue in the level chain and without it: the
-    iterates are bit-identical; the objective (whose |x| partials are summed
-    over a different CTA split) agrees to float64 rounding."""
+    iterates are bit-identical; the objective (whose |x| partials, float32
+    within a tile, are summed in float64 over a different CTA split) agrees
+    to float64 rounding."""
     prob, wt, bl, db = _setup(adj, rows, rows, J, w, mode, 9, 1.5, 1e-3, 3, bc="sym" if mode == "per" else None)
     res = []
     for chain in (True, False):
@@ -226,5 +227,5 @@ def test_level_chain_fista_steps(adj, rows, J, w, mode):
         res.append((f.x.clone(), f.y.clone(), [v for v in Fs if v is not None]))
     assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
     for a, b in zip(res[0][2], res[1][2]):
-        assert abs(a - b) <= 1e-12 * abs(b)
+        assert abs(a - b) <= 1e-13 * abs(b)
     assert adj.device_status() == 0
