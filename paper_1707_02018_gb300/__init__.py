@@ -103,8 +103,8 @@ class WtPlan:
         return out
 
     def set_level_chain(self, enabled):
-        """Run the deepest tiled-only levels as one launch (True, the default)
-        or one launch per level (False)."""
+        """Run the deepest tiled-only levels as one launch (True) or one launch
+        per level (False, the default: measured faster on GB300)."""
         _lib.check(lib().adjwt_wt_plan_set_level_chain(self._h, int(bool(enabled))))
 
     def chain_start(self):

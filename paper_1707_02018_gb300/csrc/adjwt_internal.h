@@ -142,9 +142,9 @@ struct adjwt_wt_plan {
   // TMA kernel takes the tiles the size rule gives it (set by
   // adjwt_wt_plan_set_tma / adjwt_wt_plan_autotune)
   unsigned char tma_off[3][adjwt::kMaxLevels] = {};
-  // the deepest run of tiled-only levels runs as one level-chain launch
-  // unless switched off (adjwt_wt_plan_set_level_chain)
-  bool chain_off = false;
+  // the deepest run of tiled-only levels runs as one level-chain launch only
+  // when switched on (adjwt_wt_plan_set_level_chain); off by default
+  bool chain_off = true;
 };
 
 struct adjwt_blur_plan {

@@ -1089,7 +1089,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       auto kern = k_analysis_chain<decltype(Lc)::value>;
       const size_t dyn = prox.x ? kProxSlotBytes : 0;
       if (dyn) ADJWT_CUDA_CHECK(set_smem(kern, dyn));
-      static const int per_sm = resident_per_sm(kern, kAnaThreads, kProxSlotBytes);
+      const int per_sm = resident_per_sm(kern, kAnaThreads, dyn);  // after the attribute: it bounds the query
       const int ncta = std::max(1, std::min(chain.first_item[chain.nlev], per_sm * sm_count()));
       chain.l1 = (prox.x && prox.l1_partials) ? prox.l1_partials + slot : nullptr;
       slot += ncta;
@@ -1127,7 +1127,7 @@ int launch_wt_synth(const adjwt_wt_plan* p, const float* coeffs, float* image, f
     ADJWT_CUDA_CHECK(me);
     int rc = dispatch_L(fb.L, [&](auto Lc) -> int {
       auto kern = k_synthesis_chain<decltype(Lc)::value>;
-      static const int per_sm = resident_per_sm(kern, kThreads, 0);
+      const int per_sm = resident_per_sm(kern, kThreads, 0);
       const int ncta = std::max(1, std::min(chain.first_item[chain.nlev], per_sm * sm_count()));
       ADJWT_TRACED("wt_synth_chain", j0, s, pdl_launch(kern, dim3(ncta), kThreads, 0, s, chain));
       return ADJWT_OK;

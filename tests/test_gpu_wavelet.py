@@ -181,12 +181,15 @@ def test_errors_reach_python(adj):
     (256, 256, 3, "db2", "sym"), (300, 211, 4, "db4", "zero"), (70, 45, 3, "haar", "per"),
     (64, 48, 2, "cdf97", "ppd"), (5, 7, 2, "db2", "sym")])
 def test_level_chain_equals_per_level_launches(adj, rows, cols, J, w, mode):
-    """The deep levels run as one level-chain launch by default.  The chain runs
-    the same tile code as the per-level launches, so W, W^* and W^dagger are
-    bit-identical with the chain on and off, and still match the oracle."""
+    """With the level chain switched on, the deep levels run as one launch.  The
+    chain runs the same tile code as the per-level launches, so W, W^* and
+    W^dagger are bit-identical with the chain on and off, and still match
+    the oracle."""
     if mode == "per":
         rows, cols = rows + (-rows) % 2 ** J, cols + (-cols) % 2 ** J
     plan = adj.WtPlan(rows, cols, J, w, mode)
+    assert plan.chain_start() == {"synth": 0, "analysis": 0, "prox": 0}   # off by default
+    plan.set_level_chain(True)
     starts = plan.chain_start()
     x = plan.pack(random_vector(plan.logical_size, rows + 5 * cols))
     img = image_dev(plan, random_vector((rows, cols), 3 * rows + cols))
@@ -209,9 +212,13 @@ def test_level_chain_is_where_the_rule_puts_it(adj):
     on the TMA kernels); PER hands levels 1-3 to the TMA kernels and chains
     4..5 of W (W^* runs level 1 alone on them, so it chains 2..5); PPD
     reconstruction has no chain; small images chain every level."""
+    def starts(*args):
+        plan = adj.WtPlan(*args)
+        plan.set_level_chain(True)
+        return plan.chain_start()
     for mode, want in (("sym", (2, 2)), ("zero", (2, 2)), ("per", (4, 2))):
-        s = adj.WtPlan(2048, 2048, 5, "cdf97", mode).chain_start()
+        s = starts(2048, 2048, 5, "cdf97", mode)
         assert s == {"synth": want[0], "analysis": want[1], "prox": want[1]}, (mode, s)
-    assert adj.WtPlan(512, 512, 4, "cdf97", "ppd").chain_start()["synth"] == 0
-    assert adj.WtPlan(256, 256, 3, "db2", "sym").chain_start() == {"synth": 1, "analysis": 1, "prox": 1}
-    assert adj.WtPlan(256, 256, 1, "db2", "sym").chain_start() == {"synth": 0, "analysis": 0, "prox": 0}
+    assert starts(512, 512, 4, "cdf97", "ppd")["synth"] == 0
+    assert starts(256, 256, 3, "db2", "sym") == {"synth": 1, "analysis": 1, "prox": 1}
+    assert starts(256, 256, 1, "db2", "sym") == {"synth": 0, "analysis": 0, "prox": 0}
