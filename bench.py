@@ -563,22 +563,33 @@ def learned_warm_start(adj, torch, size=512, levels=4, wavelet="cdf97", n_train=
             val = f.step(objective=(k % 50 == 0 or k == ref_iters))
             if val is not None:
                 fstar = min(fstar, val)
+        nz_sol = float((f.x != 0).sum()) / f.x.numel()  # the ref_iters solution
         f0 = f.objective(torch.zeros_like(f.x))
-        xw = net.warm_start(wt, B[i])
-        fw = f.objective(xw)
+        tau = LAM / L  # the threshold of one FISTA prox
+        xd = net.warm_start(wt, B[i])            # dense: W^dagger u_hat
+        xw = net.warm_start(wt, B[i], tau=tau)   # soft-thresholded at lambda / L
+        fd, fw = f.objective(xd), f.objective(xw)
+        nz = lambda v: float((v != 0).sum()) / v.numel()
         zs, zi, zr, zm = time_to_tol(f, None, match=fw)
-        ws_, wi, wr, _ = time_to_tol(f, lambda: net.warm_start(wt, B[i]))
+        ws_, wi, wr, _ = time_to_tol(f, lambda: net.warm_start(wt, B[i], tau=tau))
+        ds, di, dr, _ = time_to_tol(f, lambda: net.warm_start(wt, B[i]))
         tests.append({"F_star": fstar, "rel_F_at_zero": (f0 - fstar) / fstar, "rel_F_at_warm": (fw - fstar) / fstar,
+                      "rel_F_at_warm_dense": (fd - fstar) / fstar, "nonzero_frac_warm": nz(xw),
+                      "nonzero_frac_warm_dense": nz(xd), "nonzero_frac_fista_solution": nz_sol,
                       "zero_start_iterations_to_F_warm": zm,
                       "zero_start": {"seconds": zs, "iterations": zi, "reached": zr},
-                      "warm_start": {"seconds": ws_, "iterations": wi, "reached": wr}})
+                      "warm_start": {"seconds": ws_, "iterations": wi, "reached": wr},
+                      "warm_start_dense": {"seconds": ds, "iterations": di, "reached": dr}})
     zsum = sum(t["zero_start"]["seconds"] for t in tests)
     wsum = sum(t["warm_start"]["seconds"] for t in tests)
+    dsum = sum(t["warm_start_dense"]["seconds"] for t in tests)
     return {"size": size, "levels": levels, "wavelet": wavelet, "train_images": n_train, "test_images": n_test,
             "target_iterations": target_iters, "targets_sec": gen_s, "batch": batch, "train_steps": train_steps,
             "train_sec": train_s, "train_images_per_sec": train_steps * batch / train_s,
             "loss_every_100_steps": losses, "conv32": conv, "train_step_kernels": kern, "held_out": tests,
-            "zero_start_sec_total": zsum, "warm_start_sec_total": wsum, "speedup": zsum / wsum}
+            "zero_start_sec_total": zsum, "warm_start_sec_total": wsum, "speedup": zsum / wsum,
+            "warm_start": "x_0 = S_tau(W^dagger u_hat), tau = lambda / L (one prox threshold)",
+            "dense_warm_start_sec_total": dsum, "speedup_dense": zsum / dsum}
 
 
 def batch_problems(adj, torch, seed=7000):

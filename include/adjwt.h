@@ -343,6 +343,10 @@ int adjwt_fista_lipschitz(const adjwt_fista_problem* prob, float* v, int iters, 
  * adjwt_axpby: out[i] = a x[i] + b y[i], i < n (device float32; out may
  * alias x or y).
  *
+ * adjwt_soft_threshold: out[i] = sign(in[i]) max(|in[i]| - tau, 0), i < n,
+ * the soft threshold of the FISTA prox (Sec. I-B) on its own (e.g. to
+ * sparsify a warm start); out may alias in; tau >= 0 finite (INVALID_ARG).
+ *
  * adjwt_dot: *out_dev (DEVICE double) = sum over rows x cols of x y, both
  * arrays with row pitch `pitch` floats (a coefficient vector: rows = 1,
  * cols = pitch = length).  Float64 per-block partials, added in a fixed
@@ -357,6 +361,7 @@ int adjwt_fista_lipschitz(const adjwt_fista_problem* prob, float* v, int iters, 
 int adjwt_gaussian_taps(int k, double sigma, double* taps, double* dtaps_dsigma);
 size_t adjwt_reduce_workspace_size(void);
 int adjwt_axpby(int64_t n, float a, const float* x, float b, const float* y, float* out, adjwt_stream_t stream);
+int adjwt_soft_threshold(int64_t n, const float* in, double tau, float* out, adjwt_stream_t stream);
 int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* out_dev, void* ws,
               size_t ws_bytes, adjwt_stream_t stream);
 int fista_prox_vjp(int64_t n, const float* x_next, const float* xbar, float* zbar, double* sign_dot_dev, void* ws,

@@ -425,6 +425,14 @@ def axpby(a, x, b, y, out=None, stream=None):
     return out
 
 
+def soft_threshold(x, tau, out=None, stream=None):
+    """out = sign(x) max(|x| - tau, 0) (the FISTA prox's soft threshold)."""
+    out = torch.empty_like(x) if out is None else out
+    _need(out, x.numel(), "out")
+    _lib.check(lib().adjwt_soft_threshold(x.numel(), _ptr(x), float(tau), _ptr(out), _stream(stream)))
+    return out
+
+
 _reduce_ws = {}
 
 

@@ -67,6 +67,7 @@ PROTOTYPES = {
     "adjwt_fista_momentum": (C.c_int, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "adjwt_reduce_workspace_size": (SZ, []),
     "adjwt_axpby": (C.c_int, [I64, C.c_float, VP, C.c_float, VP, VP, VP]),
+    "adjwt_soft_threshold": (C.c_int, [C.c_int64, VP, C.c_double, VP, VP]),
     "adjwt_dot": (C.c_int, [C.c_int, I64, I64, VP, VP, VP, VP, SZ, VP]),
     "fista_prox_vjp": (C.c_int, [I64, VP, VP, VP, VP, VP, SZ, VP]),
     "adjwt_fista_vjp_workspace_size": (SZ, [C.POINTER(FistaProblem)]),

@@ -13,6 +13,7 @@
 //     scalar gradients), with per-block float64 partials added in a fixed
 //     order, so results are reproducible.
 #include <algorithm>
+#include <cmath>
 
 #include "adjwt_internal.h"
 #include "device_common.cuh"
@@ -33,6 +34,16 @@ __global__ void __launch_bounds__(kThreads) k_axpby(int rows, int64_t cols, int6
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     const int64_t r = i / cols, o = r * pitch + (i - r * cols);
     out[o] = fmaf(a, x[o], b * y[o]);
+  }
+}
+
+// out = S_tau(in): the soft threshold of the FISTA prox (|v| <= tau -> 0)
+__global__ void __launch_bounds__(kThreads) k_soft(int64_t n, const float* __restrict__ in, float tau,
+                                                   float* __restrict__ out) {
+  pdl_entry();
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const float v = in[i], mag = fabsf(v) - tau;
+    out[i] = mag > 0.0f ? copysignf(mag, v) : 0.0f;
   }
 }
 
@@ -115,6 +126,18 @@ extern "C" int adjwt_axpby(int64_t n, float a, const float* x, float b, const fl
   if (n == 0) return ADJWT_OK;
   if (!x || !y || !out) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_axpby: NULL pointer");
   return launch_axpby(1, n, n, a, x, b, y, out, stream);
+}
+
+extern "C" int adjwt_soft_threshold(int64_t n, const float* in, double tau, float* out, adjwt_stream_t stream) {
+  if (n < 0) return fail(ADJWT_ERR_SHAPE, "adjwt_soft_threshold: n < 0");
+  if (n == 0) return ADJWT_OK;
+  if (!in || !out) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_soft_threshold: NULL pointer");
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_soft_threshold: need finite tau >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned nb = static_cast<unsigned>(std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * 152));
+  ADJWT_TRACED("soft_threshold", 0, st, pdl_launch(k_soft, nb, kThreads, 0, st, n, in, static_cast<float>(tau), out));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
 }
 
 extern "C" int adjwt_dot(int rows, int64_t cols, int64_t pitch, const float* x, const float* y, double* out_dev,

@@ -804,7 +804,8 @@ __device__ __forceinline__ void chain_next(const int* first_item, int nlev, int*
       record_status(status, ADJWT_ERR_TIMEOUT);
       item = -1;
     }
-    __threadfence();
+    // (the acquire load of the wait, then the block barrier, orders every
+    // thread's reads of the level's input after the producers' writes)
     s_word[0] = item;
     s_word[1] = lev;
   }

@@ -17,7 +17,7 @@ import ctypes as C
 
 import torch
 
-from . import _lib, _ptr, _stream, lib, workspace, wt_analysis
+from . import _lib, _ptr, _stream, lib, soft_threshold, workspace, wt_analysis
 
 
 # (Cout, Cin) of the eight 3x3 layers
@@ -99,10 +99,13 @@ class WarmStartNet:
         self.adam(lr, stream=stream)
         return self.loss
 
-    def warm_start(self, wt, b, stream=None):
-        """x_0 = W^dagger u_hat for one observation b ((rows, image_pitch) image of plan wt)."""
+    def warm_start(self, wt, b, tau=0.0, stream=None):
+        """x_0 = S_tau(W^dagger u_hat) for one observation b ((rows, image_pitch)
+        image of plan wt); tau > 0 soft-thresholds the analysis coefficients
+        (tau = lambda / L_f is the threshold of one FISTA prox)."""
         u_hat = self.forward(b.reshape(1, wt.rows, wt.image_pitch), wt.rows, wt.cols, stream=stream)
-        return wt_analysis(wt, u_hat.reshape(wt.rows, wt.image_pitch), stream=stream)
+        x0 = wt_analysis(wt, u_hat.reshape(wt.rows, wt.image_pitch), stream=stream)
+        return soft_threshold(x0, tau, out=x0, stream=stream) if tau > 0 else x0
 
 
 def conv32(n, rows, cols, x, packed_layer, bias=None, relu=False, mask=None, out=None, stream=None):
