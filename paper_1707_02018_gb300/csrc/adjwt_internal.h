@@ -183,10 +183,10 @@ int syn_chain_start(const adjwt_wt_plan* p);
 void synth_tma_rect(const adjwt_wt_plan* p, int j, int* r0, int* r1, int* c0, int* c1);
 int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], float* out, int out_pitch,
                      cudaStream_t s);
-// Coefficient rectangle of level j computed by the persistent TMA analysis
-// kernel (W^*, optionally with the prox, or W^dagger), and its launcher;
-// *ncta receives the number of l1 partial slots it wrote.
-void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, bool prox, int* r0, int* r1, int* c0, int* c1);
+// Whether level j of the analysis direction (W^*, optionally with the prox,
+// or W^dagger) runs whole on the persistent TMA analysis kernel, and its
+// launcher; *ncta receives the number of l1 partial slots it wrote.
+bool ana_tma_level(const adjwt_wt_plan* p, int j, bool prox);
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
                    float* const px[4], float* const py[4], int out_pitch, float step, float thresh, float beta,
                    const double* beta_dev, double* l1, const float* flo, const float* fhi, const char* name,

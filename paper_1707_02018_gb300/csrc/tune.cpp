@@ -35,11 +35,9 @@ bool key_of(const adjwt_wt_plan* p, Key* k) {
 }
 
 bool uses(const adjwt_wt_plan* p, int op, int j) {
+  if (op != 0) return ana_tma_level(p, j, op == 2);
   int r0, r1, c0, c1;
-  if (op == 0)
-    synth_tma_rect(p, j, &r0, &r1, &c0, &c1);
-  else
-    ana_tma_rect(p, j, true, op == 2, &r0, &r1, &c0, &c1);
+  synth_tma_rect(p, j, &r0, &r1, &c0, &c1);
   return r1 > r0 && c1 > c0;
 }
 

@@ -947,10 +947,9 @@ int* chain_counters(const adjwt_wt_plan* p, float* llbuf1) {
 int ana_chain_start(const adjwt_wt_plan* p, bool adjoint, bool prox) {
   if (p->chain_off) return p->levels + 1;
   int j0 = p->levels + 1;
+  (void)adjoint;
   for (int j = p->levels; j >= 1; --j) {
-    int r0, r1, c0, c1;
-    ana_tma_rect(p, j, adjoint, prox, &r0, &r1, &c0, &c1);
-    if (r1 > r0) break;
+    if (ana_tma_level(p, j, prox)) break;
     j0 = j;
   }
   return p->levels - j0 + 1 >= 2 ? j0 : p->levels + 1;
@@ -1041,16 +1040,8 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       chain.first_item[i + 1] = chain.first_item[i] + ncta;
       continue;
     }
-    int r0, r1, c0, c1;  // coefficient rectangle of the TMA kernel
-    ana_tma_rect(p, j, adjoint, prox.x != nullptr, &r0, &r1, &c0, &c1);
-    if (r1 > r0) {
-      a.in_r0 = r0 / kTile;
-      a.in_r1 = r1 / kTile;
-      a.in_c0 = c0 / kTile;
-      a.in_c1 = c1 / kTile;
-      ncta -= (a.in_r1 - a.in_r0) * (a.in_c1 - a.in_c0);
-      grid = dim3(ncta, 1);
-    }
+    const bool tma = ana_tma_level(p, j, prox.x != nullptr);  // the whole level on the TMA kernel
+    if (tma) ncta = 0;
     const bool want_l1 = prox.x && prox.l1_partials;
     a.l1 = want_l1 ? prox.l1_partials + slot : nullptr;
     slot += ncta;
@@ -1066,7 +1057,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
       if (rc) return rc;
       ADJWT_CUDA_CHECK(cudaGetLastError());
     }
-    if (r1 > r0) {
+    if (tma) {
       int used = 0;
       const char* tname = !adjoint ? "wt_analysis_tma" : (prox.x ? "wt_adjoint_prox_tma" : "wt_adjoint_tma");
       int rc = launch_ana_tma(p, j, adjoint, a.in, a.in_pitch, a.dst, a.px, a.py, a.out_pitch, a.step, a.thresh,

@@ -369,9 +369,11 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 
 
 // ===================================================================== analysis
-// Persistent TMA-staged W^* (+ the FISTA prox) / W^dagger for the full tiles
-// of a level whose input window needs no weight, mirror or wrap (every full
-// tile under the zero extension: the TMA unit's zero fill is the extension).
+// Persistent TMA-staged W^* (+ the FISTA prox) / W^dagger for every tile of
+// a level.  The TMA unit's zero fill is the zero extension; a border tile's
+// window is completed after the copy from the extension map and the 1/c
+// weights (fix_window), and the last row / column tiles store only inside
+// the bands (pad columns as zero).
 // A tile is kAR x kAC coefficients of each band; its input window is
 // (2 kAR + L - 2) x (2 kAC + L - 2) samples of the extended signal, staged by
 // the TMA unit into one of two buffers while the previous tile is filtered:
@@ -410,6 +412,12 @@ struct AnaTmaArgs {
   int d_c;                // window column start minus its 16-byte-aligned start
   int ty0, tx0, ntx, ntiles;
   int out_pitch;
+  // border tiles: the level input and its extension (fix = 0 under ZERO,
+  // where the box's zero fill is the whole extension)
+  const float* in;
+  int in_pitch, Nr, Nc, nr, nc, mode, fix;
+  const float* winv_r;    // 1/c weights of W^* (null for W^dagger and PER / ZERO)
+  const float* winv_c;
   float* dst[4];          // plain destinations (LL, LH, HL, HH)
   float* px[4];           // prox state (non-null => prox band)
   float* py[4];
@@ -420,6 +428,71 @@ struct AnaTmaArgs {
   float flo[kMaxTaps], fhi[kMaxTaps];
 };
 
+// Border tiles.  The box holds img[e - sh] for every window cell whose image
+// index lies inside the image and zero elsewhere; a cell is rewritten from
+// the image when the extension gives it another value (a mirror or wrap
+// copy, or zero outside the extended signal) or a weight 1/c (W^*'s weighted
+// extension (E^dagger)^*, Eq. 2): value = w_r w_c img[src_r][src_c].  Per
+// axis the source and weight of each window row / column go to shared
+// tables first.  Interior windows return at once (uniform per tile).
+template <int L>
+__device__ __forceinline__ void fix_window(const AnaTmaArgs& a, float* S, int k0, int l0, int* tsrc, float* tw,
+                                           unsigned char* tsp) {
+  using G = AG<L>;
+  constexpr int Lp = L - 1;
+  const int e0r = 2 * k0 + 1 - Lp, e0c = 2 * l0 + 1 - Lp;  // extended coordinates of window row / column 0
+  auto plain = [&](int e0, int E, int N, const float* winv) {
+    const int lo = e0 - a.sh, g = winv ? Lp : 0;
+    return lo >= g && lo + E - 1 < N - g;
+  };
+  if (plain(e0r, G::ER, a.Nr, a.winv_r) && plain(e0c, G::EC, a.Nc, a.winv_c)) return;
+  for (int i = threadIdx.x; i < G::ER + G::EC; i += kNT) {
+    const bool row = i < G::ER;
+    const int u = row ? i : i - G::ER;
+    const int e = (row ? e0r : e0c) + u, N = row ? a.Nr : a.Nc;
+    const float* winv = row ? a.winv_r : a.winv_c;
+    const int x = e - a.sh;  // the image index the box read (zero outside the image)
+    int src;
+    if (a.mode == kPer) {
+      src = pos_mod(e, N);
+    } else {
+      src = (e >= 0 && e < N + 2 * Lp) ? ext_src(e - Lp, N, a.mode) : -1;
+    }
+    const float w = (src >= 0 && winv) ? __ldg(winv + src) : 1.0f;
+    const bool boxed = x >= 0 && x < N;
+    tsrc[i] = src;
+    tw[i] = w;
+    tsp[i] = ((src >= 0) ? (!boxed || src != x) : boxed) || w != 1.0f;
+  }
+  __syncthreads();
+  constexpr int total = G::ER * G::EC, U = 8;  // eight loads in flight per thread
+  for (int base = threadIdx.x; base < total; base += U * kNT) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kNT;
+      v[u] = 0.0f;
+      if (i < total) {
+        const int r = i / G::EC, c = i - r * G::EC;
+        if (tsp[r] || tsp[G::ER + c]) {
+          const int sr = tsrc[r], sc = tsrc[G::ER + c];
+          if (sr >= 0 && sc >= 0) v[u] = tw[r] * tw[G::ER + c] * __ldg(a.in + (size_t)sr * a.in_pitch + sc);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kNT;
+      if (i < total) {
+        const int r = i / G::EC, c = i - r * G::EC;
+        if (tsp[r] || tsp[G::ER + c]) S[r * G::BC + c] = v[u];
+      }
+    }
+  }
+  fence_proxy_async();  // these generic writes come before the TMA unit's next write into the buffer
+  __syncthreads();
+}
+
 template <int L, bool PROX>
 __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
     k_ana_tma(const __grid_constant__ CUtensorMap map, const AnaTmaArgs a) {
@@ -429,6 +502,9 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
   __shared__ double red[kNT / 32];
+  __shared__ int t_src[G::ER + G::EC];       // border tiles: per window row / column, source index,
+  __shared__ float t_w[G::ER + G::EC];       // weight and whether the box value must be rewritten
+  __shared__ unsigned char t_sp[G::ER + G::EC];
   float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
   float* V = buf0 + 2 * G::BUF;  // [2][kAR][VP]
   const int tid = threadIdx.x;
@@ -471,17 +547,21 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   // prox variant: a thread copies the prox state it will need for a tile
   // (its 8 coefficients of y and x in both of its bands) into its own slot
   // one tile ahead; only the thread itself reads the slot, so no barrier
+  // (cells past the last band row or the row pitch read as zero)
   auto prefetch_prox = [&](int tt) {
     int pk0, pl0;
     tile_origin(tt, pk0, pl0);
-    const size_t prow = (size_t)(pk0 + kk) * a.out_pitch + pl0 + kAP * warp;
+    const bool pv = pk0 + kk < a.nr;
+    const int pc = pl0 + kAP * warp;
+    const size_t prow = pv ? (size_t)(pk0 + kk) * a.out_pitch + pc : 0;
 #pragma unroll
     for (int hb = 0; hb < 2; ++hb) {
       if (!pxs[hb]) continue;
 #pragma unroll
       for (int q = 0; q < kAP / 4; ++q) {
-        cp_async16(slot + hb * 16 + 4 * q, pys[hb] + prow + 4 * q, 16u);
-        cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + prow + 4 * q, 16u);
+        const bool in = pv && pc + 4 * q + 4 <= a.out_pitch;
+        cp_async16(slot + hb * 16 + 4 * q, pys[hb] + (in ? prow + 4 * q : 0), in ? 16u : 0u);
+        cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + (in ? prow + 4 * q : 0), in ? 16u : 0u);
       }
     }
     cp_async_commit();
@@ -493,7 +573,9 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
     int k0, l0;
     tile_origin(t, k0, l0);
     if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
-    const size_t row = (size_t)(k0 + kk) * a.out_pitch + l0 + kAP * warp;
+    const bool rvalid = k0 + kk < a.nr;     // the last row tile may be partial
+    const int lbase = l0 + kAP * warp;      // and the last column tile
+    const size_t row = rvalid ? (size_t)(k0 + kk) * a.out_pitch + lbase : 0;
     // this tile's prox state from the slot, then the next tile's requested
     float yv[2][kAP], xv[2][kAP];
     if (PROX && rower) {
@@ -523,6 +605,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
       if (PROX) cp_async_wait_all();
       return;
     }
+    if (a.fix) fix_window<L>(a, buf0 + b * G::BUF + a.d_c, k0, l0, t_src, t_w, t_sp);
     const float* S = buf0 + b * G::BUF + a.d_c;
     // column pass: V[f][kk][ec] = sum_t f[t] T[2 kk + L' - t][ec]
     for (int item = tid; item < 2 * G::EC; item += kNT) {
@@ -565,21 +648,29 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
         res[1][p] = hi;
       }
       float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
+      // pad columns (band index >= nc, inside the pitch) are written as zero
+#pragma unroll
+      for (int p = 0; p < kAP; ++p)
+        if (lbase + p >= a.nc) res[0][p] = res[1][p] = 0.0f;
 #pragma unroll
       for (int hb = 0; hb < 2; ++hb) {
+        if (!rvalid) break;
         if (PROX && pxs[hb]) {
           float xn[kAP], yn[kAP];
 #pragma unroll
           for (int p = 0; p < kAP; ++p) {
             const float v = yv[hb][p] - a.step * res[hb][p];
             const float mag = fabsf(v) - a.thresh;
-            const float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
+            float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
+            float y = fmaf(beta, x - xv[hb][p], x);
+            if (lbase + p >= a.nc) x = y = 0.0f;
             xn[p] = x;
-            yn[p] = fmaf(beta, x - xv[hb][p], x);
+            yn[p] = y;
             if (a.l1) l1 += fabsf(x);
           }
 #pragma unroll
           for (int q = 0; q < kAP / 4; ++q) {
+            if (lbase + 4 * q + 4 > a.out_pitch) break;
             reinterpret_cast<float4*>(pxs[hb] + row)[q] =
                 make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
             reinterpret_cast<float4*>(pys[hb] + row)[q] =
@@ -587,9 +678,11 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
           }
         } else if (dst[hb]) {
 #pragma unroll
-          for (int q = 0; q < kAP / 4; ++q)
+          for (int q = 0; q < kAP / 4; ++q) {
+            if (lbase + 4 * q + 4 > a.out_pitch) break;
             reinterpret_cast<float4*>(dst[hb] + row)[q] =
                 make_float4(res[hb][4 * q], res[hb][4 * q + 1], res[hb][4 * q + 2], res[hb][4 * q + 3]);
+          }
         }
       }
     }
@@ -650,25 +743,13 @@ int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, co
 
 }  // namespace
 
-// Coefficient rectangle [r0, r1) x [c0, c1) of level j's bands computed by
-// the TMA kernel (rows aligned to 32, columns to 64; empty for small levels).
-void ana_tma_rect(const adjwt_wt_plan* p, int j, bool adjoint, bool prox, int* r0, int* r1, int* c0, int* c1) {
-  *r0 = *r1 = *c0 = *c1 = 0;
-  if (p->tma_off[prox ? 2 : 1][j - 1]) return;
+// Whether level j of the analysis direction runs on the persistent TMA
+// kernel (every tile of the level, border tiles included) rather than the
+// tiled kernel: levels of at least 256 x 512 unless switched off.
+bool ana_tma_level(const adjwt_wt_plan* p, int j, bool prox) {
+  if (p->tma_off[prox ? 2 : 1][j - 1]) return false;
   const Level& L = p->lv[j - 1];
-  if (L.ax[0].N < 256 || L.ax[1].N < 512) return;
-  const bool weighted = adjoint && L.ax[0].winv != nullptr;
-  int ylo, yhi, xlo, xhi;
-  ana_range(L.ax[0].N, L.ax[0].n, kAR, p->bc, p->fb.L, weighted, &ylo, &yhi);
-  ana_range(L.ax[1].N, L.ax[1].n, kAC, p->bc, p->fb.L, weighted, &xlo, &xhi);
-  int rr0 = (ylo * kAR + 31) / 32 * 32, rr1 = yhi * kAR / 32 * 32;
-  if (rr1 - rr0 < 64 || xhi <= xlo) return;
-  const bool whole = rr0 == 0 && xlo == 0 && rr1 == L.ax[0].n && xhi * kAC == L.band_pitch;
-  if (!whole && (L.ax[0].N < kSplitMin || L.ax[1].N < kSplitMin)) return;
-  *r0 = rr0;
-  *r1 = rr1;
-  *c0 = xlo * kAC;
-  *c1 = xhi * kAC;
+  return L.ax[0].N >= 256 && L.ax[1].N >= 512;
 }
 
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],
@@ -676,20 +757,28 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
                    const double* beta_dev, double* l1, const float* flo, const float* fhi, const char* name,
                    cudaStream_t s, int* ncta) {
   *ncta = 0;
-  int r0, r1, c0, c1;
-  ana_tma_rect(p, j, adjoint, px[1] != nullptr, &r0, &r1, &c0, &c1);
-  if (r1 <= r0 || c1 <= c0) return ADJWT_OK;
+  if (!ana_tma_level(p, j, px[1] != nullptr)) return ADJWT_OK;
   const Level& L = p->lv[j - 1];
   const int Lf = p->fb.L, Lp = Lf - 1;
   AnaTmaArgs a{};
   a.sh = p->bc == kPer ? 0 : Lp;
-  const int first_c = 2 * c0 + 1 - Lp - a.sh;  // window start of column tile 0; tiles add 2 kAC (16-byte multiple)
+  const int first_c = 1 - Lp - a.sh;  // window start of column tile 0; tiles add 2 kAC (16-byte multiple)
   a.d_c = ((first_c % 4) + 4) % 4;
-  a.ty0 = r0 / kAR;
-  a.tx0 = c0 / kAC;
-  a.ntx = (c1 - c0) / kAC;
-  a.ntiles = a.ntx * ((r1 - r0) / kAR);
+  a.ty0 = 0;
+  a.tx0 = 0;
+  a.ntx = (out_pitch + kAC - 1) / kAC;
+  a.ntiles = a.ntx * ((L.ax[0].n + kAR - 1) / kAR);
   a.out_pitch = out_pitch;
+  a.in = in;
+  a.in_pitch = in_pitch;
+  a.Nr = L.ax[0].N;
+  a.Nc = L.ax[1].N;
+  a.nr = L.ax[0].n;
+  a.nc = L.ax[1].n;
+  a.mode = p->bc;
+  a.fix = p->bc != kZero;
+  a.winv_r = adjoint ? L.ax[0].winv : nullptr;
+  a.winv_c = adjoint ? L.ax[1].winv : nullptr;
   for (int b = 0; b < 4; ++b) {
     a.dst[b] = dst[b];
     a.px[b] = px[b];
