@@ -294,6 +294,51 @@ size_t adjwt_fista_workspace_size(const adjwt_fista_problem* prob);
 int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* ws, size_t ws_bytes,
                double* objective_out, adjwt_stream_t stream);
 
+/* Batched FISTA engine (the batching extension; the paper solves one
+ * problem at a time).  Many independent problems (Eq. 1, each with its own
+ * plans, observation, lambda, L_f and gradient mode) advance `iters` FISTA
+ * iterations in ONE persistent kernel launch: every (problem, stage, tile)
+ * is an item (stages: the momentum update, W level J..1, the fused
+ * R^*(R u - b), W^* + prox level 1..J; tiles of 32 x 32 wavelet outputs and
+ * 64 x 64 blur outputs), numbered stage-major across problems and taken by
+ * the CTAs in order; a stage starts once the previous stage of its problem
+ * is done.  Waits are bounded (ADJWT_ERR_TIMEOUT in the device status word;
+ * the launch then drains).  The objective F(x_k) of every problem runs as a
+ * second persistent launch.  Supported: ZERO / SYM / PER wavelet boundaries
+ * with every level longer than 2L' (not PPD), PSF radius <= 12.
+ *
+ * adjwt_fista_batch_workspace_size: device bytes for the count problems (u
+ * and g images, LL buffers, momentum and objective partials of each).
+ * adjwt_fista_batch_create: probs / x / y are HOST arrays of count entries;
+ * x[i], y[i] the DEVICE coefficient vectors of problem i (its state, as in
+ * adjwt_fista_state); ws: the workspace, 256-byte aligned, which the batch
+ * uses until destroyed.  The plans, observations and state buffers must
+ * outlive the batch.  Creation uploads the item tables (allocates device
+ * memory once); later calls allocate nothing.  Errors: INVALID_ARG, SHAPE
+ * (an unsupported problem), ALIGN, WORKSPACE, CUDA.
+ * adjwt_fista_batch_reset: t_1 = 1 for every problem (the caller zeroes or
+ * sets x and y, with y = x).
+ * adjwt_fista_batch_run: iters iterations of every problem, one launch
+ * (plus a memset of its counters) on `stream`.
+ * adjwt_fista_batch_objective: objectives_dev[i] (DEVICE doubles) =
+ * F(x_i) = 1/2 ||R W x_i - b_i||^2 + lambda_i ||x_i||_1, one launch.
+ * adjwt_fista_batch_wait_selftest: one launch in which the first item waits
+ * for a stage that never runs: after about a second it records
+ * ADJWT_ERR_TIMEOUT in the device status word and the launch drains (a
+ * test of the bounded waits; the other problems may have advanced, so reset
+ * the batch before using it again).
+ * adjwt_fista_batch_info: items per iteration, stages, resident CTAs. */
+typedef struct adjwt_fista_batch adjwt_fista_batch;
+size_t adjwt_fista_batch_workspace_size(int count, const adjwt_fista_problem* probs);
+int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, const adjwt_fista_problem* probs, float* const* x,
+                             float* const* y, void* ws, size_t ws_bytes);
+void adjwt_fista_batch_destroy(adjwt_fista_batch* batch);
+int adjwt_fista_batch_reset(const adjwt_fista_batch* batch, adjwt_stream_t stream);
+int adjwt_fista_batch_run(const adjwt_fista_batch* batch, int iters, adjwt_stream_t stream);
+int adjwt_fista_batch_objective(const adjwt_fista_batch* batch, double* objectives_dev, adjwt_stream_t stream);
+int adjwt_fista_batch_wait_selftest(const adjwt_fista_batch* batch, adjwt_stream_t stream);
+int adjwt_fista_batch_info(const adjwt_fista_batch* batch, int* items_per_iteration, int* stages, int* ctas);
+
 /* FISTA's momentum as fista_step applies it (HOST, no device work):
  * t_next = (1 + sqrt(1 + 4 t^2))/2 and beta = (t - 1)/t_next rounded to
  * float32, the weight of y_{k+1} = x_k + beta (x_k - x_{k-1}).  t >= 1 and

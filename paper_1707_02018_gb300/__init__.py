@@ -400,6 +400,60 @@ class Fista:
 
 
 # ------------------------------------------------------------ differentiation
+class FistaBatch:
+    """Many FISTA problems advanced together by the batched engine (one
+    persistent launch per call of run(); see include/adjwt.h).  `fistas`: Fista
+    objects whose problem (plans, b, lambda, L_f, gradient) and state buffers
+    (x, y) the batch uses; they must outlive it."""
+
+    def __init__(self, fistas):
+        self.fistas = list(fistas)
+        n = len(self.fistas)
+        self._probs = (FistaProblem * n)(*[f.problem for f in self.fistas])
+        self._x = (C.c_void_p * n)(*[f.x.data_ptr() for f in self.fistas])
+        self._y = (C.c_void_p * n)(*[f.y.data_ptr() for f in self.fistas])
+        nbytes = lib().adjwt_fista_batch_workspace_size(n, self._probs)
+        if nbytes == 0:
+            raise ValueError("FistaBatch: invalid problems")
+        self.ws = workspace(nbytes)
+        h = C.c_void_p()
+        _lib.check(lib().adjwt_fista_batch_create(C.byref(h), n, self._probs, self._x, self._y, _ptr(self.ws),
+                                                  self.ws.numel()))
+        self._h = h
+        self.objectives = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.adjwt_fista_batch_destroy(h)
+            self._h = None
+
+    def reset(self, stream=None):
+        """x = y = 0 and t = 1 for every problem."""
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            for f in self.fistas:
+                f.x.zero_()
+                f.y.zero_()
+        _lib.check(lib().adjwt_fista_batch_reset(self._h, _stream(stream)))
+
+    def run(self, iters, stream=None):
+        _lib.check(lib().adjwt_fista_batch_run(self._h, int(iters), _stream(stream)))
+
+    def objective(self, stream=None):
+        """F(x_i) of every problem into self.objectives (device float64)."""
+        _lib.check(lib().adjwt_fista_batch_objective(self._h, _ptr(self.objectives), _stream(stream)))
+        return self.objectives
+
+    def wait_selftest(self, stream=None):
+        _lib.check(lib().adjwt_fista_batch_wait_selftest(self._h, _stream(stream)))
+
+    def info(self):
+        items, stages, ctas = C.c_int(), C.c_int(), C.c_int()
+        _lib.check(lib().adjwt_fista_batch_info(self._h, C.byref(items), C.byref(stages), C.byref(ctas)))
+        return {"items_per_iteration": items.value, "stages": stages.value, "ctas": ctas.value}
+
+
 def fista_momentum(t):
     """(beta_k, t_{k+1}) of FISTA's momentum as fista_step applies it; beta_k is
     the float32 weight of y_{k+1} = x_k + beta_k (x_k - x_{k-1})."""

@@ -58,6 +58,15 @@ PROTOTYPES = {
     "bce_gradient": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, SZ, VP]),
     "fista_step_device": (C.c_int, [C.POINTER(FistaProblem), VP, VP, VP, SZ, VP, VP]),
     "adjwt_fista_device_reset": (C.c_int, [C.POINTER(FistaProblem), VP, SZ, VP]),
+    "adjwt_fista_batch_workspace_size": (SZ, [C.c_int, C.POINTER(FistaProblem)]),
+    "adjwt_fista_batch_create": (C.c_int, [C.POINTER(VP), C.c_int, C.POINTER(FistaProblem), C.POINTER(VP),
+                                           C.POINTER(VP), VP, SZ]),
+    "adjwt_fista_batch_destroy": (None, [VP]),
+    "adjwt_fista_batch_reset": (C.c_int, [VP, VP]),
+    "adjwt_fista_batch_run": (C.c_int, [VP, C.c_int, VP]),
+    "adjwt_fista_batch_objective": (C.c_int, [VP, VP, VP]),
+    "adjwt_fista_batch_wait_selftest": (C.c_int, [VP, VP]),
+    "adjwt_fista_batch_info": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "adjwt_wt_plan_set_tma": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
     "adjwt_wt_plan_uses_tma": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "adjwt_wt_plan_set_level_chain": (C.c_int, [VP, C.c_int]),

@@ -1,0 +1,744 @@
+// Batched FISTA engine: many independent deblurring problems (Eq. 1, each
+// with its own image size, wavelet, depth and PSF) run `iters` FISTA
+// iterations in ONE persistent launch.
+//
+// Work items.  One iteration of problem p is a chain of stages
+//     MOM, W level J, ..., W level 1, R^*(R u - b), W^* level 1 (+prox), ..., W^* level J (+prox)
+// (MOM advances the device-resident momentum t_k, beta_k).  A stage is cut
+// into tiles: the tiled level bodies of wt_tiles.cuh (32 x 32 outputs) and
+// the fused blur body of blur_tile.cuh (64 x 64).  An item is one tile.  The
+// items of an iteration are numbered stage-major across problems (stage
+// slot s of every problem before slot s + 1 of any), iteration after
+// iteration; CTAs take the next item number from a counter.
+//
+// Dependencies.  A stage may start once every tile of the previous stage of
+// the same problem is done (the first stage: the last stage of the previous
+// iteration).  Per-stage done counters grow monotonically over the launch, so
+// the target of a wait is (iteration + 1) x (tiles of the stage waited on).
+// A CTA only waits on items numbered below its own, all handed out to
+// running CTAs, so the launch needs no co-residency.  Many problems keep
+// other items ready while one problem waits.
+//
+// Waits are bounded (kWaitCycles, about a second): a CTA that gives up
+// records ADJWT_ERR_TIMEOUT in the device status word and raises the
+// launch's abort flag, on which every other CTA stops taking items and every
+// wait returns.
+//
+// The objective F(x_k) = 1/2 ||R W x_k - b||^2 + lambda ||x_k||_1 runs as a
+// second persistent launch over all problems (W on x_k, the blur residual
+// norm, |x_k|, then a fixed-order sum per problem).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "adjwt_internal.h"
+#include "blur_tile.cuh"
+#include "device_common.cuh"
+#include "tma.cuh"
+#include "wt_tiles.cuh"
+
+namespace adjwt {
+namespace {
+
+constexpr int kEngineThreads = 256;
+constexpr int kEngineMaxRadius = 12;
+
+enum StageKind : int { kMom = 0, kSyn = 1, kBlur = 2, kAna = 3, kSum = 4, kL1 = 5 };
+
+// One stage of one problem's iteration.
+struct Stage {
+  int kind;
+  int param;       // filter length L (kSyn, kAna, kL1) or padded blur radius (kBlur)
+  int problem;
+  int args;        // index into the argument array of its kind
+  int ntiles, tiles_c;
+  int prev;        // stage waited on (-1: none)
+  int prev_tiles;  // its tiles
+  int prev_lag;    // 1: prev belongs to the previous iteration
+  int part;        // first partial slot of its tiles (kBlur, kAna with prox, kL1), else -1
+};
+
+struct ProbDev {
+  double* mom;      // m[0] = t_k, m[1] = beta_k
+  double* parts;    // partial slots: blur tiles first, then the |x| tiles
+  int nblur, nl1;
+  double lambda;
+};
+
+struct EngineArgs {
+  const Stage* stages;
+  const int* item_stage;   // per item of one iteration: its stage
+  const int* stage_first;  // per stage: its first item within the iteration
+  int items_per_iter;
+  int iters;
+  const SynArgs* syn;
+  const AnaArgs* ana;
+  const TiledArgs* blur;
+  const ProbDev* prob;
+  double* objectives;      // objective launch: one per problem
+  int* counters;           // [0] next item, [1] abort flag, [2 + stage] tiles done
+  int* status;
+  int stall;               // wait self-test: the first item waits for a stage that never runs
+};
+
+constexpr int kCtrDone = 2;
+
+// Bounded wait with acquire semantics until *ctr >= target, or the abort flag.
+__device__ __forceinline__ bool engine_wait(const int* ctr, int target, const int* abort_flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    int v, ab;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
+    if (ab) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
+    __nanosleep(64);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_block_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += kEngineThreads) d[i] = s[i];
+}
+
+template <typename Fn>
+__device__ __forceinline__ void with_L(int L, Fn&& fn) {
+  switch (L) {
+    case 2: fn(std::integral_constant<int, 2>()); break;
+    case 4: fn(std::integral_constant<int, 4>()); break;
+    case 8: fn(std::integral_constant<int, 8>()); break;
+    default: fn(std::integral_constant<int, 10>()); break;
+  }
+}
+
+// blur radii are padded up to one of these (zero taps leave the operator unchanged)
+__host__ __device__ constexpr int padded_radius(int r) { return r <= 2 ? 2 : r <= 4 ? 4 : r <= 6 ? 6 : r <= 9 ? 9 : 12; }
+
+template <typename Fn>
+__device__ __forceinline__ void with_R(int R, Fn&& fn) {
+  switch (R) {
+    case 2: fn(std::integral_constant<int, 2>()); break;
+    case 4: fn(std::integral_constant<int, 4>()); break;
+    case 6: fn(std::integral_constant<int, 6>()); break;
+    case 9: fn(std::integral_constant<int, 9>()); break;
+    default: fn(std::integral_constant<int, 12>()); break;
+  }
+}
+
+union StageArgs {
+  SynArgs syn;
+  AnaArgs ana;
+  TiledArgs blur;
+};
+
+constexpr int kL1Chunk = 8192;  // coefficients per |x| tile of the objective launch
+
+struct L1Args {
+  const float* x;
+  int64_t n;
+};
+
+// Shared memory of the engine: the bodies' smem (one at a time) at the start,
+// the prox slots of the analysis body after the largest analysis smem.
+constexpr size_t kProxOffset = (sizeof(AnaSmem<10>) + 127) / 128 * 128;
+
+// One body per call, kept out of line so that each is register-allocated on
+// its own rather than all of them together in the engine loop.
+template <int L>
+__device__ __noinline__ void engine_syn(const SynArgs& a, int ty, int tx, unsigned char* dyn) {
+  synthesis_tile<L, true>(a, ty, tx, *reinterpret_cast<SynSmem<L>*>(dyn));
+}
+
+template <int L>
+__device__ __noinline__ float engine_ana(const AnaArgs& a, int ty, int tx, unsigned char* dyn) {
+  float l1 = 0.0f;
+  analysis_tile<L, true, kEngineThreads>(a, ty, tx, l1, *reinterpret_cast<AnaSmem<L>*>(dyn),
+                                         reinterpret_cast<float*>(dyn + kProxOffset));
+  return l1;
+}
+
+template <int R>
+__device__ __noinline__ float engine_blur(const TiledArgs& a, int ty, int tx, unsigned char* dyn, int* s_border) {
+  float sq = 0.0f;
+  blur_normal_tile<R, true>(a, ty, tx, reinterpret_cast<float*>(dyn), s_border, sq);
+  return sq;
+}
+
+__global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const EngineArgs e, const L1Args* l1args) {
+  pdl_entry();
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ StageArgs s_args;
+  __shared__ int s_word[2];
+  __shared__ double red[kEngineThreads / 32];
+  __shared__ int s_border;
+  const int tid = threadIdx.x;
+  int* abort_flag = e.counters + 1;
+  const int total = e.items_per_iter * e.iters;
+  for (;;) {
+    if (tid == 0) {
+      int item = -1, st = 0;
+      int ab;
+      asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
+      if (!ab) {
+        item = atomicAdd(&e.counters[0], 1);
+        if (item >= total) item = -1;
+      }
+      if (item >= 0) {
+        const int it = item / e.items_per_iter;
+        st = e.item_stage[item - it * e.items_per_iter];
+        const Stage& S = e.stages[st];
+        int target = (it + 1 - S.prev_lag) * S.prev_tiles;
+        if (e.stall && item == 0) target = S.prev_tiles;  // a previous iteration that never ran
+        if (S.prev >= 0 && target > 0 && !engine_wait(&e.counters[kCtrDone + S.prev], target, abort_flag)) {
+          record_status(e.status, ADJWT_ERR_TIMEOUT);
+          atomicExch(abort_flag, 1);
+          item = -1;
+        }
+      }
+      s_word[0] = item;
+      s_word[1] = st;
+    }
+    __syncthreads();
+    const int item = s_word[0], st = s_word[1];
+    if (item < 0) break;
+    const int it = item / e.items_per_iter;
+    const Stage S = e.stages[st];
+    const int tile = item - it * e.items_per_iter - e.stage_first[st];
+    const int ty = tile / S.tiles_c, tx = tile - ty * S.tiles_c;
+    switch (S.kind) {
+      case kMom:
+        if (tid == 0) {
+          // device-resident momentum (the method cited in Sec. I-B):
+          // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, beta_k = (t_k - 1) / t_{k+1}
+          double* m = e.prob[S.problem].mom;
+          const double t = __ldcg(m);
+          const double t1 = 0.5 * (1.0 + sqrt(__dadd_rn(1.0, __dmul_rn(4.0 * t, t))));
+          m[1] = (t - 1.0) / t1;
+          m[0] = t1;
+        }
+        break;
+      case kSyn:
+        copy_block_args(&s_args.syn, &e.syn[S.args]);
+        __syncthreads();
+        with_L(S.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
+        break;
+      case kAna: {
+        copy_block_args(&s_args.ana, &e.ana[S.args]);
+        __syncthreads();
+        float l1 = 0.0f;
+        with_L(S.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
+        if (S.part >= 0) {
+          const double tot = block_sum<kEngineThreads>((double)l1, red);
+          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = tot;
+        }
+        break;
+      }
+      case kBlur: {
+        copy_block_args(&s_args.blur, &e.blur[S.args]);
+        __syncthreads();
+        float sq = 0.0f;
+        with_R(S.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
+        if (S.part >= 0) {
+          const double tot = block_sum<kEngineThreads>((double)sq, red);
+          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = 0.5 * tot;
+        }
+        break;
+      }
+      case kL1: {
+        const L1Args la = l1args[S.args];
+        const int64_t i0 = (int64_t)tile * kL1Chunk;
+        float acc = 0.0f;
+        for (int64_t i = i0 + tid; i < la.n && i < i0 + kL1Chunk; i += kEngineThreads) acc += fabsf(__ldcg(la.x + i));
+        const double tot = block_sum<kEngineThreads>((double)acc, red);
+        if (tid == 0) e.prob[S.problem].parts[S.part + tile] = tot;
+        break;
+      }
+      case kSum:
+        if (tid == 0) {
+          // F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1, partials added in a fixed order
+          const ProbDev pd = e.prob[S.problem];
+          double r = 0.0, l1 = 0.0;
+          for (int i = 0; i < pd.nblur; ++i) r += __ldcg(pd.parts + i);
+          for (int i = 0; i < pd.nl1; ++i) l1 += __ldcg(pd.parts + pd.nblur + i);
+          e.objectives[S.problem] = r + pd.lambda * l1;
+        }
+        break;
+      default:
+        break;
+    }
+    // every write of the tile happens before its count is published
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&e.counters[kCtrDone + st], 1);
+    }
+  }
+}
+
+__global__ void k_batch_reset(double* const* mom, int count) {
+  pdl_entry();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    mom[i][0] = 1.0;
+    mom[i][1] = 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace adjwt
+
+// ===================================================================== host
+namespace adjwt {
+namespace {
+
+// Workspace of one problem: u and g images, the LL ping-pong buffers, the
+// momentum (2 doubles) and the objective partials.
+struct ProbWs {
+  size_t u, g, ll0, ll1, mom, parts, bytes;
+  int nblur, nl1;
+};
+
+int blur_tiles(const adjwt_blur_plan* b) { return ((b->cols + kT - 1) / kT) * ((b->rows + kT - 1) / kT); }
+int l1_tiles(const adjwt_wt_plan* w) { return static_cast<int>((w->num_coeffs + kL1Chunk - 1) / kL1Chunk); }
+
+ProbWs prob_ws(const adjwt_fista_problem& pr) {
+  ProbWs w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += static_cast<size_t>(round_up(static_cast<int64_t>(bytes), 256));
+    return o;
+  };
+  const size_t img = (size_t)pr.wt->rows * pr.wt->image_pitch * sizeof(float);
+  w.u = take(img);
+  w.g = take(img);
+  w.ll0 = take(std::max<int64_t>(pr.wt->ll_buf_floats[0], 1) * sizeof(float));
+  w.ll1 = take(std::max<int64_t>(pr.wt->ll_buf_floats[1], 1) * sizeof(float));
+  w.mom = take(2 * sizeof(double));
+  w.nblur = blur_tiles(pr.blur);
+  w.nl1 = l1_tiles(pr.wt);
+  w.parts = take((size_t)(w.nblur + w.nl1) * sizeof(double));
+  w.bytes = off;
+  return w;
+}
+
+int blur_radius(const adjwt_blur_plan* b) { return padded_radius(std::max(b->kr / 2, b->kc / 2)); }
+
+int check_batch_problem(const adjwt_fista_problem& pr, int i) {
+  const std::string who = "fista_batch: problem " + std::to_string(i);
+  if (!pr.wt || !pr.blur || !pr.b) return fail(ADJWT_ERR_INVALID_ARG, who + ": plan or b is NULL");
+  if (pr.wt->rows != pr.blur->rows || pr.wt->cols != pr.blur->cols)
+    return fail(ADJWT_ERR_SHAPE, who + ": wavelet and blur plans describe different images");
+  if (pr.wt->bc == kPpd) return fail(ADJWT_ERR_SHAPE, who + ": the redundant periodic reconstruction is not batched");
+  for (const Level& L : pr.wt->lv)
+    if (L.generic_synth) return fail(ADJWT_ERR_SHAPE, who + ": a level of at most 2L' samples is not batched");
+  if (std::max(pr.blur->kr, pr.blur->kc) / 2 > kEngineMaxRadius)
+    return fail(ADJWT_ERR_SHAPE, who + ": PSF radius above 12");
+  if (!(pr.lambda >= 0.0) || !std::isfinite(pr.lambda)) return fail(ADJWT_ERR_INVALID_ARG, who + ": bad lambda");
+  if (!(pr.lipschitz > 0.0) || !std::isfinite(pr.lipschitz))
+    return fail(ADJWT_ERR_INVALID_ARG, who + ": lipschitz must be finite and > 0");
+  if (pr.gradient != ADJWT_GRAD_ADJOINT && pr.gradient != ADJWT_GRAD_PINV)
+    return fail(ADJWT_ERR_INVALID_ARG, who + ": unknown gradient mode");
+  if ((reinterpret_cast<uintptr_t>(pr.b) & 15u) != 0) return fail(ADJWT_ERR_ALIGN, who + ": b not 16-byte aligned");
+  return ADJWT_OK;
+}
+
+SynArgs syn_level(const adjwt_wt_plan* w, int j, const float* coeffs, float* out_image, float* const ll[2]) {
+  const Level& L = w->lv[j - 1];
+  SynArgs a{};
+  for (int b = 0; b < 4; ++b) a.band[b] = (b == 0 && j < w->levels) ? ll[j % 2] : coeffs + L.off_band[b];
+  a.band_pitch = L.band_pitch;
+  a.out = (j == 1) ? out_image : ll[(j - 1) % 2];
+  a.out_pitch = L.in_pitch;
+  a.Nr = L.ax[0].N;
+  a.Nc = L.ax[1].N;
+  a.nr = L.ax[0].n;
+  a.nc = L.ax[1].n;
+  a.mode = w->bc;
+  a.winv_r = L.ax[0].winv;
+  a.winv_c = L.ax[1].winv;
+  for (int t = 0; t < w->fb.L; ++t) {
+    a.g[0][t] = static_cast<float>(w->fb.rec_lo[t]);
+    a.g[1][t] = static_cast<float>(w->fb.rec_hi[t]);
+  }
+  a.tiles_c = (a.Nc + kTile - 1) / kTile;
+  a.tiles_r = (a.Nr + kTile - 1) / kTile;
+  return a;
+}
+
+AnaArgs ana_level(const adjwt_fista_problem& pr, int j, const float* in_image, float* x, float* y, float* const ll[2],
+                  const double* beta_dev) {
+  const adjwt_wt_plan* w = pr.wt;
+  const Level& L = w->lv[j - 1];
+  const bool adjoint = pr.gradient == ADJWT_GRAD_ADJOINT;
+  AnaArgs a{};
+  a.in = (j == 1) ? in_image : ll[(j - 1) % 2];
+  a.in_pitch = L.in_pitch;
+  a.Nr = L.ax[0].N;
+  a.Nc = L.ax[1].N;
+  a.nr = L.ax[0].n;
+  a.nc = L.ax[1].n;
+  a.mode = w->bc;
+  a.winv_r = adjoint ? L.ax[0].winv : nullptr;
+  a.winv_c = adjoint ? L.ax[1].winv : nullptr;
+  a.out_pitch = L.band_pitch;
+  for (int b = 0; b < 4; ++b) {
+    if (b > 0 || j == w->levels) {
+      a.px[b] = x + L.off_band[b];
+      a.py[b] = y + L.off_band[b];
+    } else {
+      a.dst[b] = ll[j % 2];
+    }
+  }
+  a.step = static_cast<float>(1.0 / pr.lipschitz);
+  a.thresh = static_cast<float>(pr.lambda / pr.lipschitz);
+  a.beta_dev = beta_dev;
+  const FilterBank& fb = w->fb;
+  for (int t = 0; t < fb.L; ++t) {
+    if (adjoint) {  // dual analysis filters: synthesis filters reversed (Eq. 3, Eq. 4)
+      a.flo[t] = static_cast<float>(fb.rec_lo[fb.L - 1 - t]);
+      a.fhi[t] = static_cast<float>(fb.rec_hi[fb.L - 1 - t]);
+    } else {
+      a.flo[t] = static_cast<float>(fb.dec_lo[t]);
+      a.fhi[t] = static_cast<float>(fb.dec_hi[t]);
+    }
+  }
+  a.tiles_c = (L.band_pitch + kTile - 1) / kTile;
+  a.tiles_r = (L.ax[0].n + kTile - 1) / kTile;
+  return a;
+}
+
+TiledArgs blur_args(const adjwt_fista_problem& pr, const float* u, float* g, double* partials) {
+  const adjwt_blur_plan* p = pr.blur;
+  const int R = blur_radius(p);
+  TiledArgs a{};
+  a.in = u;
+  a.b = pr.b;
+  a.out = g;
+  a.partials = partials;
+  a.rows = p->rows;
+  a.cols = p->cols;
+  a.pitch = p->image_pitch;
+  a.bc = p->bc;
+  const int orr = R - p->kr / 2, oc = R - p->kc / 2;
+  for (int t = 0; t < p->kr; ++t) a.pr[orr + t] = static_cast<float>(p->taps_r[t]);
+  for (int t = 0; t < p->kc; ++t) a.pc[oc + t] = static_cast<float>(p->taps_c[t]);
+  return a;
+}
+
+}  // namespace
+}  // namespace adjwt
+
+namespace adjwt {
+namespace {
+// One launch's tables (the iteration launch and the objective launch).
+struct BatchLaunch {
+  EngineArgs args{};
+  int nstages = 0;
+  int items = 0;  // per iteration
+};
+}  // namespace
+}  // namespace adjwt
+
+struct adjwt_fista_batch {
+  int count = 0;
+  std::vector<adjwt_fista_problem> probs;
+  std::vector<size_t> ws_off;
+  void* dev = nullptr;            // tables, argument blocks, counters (owned)
+  adjwt::BatchLaunch run, obj;
+  const adjwt::L1Args* l1args = nullptr;
+  double* const* mom_ptrs = nullptr;
+  int* counters = nullptr;
+  size_t counter_bytes = 0;
+  size_t dyn = 0;
+  int per_sm = 1;
+  ~adjwt_fista_batch() {
+    if (dev) cudaFree(dev);
+  }
+};
+
+namespace adjwt {
+namespace {
+
+struct StageList {
+  std::vector<Stage> st;  // in stage order, prev = index within the same problem's list (-1: none)
+};
+
+// Stage-major order across problems; prev indices become global; the first
+// stage of a problem waits on its last one (previous iteration) when `wrap`.
+void order_stages(const std::vector<StageList>& per, bool wrap, std::vector<Stage>* out, std::vector<int>* item_stage,
+                  std::vector<int>* first, int* items) {
+  size_t smax = 0;
+  for (const auto& l : per) smax = std::max(smax, l.st.size());
+  std::vector<std::vector<int>> gidx(per.size());
+  for (size_t p = 0; p < per.size(); ++p) gidx[p].assign(per[p].st.size(), -1);
+  out->clear();
+  for (size_t s = 0; s < smax; ++s)
+    for (size_t p = 0; p < per.size(); ++p)
+      if (s < per[p].st.size()) {
+        gidx[p][s] = static_cast<int>(out->size());
+        out->push_back(per[p].st[s]);
+      }
+  for (size_t p = 0; p < per.size(); ++p) {
+    const size_t n = per[p].st.size();
+    for (size_t s = 0; s < n; ++s) {
+      Stage& S = (*out)[gidx[p][s]];
+      if (s > 0) {
+        S.prev = gidx[p][s - 1];
+        S.prev_lag = 0;
+      } else if (wrap) {
+        S.prev = gidx[p][n - 1];
+        S.prev_lag = 1;
+      } else {
+        S.prev = -1;
+        S.prev_lag = 0;
+      }
+      S.prev_tiles = S.prev >= 0 ? (*out)[S.prev].ntiles : 0;
+    }
+  }
+  item_stage->clear();
+  first->clear();
+  for (size_t i = 0; i < out->size(); ++i) {
+    first->push_back(static_cast<int>(item_stage->size()));
+    for (int t = 0; t < (*out)[i].ntiles; ++t) item_stage->push_back(static_cast<int>(i));
+  }
+  *items = static_cast<int>(item_stage->size());
+}
+
+Stage make_stage(int kind, int param, int problem, int args, int ntiles, int tiles_c, int part) {
+  Stage s{};
+  s.kind = kind;
+  s.param = param;
+  s.problem = problem;
+  s.args = args;
+  s.ntiles = ntiles;
+  s.tiles_c = tiles_c;
+  s.part = part;
+  s.prev = -1;
+  return s;
+}
+
+template <typename T>
+size_t put(std::vector<unsigned char>& blob, const std::vector<T>& v) {
+  const size_t off = static_cast<size_t>(round_up(static_cast<int64_t>(blob.size()), 256));
+  blob.resize(off + v.size() * sizeof(T) + 1);
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+size_t engine_smem(int rmax) {
+  size_t blur = 0;
+  switch (rmax) {
+    case 2: blur = blur_tile_smem<2>(); break;
+    case 4: blur = blur_tile_smem<4>(); break;
+    case 6: blur = blur_tile_smem<6>(); break;
+    case 9: blur = blur_tile_smem<9>(); break;
+    default: blur = blur_tile_smem<12>(); break;
+  }
+  return std::max({kProxOffset + kProxSlotBytes, sizeof(SynSmem<10>), blur});
+}
+
+}  // namespace
+}  // namespace adjwt
+
+using namespace adjwt;
+
+extern "C" size_t adjwt_fista_batch_workspace_size(int count, const adjwt_fista_problem* probs) {
+  if (count <= 0 || !probs) return 0;
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i].wt || !probs[i].blur) return 0;
+    total += prob_ws(probs[i]).bytes;
+  }
+  return total;
+}
+
+extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, const adjwt_fista_problem* probs,
+                                        float* const* x, float* const* y, void* ws, size_t ws_bytes) {
+  if (!out) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_create: out is NULL");
+  *out = nullptr;
+  if (count < 1 || count > 65535 || !probs || !x || !y)
+    return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_create: need 1 <= count <= 65535 and non-NULL arrays");
+  for (int i = 0; i < count; ++i) {
+    int rc = check_batch_problem(probs[i], i);
+    if (rc) return rc;
+    if (!x[i] || !y[i] || ((reinterpret_cast<uintptr_t>(x[i]) | reinterpret_cast<uintptr_t>(y[i])) & 15u))
+      return fail(ADJWT_ERR_ALIGN, "adjwt_fista_batch_create: x and y must be non-NULL and 16-byte aligned");
+  }
+  const size_t need = adjwt_fista_batch_workspace_size(count, probs);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need)
+    return fail(ADJWT_ERR_WORKSPACE, "adjwt_fista_batch_create: workspace of adjwt_fista_batch_workspace_size() "
+                                     "bytes, 256-byte aligned, needed (" + std::to_string(need) + ")");
+  auto* B = new adjwt_fista_batch();
+  B->count = count;
+  B->probs.assign(probs, probs + count);
+
+  std::vector<SynArgs> syn;
+  std::vector<AnaArgs> ana;
+  std::vector<TiledArgs> blr;
+  std::vector<L1Args> l1;
+  std::vector<ProbDev> pdev;
+  std::vector<double*> moms;
+  std::vector<StageList> run_lists(count), obj_lists(count);
+  char* base = static_cast<char*>(ws);
+  int rmax = 2;
+  for (int p = 0; p < count; ++p) {
+    const adjwt_fista_problem& pr = probs[p];
+    const adjwt_wt_plan* w = pr.wt;
+    const ProbWs pw = prob_ws(pr);
+    char* pb = base;
+    base += pw.bytes;
+    float* u = reinterpret_cast<float*>(pb + pw.u);
+    float* g = reinterpret_cast<float*>(pb + pw.g);
+    float* ll[2] = {reinterpret_cast<float*>(pb + pw.ll0), reinterpret_cast<float*>(pb + pw.ll1)};
+    double* mom = reinterpret_cast<double*>(pb + pw.mom);
+    double* parts = reinterpret_cast<double*>(pb + pw.parts);
+    pdev.push_back(ProbDev{mom, parts, pw.nblur, pw.nl1, pr.lambda});
+    moms.push_back(mom);
+    const int J = w->levels, Lf = w->fb.L, R = blur_radius(pr.blur);
+    rmax = std::max(rmax, R);
+    const int btc = (pr.blur->cols + kT - 1) / kT;
+    // iteration: MOM, W levels J..1 on y, R^*(R u - b), W^* + prox levels 1..J
+    auto& rl = run_lists[p].st;
+    rl.push_back(make_stage(kMom, 0, p, 0, 1, 1, -1));
+    for (int j = J; j >= 1; --j) {
+      const SynArgs a = syn_level(w, j, y[p], u, ll);
+      rl.push_back(make_stage(kSyn, Lf, p, static_cast<int>(syn.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
+      syn.push_back(a);
+    }
+    rl.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, -1));
+    blr.push_back(blur_args(pr, u, g, nullptr));
+    for (int j = 1; j <= J; ++j) {
+      const AnaArgs a = ana_level(pr, j, g, x[p], y[p], ll, mom + 1);
+      rl.push_back(make_stage(kAna, Lf, p, static_cast<int>(ana.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
+      ana.push_back(a);
+    }
+    // objective: W levels J..1 on x, 1/2 ||R u - b||^2 partials, |x| partials, the sum
+    auto& ol = obj_lists[p].st;
+    for (int j = J; j >= 1; --j) {
+      const SynArgs a = syn_level(w, j, x[p], u, ll);
+      ol.push_back(make_stage(kSyn, Lf, p, static_cast<int>(syn.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
+      syn.push_back(a);
+    }
+    ol.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, 0));
+    blr.push_back(blur_args(pr, u, nullptr, parts));
+    ol.push_back(make_stage(kL1, 0, p, static_cast<int>(l1.size()), pw.nl1, pw.nl1, pw.nblur));
+    l1.push_back(L1Args{x[p], w->num_coeffs});
+    ol.push_back(make_stage(kSum, 0, p, 0, 1, 1, -1));
+  }
+  std::vector<Stage> rst, ost;
+  std::vector<int> ritem, rfirst, oitem, ofirst;
+  int ritems = 0, oitems = 0;
+  order_stages(run_lists, true, &rst, &ritem, &rfirst, &ritems);
+  order_stages(obj_lists, false, &ost, &oitem, &ofirst, &oitems);
+
+  std::vector<unsigned char> blob;
+  const size_t o_rst = put(blob, rst), o_ritem = put(blob, ritem), o_rfirst = put(blob, rfirst);
+  const size_t o_ost = put(blob, ost), o_oitem = put(blob, oitem), o_ofirst = put(blob, ofirst);
+  const size_t o_syn = put(blob, syn), o_ana = put(blob, ana), o_blr = put(blob, blr), o_l1 = put(blob, l1);
+  const size_t o_prob = put(blob, pdev), o_mom = put(blob, moms);
+  const size_t nctr = kCtrDone + std::max(rst.size(), ost.size());
+  const size_t o_ctr = static_cast<size_t>(round_up(static_cast<int64_t>(blob.size()), 256));
+  B->counter_bytes = nctr * sizeof(int);
+  const size_t total = o_ctr + B->counter_bytes;
+  cudaError_t e = cudaMalloc(&B->dev, total);
+  if (e == cudaSuccess) e = cudaMemcpy(B->dev, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "adjwt_fista_batch_create");
+  }
+  char* d = static_cast<char*>(B->dev);
+  auto fill = [&](BatchLaunch& L, size_t ost_, size_t oitem_, size_t ofirst_, int nst, int items) {
+    L.nstages = nst;
+    L.items = items;
+    L.args.stages = reinterpret_cast<const Stage*>(d + ost_);
+    L.args.item_stage = reinterpret_cast<const int*>(d + oitem_);
+    L.args.stage_first = reinterpret_cast<const int*>(d + ofirst_);
+    L.args.items_per_iter = items;
+    L.args.syn = reinterpret_cast<const SynArgs*>(d + o_syn);
+    L.args.ana = reinterpret_cast<const AnaArgs*>(d + o_ana);
+    L.args.blur = reinterpret_cast<const TiledArgs*>(d + o_blr);
+    L.args.prob = reinterpret_cast<const ProbDev*>(d + o_prob);
+    L.args.counters = reinterpret_cast<int*>(d + o_ctr);
+    L.args.status = device_status_ptr();
+  };
+  fill(B->run, o_rst, o_ritem, o_rfirst, static_cast<int>(rst.size()), ritems);
+  fill(B->obj, o_ost, o_oitem, o_ofirst, static_cast<int>(ost.size()), oitems);
+  B->l1args = reinterpret_cast<const L1Args*>(d + o_l1);
+  B->mom_ptrs = reinterpret_cast<double* const*>(d + o_mom);
+  B->counters = reinterpret_cast<int*>(d + o_ctr);
+  B->dyn = engine_smem(rmax);
+  e = set_smem(k_fista_engine, B->dyn);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fista_engine, kEngineThreads, B->dyn);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "adjwt_fista_batch_create");
+  }
+  B->per_sm = std::max(per_sm, 1);
+  *out = B;
+  return ADJWT_OK;
+}
+
+extern "C" void adjwt_fista_batch_destroy(adjwt_fista_batch* b) { delete b; }
+
+extern "C" int adjwt_fista_batch_reset(const adjwt_fista_batch* b, adjwt_stream_t stream) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_reset: batch is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned nb = static_cast<unsigned>((b->count + 127) / 128);
+  ADJWT_TRACED("fista_batch_reset", 0, s, pdl_launch(k_batch_reset, nb, 128, 0, s, b->mom_ptrs, b->count));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+
+namespace {
+int engine_launch(const adjwt_fista_batch* b, const BatchLaunch& L, int iters, double* objectives, int stall,
+                  cudaStream_t s, const char* name) {
+  if ((int64_t)L.items * iters > 0x7fffffff)
+    return fail(ADJWT_ERR_SHAPE, std::string(name) + ": iterations x items above 2^31");
+  EngineArgs a = L.args;
+  a.iters = iters;
+  a.objectives = objectives;
+  a.stall = stall;
+  const int64_t total = (int64_t)L.items * iters;
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(total, (int64_t)b->per_sm * sm_count())));
+  cudaError_t me = cudaSuccess;
+  ADJWT_TRACED("fista_batch_reset_counters", 0, s, me = cudaMemsetAsync(b->counters, 0, b->counter_bytes, s));
+  ADJWT_CUDA_CHECK(me);
+  ADJWT_TRACED(name, 0, s, pdl_launch(k_fista_engine, dim3(grid), kEngineThreads, b->dyn, s, a, b->l1args));
+  ADJWT_CUDA_CHECK(cudaGetLastError());
+  return ADJWT_OK;
+}
+}  // namespace
+
+extern "C" int adjwt_fista_batch_run(const adjwt_fista_batch* b, int iters, adjwt_stream_t stream) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_run: batch is NULL");
+  if (iters < 0) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_run: iters < 0");
+  if (iters == 0) return ADJWT_OK;
+  return engine_launch(b, b->run, iters, nullptr, 0, static_cast<cudaStream_t>(stream), "fista_batch");
+}
+
+extern "C" int adjwt_fista_batch_objective(const adjwt_fista_batch* b, double* objectives_dev, adjwt_stream_t stream) {
+  if (!b || !objectives_dev) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_objective: NULL argument");
+  return engine_launch(b, b->obj, 1, objectives_dev, 0, static_cast<cudaStream_t>(stream), "fista_batch_objective");
+}
+
+extern "C" int adjwt_fista_batch_wait_selftest(const adjwt_fista_batch* b, adjwt_stream_t stream) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_wait_selftest: batch is NULL");
+  return engine_launch(b, b->run, 1, nullptr, 1, static_cast<cudaStream_t>(stream), "fista_batch_selftest");
+}
+
+extern "C" int adjwt_fista_batch_info(const adjwt_fista_batch* b, int* items_per_iteration, int* stages,
+                                      int* ctas) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_info: batch is NULL");
+  if (items_per_iteration) *items_per_iteration = b->run.items;
+  if (stages) *stages = b->run.nstages;
+  if (ctas) *ctas = b->per_sm * sm_count();
+  return ADJWT_OK;
+}

@@ -31,7 +31,7 @@ constexpr int kTH = 32;    // output rows per tile
 constexpr int kTW = 128;   // output columns per tile
 constexpr int kP = 8;      // output pairs per thread and pass
 constexpr int kNT = 288;   // 9 warps: column-pass items; 8 of them in the row pass
-constexpr int kSplitMin = 1536;  // levels shared with the tiled kernel: both sides at least this long
+constexpr int kSplitMin = 1536;  // W: levels shared with the tiled kernel; W^*: levels on the TMA kernel
 constexpr int kWrapCols = 16;  // PER: the box of a full tile overhangs the band end by at most
 constexpr int kWrapRows = 8;   // this many columns / rows (checked on the host)
 
@@ -429,64 +429,162 @@ struct AnaTmaArgs {
 };
 
 // Border tiles.  The box holds img[e - sh] for every window cell whose image
-// index lies inside the image and zero elsewhere; a cell is rewritten from
-// the image when the extension gives it another value (a mirror or wrap
-// copy, or zero outside the extended signal) or a weight 1/c (W^*'s weighted
-// extension (E^dagger)^*, Eq. 2): value = w_r w_c img[src_r][src_c].  Per
-// axis the source and weight of each window row / column go to shared
-// tables first.  Interior windows return at once (uniform per tile).
+// index lies inside the image and zero elsewhere.  What the extension needs
+// beyond that:
+//   * off-image cells under the symmetric / periodic extensions hold a mirror
+//     or wrap copy (zero outside the extended signal).  A half-point mirror
+//     of a border window lies inside the same window (for levels of the TMA
+//     size), so those cells are copied within shared memory; wrap copies
+//     (and mirrors outside the window) are fetched from the image into
+//     registers while the copy is in flight;
+//   * every cell then takes the weights 1/c of its source row and column
+//     (W^*'s weighted extension (E^dagger)^*, Eq. 2), from per-row and
+//     per-column tables built before the copy has landed.
+// Off-image cells are enumerated as strips (rows above / below the image at
+// full width, then the columns beside it on the other rows).
+struct AnaBorder {
+  int e0r, e0c;             // extended coordinates of window row / column 0
+  int rlo, rhi, clo, chi;   // in-image window rows [rlo, rhi), columns [clo, chi)
+  int side, ntop, nbot, total;
+  bool any;                 // anything to do for this tile (uniform)
+  bool weighted;            // some weight differs from 1
+};
+
+// Per window row (first ER entries) and column (next EC): the source image
+// index (-1: zero), the window index of the source when the window holds it
+// (-1: not held), and the weight 1/c of the source (1 without weights).
 template <int L>
-__device__ __forceinline__ void fix_window(const AnaTmaArgs& a, float* S, int k0, int l0, int* tsrc, float* tw,
-                                           unsigned char* tsp) {
+struct BorderTables {
+  int img[AG<L>::ER + AG<L>::EC];
+  int win[AG<L>::ER + AG<L>::EC];
+  float w[AG<L>::ER + AG<L>::EC];
+};
+
+template <int L>
+__device__ __forceinline__ AnaBorder ana_border(const AnaTmaArgs& a, int k0, int l0) {
   using G = AG<L>;
   constexpr int Lp = L - 1;
-  const int e0r = 2 * k0 + 1 - Lp, e0c = 2 * l0 + 1 - Lp;  // extended coordinates of window row / column 0
-  auto plain = [&](int e0, int E, int N, const float* winv) {
-    const int lo = e0 - a.sh, g = winv ? Lp : 0;
-    return lo >= g && lo + E - 1 < N - g;
-  };
-  if (plain(e0r, G::ER, a.Nr, a.winv_r) && plain(e0c, G::EC, a.Nc, a.winv_c)) return;
+  AnaBorder b;
+  b.e0r = 2 * k0 + 1 - Lp;
+  b.e0c = 2 * l0 + 1 - Lp;
+  const int xr = b.e0r - a.sh, xc = b.e0c - a.sh;  // image index of window row / column 0
+  b.rlo = min(max(-xr, 0), G::ER);
+  b.rhi = min(max(a.Nr - xr, b.rlo), G::ER);
+  b.clo = min(max(-xc, 0), G::EC);
+  b.chi = min(max(a.Nc - xc, b.clo), G::EC);
+  b.side = b.clo + (G::EC - b.chi);
+  b.ntop = b.rlo * G::EC;
+  b.nbot = (G::ER - b.rhi) * G::EC;
+  b.total = a.fix ? b.ntop + b.nbot + (b.rhi - b.rlo) * b.side : 0;
+  const bool wr = a.winv_r && (xr < Lp || xr + G::ER > a.Nr - Lp);
+  const bool wc = a.winv_c && (xc < Lp || xc + G::EC > a.Nc - Lp);
+  b.weighted = wr || wc;
+  b.any = b.total > 0 || b.weighted;
+  return b;
+}
+
+// window cell (row * EC + col) of off-image cell i < total
+template <int L>
+__device__ __forceinline__ int border_cell(const AnaBorder& b, int i) {
+  using G = AG<L>;
+  if (i < b.ntop) return i;
+  if (i < b.ntop + b.nbot) return b.rhi * G::EC + (i - b.ntop);
+  const int j = i - b.ntop - b.nbot, rr = j / b.side, k = j - rr * b.side;
+  return (b.rlo + rr) * G::EC + (k < b.clo ? k : b.chi + (k - b.clo));
+}
+
+// source image index of extended coordinate e (-1: zero)
+template <int L>
+__device__ __forceinline__ int ana_src(const AnaTmaArgs& a, int e, int N) {
+  constexpr int Lp = L - 1;
+  if (a.mode == kPer) return pos_mod(e, N);
+  return (e >= 0 && e < N + 2 * Lp) ? ext_src(e - Lp, N, a.mode) : -1;
+}
+
+template <int L>
+__device__ __forceinline__ void border_tables(const AnaTmaArgs& a, const AnaBorder& b, BorderTables<L>& t) {
+  using G = AG<L>;
   for (int i = threadIdx.x; i < G::ER + G::EC; i += kNT) {
     const bool row = i < G::ER;
     const int u = row ? i : i - G::ER;
-    const int e = (row ? e0r : e0c) + u, N = row ? a.Nr : a.Nc;
+    const int N = row ? a.Nr : a.Nc, E = row ? G::ER : G::EC;
+    const int x0 = (row ? b.e0r : b.e0c) - a.sh;
+    const int src = ana_src<L>(a, x0 + u + a.sh, N);
     const float* winv = row ? a.winv_r : a.winv_c;
-    const int x = e - a.sh;  // the image index the box read (zero outside the image)
-    int src;
-    if (a.mode == kPer) {
-      src = pos_mod(e, N);
-    } else {
-      src = (e >= 0 && e < N + 2 * Lp) ? ext_src(e - Lp, N, a.mode) : -1;
-    }
-    const float w = (src >= 0 && winv) ? __ldg(winv + src) : 1.0f;
-    const bool boxed = x >= 0 && x < N;
-    tsrc[i] = src;
-    tw[i] = w;
-    tsp[i] = ((src >= 0) ? (!boxed || src != x) : boxed) || w != 1.0f;
+    const int wi = src >= 0 ? src - x0 : -1;
+    t.img[i] = src;
+    t.win[i] = (wi >= 0 && wi < E) ? wi : -1;
+    t.w[i] = (src >= 0 && winv) ? __ldg(winv + src) : 1.0f;
   }
-  __syncthreads();
-  constexpr int total = G::ER * G::EC, U = 8;  // eight loads in flight per thread
-  for (int base = threadIdx.x; base < total; base += U * kNT) {
-    float v[U];
+}
+
+constexpr int kFixRegs = 10;  // far off-image cells per thread fetched before the copy has landed
+
+// far source of an off-image cell (not held by the window): straight from the image, unweighted
+template <int L>
+__device__ __forceinline__ float border_far(const AnaTmaArgs& a, const AnaBorder& b, int cell) {
+  using G = AG<L>;
+  const int r = cell / G::EC, c = cell - r * G::EC;
+  const int sr = ana_src<L>(a, b.e0r + r, a.Nr), sc = ana_src<L>(a, b.e0c + c, a.Nc);
+  return (sr >= 0 && sc >= 0) ? __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+}
+
+// Before the copy has landed: the tables, and (periodic extensions) the far
+// off-image cells into registers.
+template <int L>
+__device__ __forceinline__ void border_prefetch(const AnaTmaArgs& a, const AnaBorder& b, BorderTables<L>& t,
+                                                float (&fv)[kFixRegs]) {
+  border_tables<L>(a, b, t);
+  if (a.mode != kSym) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kNT;
-      v[u] = 0.0f;
-      if (i < total) {
-        const int r = i / G::EC, c = i - r * G::EC;
-        if (tsp[r] || tsp[G::ER + c]) {
-          const int sr = tsrc[r], sc = tsrc[G::ER + c];
-          if (sr >= 0 && sc >= 0) v[u] = tw[r] * tw[G::ER + c] * __ldg(a.in + (size_t)sr * a.in_pitch + sc);
-        }
+    for (int u = 0; u < kFixRegs; ++u) {
+      const int i = threadIdx.x + u * kNT;
+      fv[u] = i < b.total ? border_far<L>(a, b, border_cell<L>(b, i)) : 0.0f;
+    }
+  }
+}
+
+// After the copy (and a block barrier, so the tables are visible): the
+// off-image cells, then the weights.  Ends with a block barrier.
+template <int L>
+__device__ __forceinline__ void border_apply(const AnaTmaArgs& a, const AnaBorder& b, const BorderTables<L>& t,
+                                             const float (&fv)[kFixRegs], float* S) {
+  using G = AG<L>;
+  if (a.mode == kSym) {
+    // mirror copies from in-image cells of the same window (never off-image
+    // themselves, so the copies can run in any order)
+    for (int i = threadIdx.x; i < b.total; i += kNT) {
+      const int cell = border_cell<L>(b, i), r = cell / G::EC, c = cell - r * G::EC;
+      const int wr = t.win[r], wc = t.win[G::ER + c];
+      float v;
+      if (wr >= 0 && wc >= 0) {
+        v = S[wr * G::BC + wc];
+      } else {
+        const int sr = t.img[r], sc = t.img[G::ER + c];
+        v = (sr >= 0 && sc >= 0) ? __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+      }
+      S[r * G::BC + c] = v;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < kFixRegs; ++u) {
+      const int i = threadIdx.x + u * kNT;
+      if (i < b.total) {
+        const int c = border_cell<L>(b, i), r = c / G::EC;
+        S[r * G::BC + (c - r * G::EC)] = fv[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kNT;
-      if (i < total) {
-        const int r = i / G::EC, c = i - r * G::EC;
-        if (tsp[r] || tsp[G::ER + c]) S[r * G::BC + c] = v[u];
-      }
+    for (int i = threadIdx.x + kFixRegs * kNT; i < b.total; i += kNT) {  // larger overhangs
+      const int c = border_cell<L>(b, i), r = c / G::EC;
+      S[r * G::BC + (c - r * G::EC)] = border_far<L>(a, b, c);
+    }
+  }
+  if (b.weighted) {
+    __syncthreads();  // every cell holds its unweighted source value
+    for (int i = threadIdx.x; i < G::ER * G::EC; i += kNT) {
+      const int r = i / G::EC, c = i - r * G::EC;
+      const float w = t.w[r] * t.w[G::ER + c];
+      if (w != 1.0f) S[r * G::BC + c] *= w;
     }
   }
   fence_proxy_async();  // these generic writes come before the TMA unit's next write into the buffer
@@ -502,9 +600,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
   __shared__ double red[kNT / 32];
-  __shared__ int t_src[G::ER + G::EC];       // border tiles: per window row / column, source index,
-  __shared__ float t_w[G::ER + G::EC];       // weight and whether the box value must be rewritten
-  __shared__ unsigned char t_sp[G::ER + G::EC];
+  __shared__ BorderTables<L> tabs;  // border tiles
   float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
   float* V = buf0 + 2 * G::BUF;  // [2][kAR][VP]
   const int tid = threadIdx.x;
@@ -576,6 +672,10 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
     const bool rvalid = k0 + kk < a.nr;     // the last row tile may be partial
     const int lbase = l0 + kAP * warp;      // and the last column tile
     const size_t row = rvalid ? (size_t)(k0 + kk) * a.out_pitch + lbase : 0;
+    // border tile: tables (and far off-image cells) fetched while the copy is in flight
+    const AnaBorder bd = ana_border<L>(a, k0, l0);
+    float fv[kFixRegs];
+    if (bd.any) border_prefetch<L>(a, bd, tabs, fv);
     // this tile's prox state from the slot, then the next tile's requested
     float yv[2][kAP], xv[2][kAP];
     if (PROX && rower) {
@@ -605,7 +705,7 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
       if (PROX) cp_async_wait_all();
       return;
     }
-    if (a.fix) fix_window<L>(a, buf0 + b * G::BUF + a.d_c, k0, l0, t_src, t_w, t_sp);
+    if (bd.any) border_apply<L>(a, bd, tabs, fv, buf0 + b * G::BUF + a.d_c);
     const float* S = buf0 + b * G::BUF + a.d_c;
     // column pass: V[f][kk][ec] = sum_t f[t] T[2 kk + L' - t][ec]
     for (int item = tid; item < 2 * G::EC; item += kNT) {
@@ -745,11 +845,12 @@ int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, co
 
 // Whether level j of the analysis direction runs on the persistent TMA
 // kernel (every tile of the level, border tiles included) rather than the
-// tiled kernel: levels of at least 256 x 512 unless switched off.
+// tiled kernel: levels of at least 1536 x 1536 unless switched off.
 bool ana_tma_level(const adjwt_wt_plan* p, int j, bool prox) {
   if (p->tma_off[prox ? 2 : 1][j - 1]) return false;
   const Level& L = p->lv[j - 1];
-  return L.ax[0].N >= 256 && L.ax[1].N >= 512;
+  // measured on GB300: below about 1536 x 1536 the tiled kernel is as fast or faster
+  return L.ax[0].N >= kSplitMin && L.ax[1].N >= kSplitMin;
 }
 
 int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in, int in_pitch, float* const dst[4],

@@ -1,0 +1,147 @@
+"""The batched FISTA engine: many problems of uneven sizes, depths, wavelets,
+boundaries and PSF widths advanced in one persistent launch, checked against
+the float64 oracle's FISTA (Eq. 1, the method cited in Sec. I-B) iteration by
+iteration, and its bounded waits run out without faulting."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import blur as oblur
+from oracle import fista as ofista
+from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
+from tests.gpu_util import image_dev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+ADJWT_ERR_TIMEOUT = -8
+
+# (rows, cols, levels, wavelet, wavelet boundary, PSF taps, sigma, blur boundary, gradient)
+MIX = [
+    (96, 96, 2, "db2", "sym", 5, 0.9, "sym", "adjoint"),
+    (128, 112, 3, "db4", "zero", 9, 1.5, "zero", "adjoint"),
+    (160, 160, 3, "cdf97", "sym", 15, 2.5, "sym", "adjoint"),
+    (64, 64, 2, "haar", "per", 3, 0.8, "per", "adjoint"),
+    (200, 136, 2, "cdf97", "zero", 11, 1.8, "sym", "pinv"),
+    (128, 128, 4, "db2", "per", 7, 1.2, "per", "adjoint"),
+    (90, 150, 3, "db4", "sym", 13, 2.0, "zero", "adjoint"),
+    (120, 120, 3, "cdf97", "sym", 19, 3.0, "sym", "adjoint"),
+]
+LAM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def adj():
+    import paper_1707_02018_gb300 as adj
+    adj.lib()
+    return adj
+
+
+def _problems(adj):
+    out = []
+    for i, (rows, cols, J, w, mode, k, sigma, bbc, grad) in enumerate(MIX):
+        p = oblur.gaussian_psf(k, sigma)
+        img = piecewise_smooth_image(rows, cols, 900 + i)
+        b = oblur.blur(img, p, p, bbc) + gaussian_noise((rows, cols), 950 + i)
+        prob = ofista.Problem(rows, cols, J, w, mode, p, p, bbc, b, LAM, gradient=grad)
+        wt = adj.WtPlan(rows, cols, J, w, mode)
+        bl = adj.BlurPlan(rows, cols, p, p, bbc)
+        db = image_dev(wt, b)
+        f = adj.Fista(wt, bl, db, LAM, 1.0, gradient=grad)
+        L = 1.05 * f.lipschitz(wt.pack(random_vector(wt.logical_size, 970 + i)), iters=30)
+        f.set_lipschitz(L)
+        out.append({"oracle": prob, "fista": f, "wt": wt, "bl": bl, "b": db, "L": L})
+    return out
+
+
+def test_batch_iterates_and_objectives_match_the_oracle(adj):
+    """8 mixed problems, 6 iterations in one launch, then 4 more in a second:
+    every iterate within 1e-4 (relative L2) of the float64 oracle after each
+    launch, and the batched objective F(x_k) within 1e-5."""
+    probs = _problems(adj)
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    info = batch.info()
+    assert info["stages"] == sum(2 * m[2] + 2 for m in MIX)
+    batch.reset()
+    xs = [np.zeros(p["wt"].logical_size) for p in probs]
+    ys = [x.copy() for x in xs]
+    ts = [1.0] * len(probs)
+    done = 0
+    for iters in (6, 4):
+        batch.run(iters)
+        for i, p in enumerate(probs):
+            for _ in range(iters):
+                xs[i], ys[i], ts[i] = ofista.fista_step(p["oracle"], xs[i], ys[i], ts[i], p["L"])
+        done += iters
+        F = batch.objective().cpu().numpy()
+        torch.cuda.synchronize()
+        for i, p in enumerate(probs):
+            xg = p["wt"].unpack(p["fista"].x).cpu().numpy()
+            assert rel_err(xg, xs[i]) <= 1e-4, (i, done, rel_err(xg, xs[i]))
+            Fo = p["oracle"].objective(xs[i])
+            assert abs(F[i] - Fo) <= 1e-5 * Fo, (i, done, F[i], Fo)
+    assert adj.device_status() == 0
+
+
+def test_batch_matches_one_problem_at_a_time(adj):
+    """The engine and fista_step (one problem at a time, other kernels) give
+    the same iterates within float32 tolerance after 10 iterations."""
+    probs = _problems(adj)
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    batch.reset()
+    batch.run(10)
+    torch.cuda.synchronize()
+    got = [p["fista"].x.clone() for p in probs]
+    for i, p in enumerate(probs):
+        f = p["fista"]
+        f.reset()
+        for _ in range(10):
+            f.step()
+        torch.cuda.synchronize()
+        r = float((got[i] - f.x).norm() / f.x.norm())
+        assert r <= 1e-5, (i, r)
+
+
+def test_batch_wait_runs_out_and_the_launch_drains(adj):
+    """A host-side setup in which the first stage waits for one that never
+    runs: the bounded wait gives up after about a second, records
+    ADJWT_ERR_TIMEOUT, every other CTA stops, and the context still computes
+    (the next launch gives the oracle's iterates)."""
+    probs = _problems(adj)[:3]
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    batch.reset()
+    adj.device_status(clear=True)
+    t0 = time.perf_counter()
+    batch.wait_selftest()
+    status = adj.device_status(clear=True)   # synchronises
+    elapsed = time.perf_counter() - t0
+    assert status == ADJWT_ERR_TIMEOUT
+    assert 0.1 < elapsed < 60.0, elapsed
+    assert adj.device_status() == 0
+    batch.reset()
+    batch.run(3)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        x, y, t = np.zeros(p["wt"].logical_size), np.zeros(p["wt"].logical_size), 1.0
+        for _ in range(3):
+            x, y, t = ofista.fista_step(p["oracle"], x, y, t, p["L"])
+        assert rel_err(p["wt"].unpack(p["fista"].x).cpu().numpy(), x) <= 1e-4
+    assert adj.device_status() == 0
+
+
+def test_batch_rejects_what_it_cannot_run(adj):
+    p = oblur.gaussian_psf(5, 1.0)
+    wt = adj.WtPlan(64, 64, 2, "db2", "ppd")
+    bl = adj.BlurPlan(64, 64, p, p, "sym")
+    f = adj.Fista(wt, bl, image_dev(wt, np.zeros((64, 64))), LAM, 1.0)
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.FistaBatch([f])
+    assert e.value.code == -2                 # SHAPE: redundant periodic reconstruction
+    wide = oblur.gaussian_psf(27, 4.0)        # radius 13
+    wt = adj.WtPlan(64, 64, 2, "db2", "sym")
+    bl = adj.BlurPlan(64, 64, wide, wide, "sym")
+    f = adj.Fista(wt, bl, image_dev(wt, np.zeros((64, 64))), LAM, 1.0)
+    with pytest.raises(adj.AdjwtError) as e:
+        adj.FistaBatch([f])
+    assert e.value.code == -2
