@@ -615,6 +615,129 @@ def batch_problems(adj, torch, seed=7000):
     return out
 
 
+# The batching workload at its stated size: 512 problems, 150 iterations each.
+CFG4_PROBLEMS, CFG4_ITERS = 512, 150
+
+
+def cfg4_problems(adj, torch, count, seed=8000):
+    """Seeded problems of the batching workload: square sizes U{128 ... 1024},
+    levels U{3..6}, db2 / db4 / CDF 9/7, Gaussian PSF sigma U[0.8, 3] with
+    2 ceil(3 sigma) + 1 taps, symmetric boundaries, lambda = 1e-3.  The step
+    1/L_f uses L_f = 1.01 ||W||^2 >= ||R W||^2 (||R|| <= 1 for a normalised
+    nonnegative PSF under symmetric boundaries), ||W||^2 by a 20-step power
+    iteration on W^* W per (size, levels, wavelet)."""
+    from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
+    rng = np.random.default_rng(seed)
+    norms, out = {}, []
+    for i in range(count):
+        n = int(rng.choice(BATCH_SIZES))
+        J = int(rng.integers(3, 7))
+        w = str(rng.choice(BATCH_WAVELETS))
+        sigma = float(rng.uniform(0.8, 3.0))
+        k = 2 * int(np.ceil(3 * sigma)) + 1
+        p = gaussian_taps(k, sigma)
+        wt = adj.WtPlan(n, n, J, w, "sym")
+        bl = adj.BlurPlan(n, n, p, p, "sym")
+        key = (n, J, w)
+        if key not in norms:
+            v = wt.pack(random_vector(wt.logical_size, seed + 1))
+            for _ in range(20):
+                v = adj.wt_synth_adjoint(wt, adj.wt_synth(wt, v))
+                nv = float(v.double().norm())
+                v = v / nv
+            norms[key] = nv
+        img = wt.image(torch.as_tensor(piecewise_smooth_image(n, n, seed + 10 * i)))
+        b = adj.blur(bl, img)
+        b[:, :n] += torch.as_tensor(gaussian_noise((n, n), seed + 10 * i + 1, NOISE), dtype=torch.float32,
+                                    device="cuda")
+        f = adj.Fista(wt, bl, b, LAM, 1.01 * norms[key])
+        out.append({"n": n, "J": J, "wavelet": w, "sigma": sigma, "fista": f})
+    return out
+
+
+def batch_engine_cfg4(adj, torch, count=CFG4_PROBLEMS, iters=CFG4_ITERS, check_every=10):
+    """The batching workload as stated: `count` problems, `iters` FISTA
+    iterations each, timed three ways on the same problems (CUDA events):
+      * engine: the batched engine, ONE persistent launch for all iterations
+        of all problems;
+      * graph: the problems on their own streams, `check_every` device-momentum
+        iterations of every problem captured in one CUDA graph and replayed;
+      * plain: one problem after another, host-driven fista_step.
+    Afterwards F(x_150) of every problem from the engine's objective launch is
+    compared with the plain run's."""
+    probs = cfg4_problems(adj, torch, count)
+    fs = [p["fista"] for p in probs]
+    t0 = time.perf_counter()
+    batch = adj.FistaBatch(fs)
+    create_s = time.perf_counter() - t0
+    info = batch.info()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # engine
+    batch.reset()
+    batch.run(2)  # warm-up
+    batch.reset()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    batch.run(iters)
+    e1.record()
+    torch.cuda.synchronize()
+    engine_ms = e0.elapsed_time(e1)
+    F_engine = batch.objective().cpu().numpy().copy()
+    status = adj.device_status()
+    # graph of streams
+    streams = [torch.cuda.Stream() for _ in fs]
+    for f, st in zip(fs, streams):
+        f.reset_device(stream=st)
+        f.step_device(stream=st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=torch.cuda.Stream()):
+        main = torch.cuda.current_stream()
+        for st in streams:
+            st.wait_stream(main)
+        for f, st in zip(fs, streams):
+            for _ in range(check_every):
+                f.step_device(stream=st)
+        for st in streams:
+            main.wait_stream(st)
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
+    for f, st in zip(fs, streams):
+        f.reset_device(stream=st)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(iters // check_every):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    del graph
+    # plain
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f in fs:
+        f.reset()
+        for _ in range(iters):
+            f.step()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    F_plain = np.array([f.objective() for f in fs])
+    rel = np.abs(F_engine - F_plain) / F_plain
+    px = sum(p["n"] * p["n"] for p in probs)
+    return {"problems": count, "iterations": iters, "pixels": px,
+            "sizes": {str(s): sum(1 for p in probs if p["n"] == s) for s in BATCH_SIZES},
+            "engine_sec": engine_ms / 1e3, "graph_sec": graph_ms / 1e3, "plain_sec": plain_s,
+            "engine_vs_plain": plain_s / (engine_ms / 1e3), "engine_vs_graph": graph_ms / engine_ms,
+            "engine_launches": 1, "engine_items_per_iteration": info["items_per_iteration"],
+            "engine_stages": info["stages"], "engine_ctas": info["ctas"], "engine_create_sec": create_s,
+            "graph_capture_sec": capture_s,
+            "F_engine_vs_plain_max_rel": float(rel.max()), "device_status": status,
+            "mix": "sizes U{128..1024}, levels U{3..6}, db2/db4/cdf97, sigma U[0.8,3], SYM, lambda 1e-3"}
+
+
 def batched_vs_plain(adj, torch, tol=1e-4, check_every=10, ref_iters=5000, max_iters=5000):
     """Wall seconds until every problem of the batch has (F(x_k) - F*)/F* <= tol:
     plain = one problem after another, host-driven fista_step with an objective
@@ -875,6 +998,7 @@ def ours(args):
     if rank == 0 and not args.no_solve:
         extra["fista_sec_to_1e-4"] = fista_time_to_tol(adj, torch, probs[1])
         extra["fista_batched_vs_plain_to_1e-4"] = batched_vs_plain(adj, torch)
+        extra["fista_batch_engine_512x150"] = batch_engine_cfg4(adj, torch)
         extra["fista_adjoint_vs_pinv"] = adjoint_vs_pinv(adj, torch, probs[1])
         extra["unrolled_fista_gradient"] = unrolled_gradient_timing(adj, torch)
         extra["learned_warm_start"] = learned_warm_start(adj, torch)

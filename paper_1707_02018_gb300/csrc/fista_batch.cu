@@ -44,7 +44,8 @@ namespace {
 constexpr int kEngineThreads = 256;
 constexpr int kEngineMaxRadius = 12;
 
-enum StageKind : int { kMom = 0, kSyn = 1, kBlur = 2, kAna = 3, kSum = 4, kL1 = 5 };
+enum StageKind : int { kMom = 0, kSyn = 1, kBlur = 2, kAna = 3, kSum = 4, kL1 = 5, kGat = 6 };
+constexpr int kGatherPixels = kEngineThreads;  // pixels per item of a per-pixel gather level
 
 // One stage of one problem's iteration.
 struct Stage {
@@ -155,6 +156,11 @@ __device__ __noinline__ void engine_syn(const SynArgs& a, int ty, int tx, unsign
 }
 
 template <int L>
+__device__ __noinline__ void engine_gat(const SynArgs& a, int tr, int tc) {
+  synthesis_gather_pixel<L, true>(a, tr, tc);
+}
+
+template <int L>
 __device__ __noinline__ float engine_ana(const AnaArgs& a, int ty, int tx, unsigned char* dyn) {
   float l1 = 0.0f;
   analysis_tile<L, true, kEngineThreads>(a, ty, tx, l1, *reinterpret_cast<AnaSmem<L>*>(dyn),
@@ -227,6 +233,17 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         __syncthreads();
         with_L(S.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
         break;
+      case kGat: {
+        copy_block_args(&s_args.syn, &e.syn[S.args]);
+        __syncthreads();
+        const int64_t idx = (int64_t)tile * kGatherPixels + tid;
+        if (idx < (int64_t)s_args.syn.Nr * s_args.syn.Nc) {
+          const int tr = static_cast<int>(idx / s_args.syn.Nc);
+          const int tc = static_cast<int>(idx - (int64_t)tr * s_args.syn.Nc);
+          with_L(S.param, [&](auto Lc) { engine_gat<decltype(Lc)::value>(s_args.syn, tr, tc); });
+        }
+        break;
+      }
       case kAna: {
         copy_block_args(&s_args.ana, &e.ana[S.args]);
         __syncthreads();
@@ -335,8 +352,6 @@ int check_batch_problem(const adjwt_fista_problem& pr, int i) {
   if (pr.wt->rows != pr.blur->rows || pr.wt->cols != pr.blur->cols)
     return fail(ADJWT_ERR_SHAPE, who + ": wavelet and blur plans describe different images");
   if (pr.wt->bc == kPpd) return fail(ADJWT_ERR_SHAPE, who + ": the redundant periodic reconstruction is not batched");
-  for (const Level& L : pr.wt->lv)
-    if (L.generic_synth) return fail(ADJWT_ERR_SHAPE, who + ": a level of at most 2L' samples is not batched");
   if (std::max(pr.blur->kr, pr.blur->kc) / 2 > kEngineMaxRadius)
     return fail(ADJWT_ERR_SHAPE, who + ": PSF radius above 12");
   if (!(pr.lambda >= 0.0) || !std::isfinite(pr.lambda)) return fail(ADJWT_ERR_INVALID_ARG, who + ": bad lambda");
@@ -523,6 +538,16 @@ Stage make_stage(int kind, int param, int problem, int args, int ntiles, int til
   return s;
 }
 
+// a reconstruction level: 32 x 32 tiles, or 256-pixel items of the per-pixel
+// gather for levels the tiles cannot fold (see the plan's generic_synth)
+Stage syn_stage(const adjwt_wt_plan* w, int j, const SynArgs& a, int Lf, int p, int args) {
+  if (w->lv[j - 1].generic_synth) {
+    const int n = static_cast<int>(((int64_t)a.Nr * a.Nc + kGatherPixels - 1) / kGatherPixels);
+    return make_stage(kGat, Lf, p, args, n, n, -1);
+  }
+  return make_stage(kSyn, Lf, p, args, a.tiles_c * a.tiles_r, a.tiles_c, -1);
+}
+
 template <typename T>
 size_t put(std::vector<unsigned char>& blob, const std::vector<T>& v) {
   const size_t off = static_cast<size_t>(round_up(static_cast<int64_t>(blob.size()), 256));
@@ -608,7 +633,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     rl.push_back(make_stage(kMom, 0, p, 0, 1, 1, -1));
     for (int j = J; j >= 1; --j) {
       const SynArgs a = syn_level(w, j, y[p], u, ll);
-      rl.push_back(make_stage(kSyn, Lf, p, static_cast<int>(syn.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
+      rl.push_back(syn_stage(w, j, a, Lf, p, static_cast<int>(syn.size())));
       syn.push_back(a);
     }
     rl.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, -1));
@@ -622,7 +647,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     auto& ol = obj_lists[p].st;
     for (int j = J; j >= 1; --j) {
       const SynArgs a = syn_level(w, j, x[p], u, ll);
-      ol.push_back(make_stage(kSyn, Lf, p, static_cast<int>(syn.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
+      ol.push_back(syn_stage(w, j, a, Lf, p, static_cast<int>(syn.size())));
       syn.push_back(a);
     }
     ol.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, 0));

@@ -80,51 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_synthesis_gather(const SynArgs a, 
       tc = cc < Lp ? cc : a.Nc - 2 * Lp + cc;
     }
   }
-  // copies of t in [-L', N + L'): translation class (and mirror class for SYM)
-  const int N[2] = {a.Nr, a.Nc};
-  const int t[2] = {tr, tc};
-  int xs[2][2 * kMaxTaps];
-  int nx[2] = {0, 0};
-#pragma unroll
-  for (int ax = 0; ax < 2; ++ax) {
-    const int P = a.mode == 1 ? 2 * N[ax] : (a.mode == 0 ? 0 : N[ax]);
-    if (P == 0) {
-      xs[ax][nx[ax]++] = t[ax];
-      continue;
-    }
-    const int starts[2] = {t[ax], -1 - t[ax]};
-    const int nclass = a.mode == 1 ? 2 : 1;
-    for (int c = 0; c < nclass; ++c) {
-      int x = starts[c] - P * floor_div(starts[c] + Lp, P);
-      for (; x < N[ax] + Lp && nx[ax] < 2 * kMaxTaps; x += P) xs[ax][nx[ax]++] = x;
-    }
-  }
-  float acc = 0.0f;
-  for (int ir = 0; ir < nx[0]; ++ir) {
-    const int xr = xs[0][ir];
-    for (int ic = 0; ic < nx[1]; ++ic) {
-      const int xc = xs[1][ic];
-      for (int qr = 0; qr < L / 2; ++qr) {
-        const int mr = ((xr + 1) & 1) + 2 * qr;
-        const int k = (xr + 2 * Lp - 1 - mr) >> 1;
-        if (k < 0 || k >= a.nr) continue;
-        for (int qc = 0; qc < L / 2; ++qc) {
-          const int mc = ((xc + 1) & 1) + 2 * qc;
-          const int l = (xc + 2 * Lp - 1 - mc) >> 1;
-          if (l < 0 || l >= a.nc) continue;
-          const size_t o = (size_t)k * a.band_pitch + l;
-#pragma unroll
-          for (int va = 0; va < 2; ++va)
-#pragma unroll
-            for (int hb = 0; hb < 2; ++hb)
-              acc = fmaf(__ldg(a.band[va + 2 * hb] + o), a.g[va][mr] * a.g[hb][mc], acc);
-        }
-      }
-    }
-  }
-  if (a.winv_r) acc *= __ldg(a.winv_r + tr);
-  if (a.winv_c) acc *= __ldg(a.winv_c + tc);
-  a.out[(size_t)tr * a.out_pitch + tc] = acc;
+  synthesis_gather_pixel<L, false>(a, tr, tc);
 }
 
 // ---------------------------------------------------------------- level chain
