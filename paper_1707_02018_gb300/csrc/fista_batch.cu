@@ -185,15 +185,19 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
   const int tid = threadIdx.x;
   int* abort_flag = e.counters + 1;
   const int total = e.items_per_iter * e.iters;
+  // thread 0 holds the next ticket while the current item runs (taken one
+  // ahead: the smallest unfinished ticket is always some CTA's current item,
+  // whose dependencies all have smaller tickets, so the launch still makes
+  // progress)
+  int next = tid == 0 ? atomicAdd(&e.counters[0], 1) : 0;
+  int cur_st = -1;  // stage whose argument block is in s_args
   for (;;) {
     if (tid == 0) {
-      int item = -1, st = 0;
+      int item = next, st = 0;
       int ab;
       asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
-      if (!ab) {
-        item = atomicAdd(&e.counters[0], 1);
-        if (item >= total) item = -1;
-      }
+      if (ab || item >= total) item = -1;
+      if (item >= 0) next = atomicAdd(&e.counters[0], 1);
       if (item >= 0) {
         const int it = item / e.items_per_iter;
         st = e.item_stage[item - it * e.items_per_iter];
@@ -229,13 +233,17 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         }
         break;
       case kSyn:
-        copy_block_args(&s_args.syn, &e.syn[S.args]);
-        __syncthreads();
+        if (st != cur_st) {
+          copy_block_args(&s_args.syn, &e.syn[S.args]);
+          __syncthreads();
+        }
         with_L(S.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
         break;
       case kGat: {
-        copy_block_args(&s_args.syn, &e.syn[S.args]);
-        __syncthreads();
+        if (st != cur_st) {
+          copy_block_args(&s_args.syn, &e.syn[S.args]);
+          __syncthreads();
+        }
         const int64_t idx = (int64_t)tile * kGatherPixels + tid;
         if (idx < (int64_t)s_args.syn.Nr * s_args.syn.Nc) {
           const int tr = static_cast<int>(idx / s_args.syn.Nc);
@@ -245,8 +253,10 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         break;
       }
       case kAna: {
-        copy_block_args(&s_args.ana, &e.ana[S.args]);
-        __syncthreads();
+        if (st != cur_st) {
+          copy_block_args(&s_args.ana, &e.ana[S.args]);
+          __syncthreads();
+        }
         float l1 = 0.0f;
         with_L(S.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
         if (S.part >= 0) {
@@ -256,8 +266,10 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         break;
       }
       case kBlur: {
-        copy_block_args(&s_args.blur, &e.blur[S.args]);
-        __syncthreads();
+        if (st != cur_st) {
+          copy_block_args(&s_args.blur, &e.blur[S.args]);
+          __syncthreads();
+        }
         float sq = 0.0f;
         with_R(S.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
         if (S.part >= 0) {
@@ -288,12 +300,11 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
       default:
         break;
     }
-    // every write of the tile happens before its count is published
+    cur_st = st;
+    // every write of the tile happens before its count is published: block
+    // barrier, then a release add by one thread (cumulative over the barrier)
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(&e.counters[kCtrDone + st], 1);
-    }
+    if (tid == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(e.counters + kCtrDone + st) : "memory");
   }
 }
 

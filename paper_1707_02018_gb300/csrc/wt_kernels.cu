@@ -157,13 +157,11 @@ __device__ __forceinline__ void chain_next(const int* first_item, int nlev, int*
 }
 
 // Every write of the finished tile happens before the count is published
-// (block barrier, then a device-scope fence by the counting thread).
+// (block barrier, then a release add by the counting thread, cumulative over
+// the barrier).
 __device__ __forceinline__ void chain_done(int* counters, int lev) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&counters[kChainDone + lev], 1);
-  }
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counters + kChainDone + lev) : "memory");
 }
 
 // Copy one level's argument block from the launch parameters into shared
