@@ -117,15 +117,21 @@ __device__ __forceinline__ void with_L(int L, Fn&& fn) {
   }
 }
 
-// blur radii are padded up to one of these (zero taps leave the operator unchanged)
-__host__ __device__ constexpr int padded_radius(int r) { return r <= 2 ? 2 : r <= 4 ? 4 : r <= 6 ? 6 : r <= 9 ? 9 : 12; }
+// blur radius of the fused tile: exact from 2 to 9 (the radii of Gaussian
+// PSFs with sigma up to 3), radii 0 and 1 padded to 2 and 10..12 to 12 (zero
+// taps leave the operator unchanged)
+__host__ __device__ constexpr int padded_radius(int r) { return r <= 2 ? 2 : r <= 9 ? r : 12; }
 
 template <typename Fn>
 __device__ __forceinline__ void with_R(int R, Fn&& fn) {
   switch (R) {
     case 2: fn(std::integral_constant<int, 2>()); break;
+    case 3: fn(std::integral_constant<int, 3>()); break;
     case 4: fn(std::integral_constant<int, 4>()); break;
+    case 5: fn(std::integral_constant<int, 5>()); break;
     case 6: fn(std::integral_constant<int, 6>()); break;
+    case 7: fn(std::integral_constant<int, 7>()); break;
+    case 8: fn(std::integral_constant<int, 8>()); break;
     case 9: fn(std::integral_constant<int, 9>()); break;
     default: fn(std::integral_constant<int, 12>()); break;
   }
@@ -571,8 +577,12 @@ size_t engine_smem(int rmax) {
   size_t blur = 0;
   switch (rmax) {
     case 2: blur = blur_tile_smem<2>(); break;
+    case 3: blur = blur_tile_smem<3>(); break;
     case 4: blur = blur_tile_smem<4>(); break;
+    case 5: blur = blur_tile_smem<5>(); break;
     case 6: blur = blur_tile_smem<6>(); break;
+    case 7: blur = blur_tile_smem<7>(); break;
+    case 8: blur = blur_tile_smem<8>(); break;
     case 9: blur = blur_tile_smem<9>(); break;
     default: blur = blur_tile_smem<12>(); break;
   }
