@@ -503,15 +503,18 @@ struct StageList {
 
 // Stage-major order across problems; prev indices become global; the first
 // stage of a problem waits on its last one (previous iteration) when `wrap`.
-void order_stages(const std::vector<StageList>& per, bool wrap, std::vector<Stage>* out, std::vector<int>* item_stage,
-                  std::vector<int>* first, int* items) {
+// Within a stage slot the problems come in the order `rank` (grouped by
+// filter length and blur radius, so that consecutive items run the same
+// stage body and the instruction cache keeps it).
+void order_stages(const std::vector<StageList>& per, const std::vector<int>& rank, bool wrap, std::vector<Stage>* out,
+                  std::vector<int>* item_stage, std::vector<int>* first, int* items) {
   size_t smax = 0;
   for (const auto& l : per) smax = std::max(smax, l.st.size());
   std::vector<std::vector<int>> gidx(per.size());
   for (size_t p = 0; p < per.size(); ++p) gidx[p].assign(per[p].st.size(), -1);
   out->clear();
   for (size_t s = 0; s < smax; ++s)
-    for (size_t p = 0; p < per.size(); ++p)
+    for (int p : rank)
       if (s < per[p].st.size()) {
         gidx[p][s] = static_cast<int>(out->size());
         out->push_back(per[p].st[s]);
@@ -680,8 +683,15 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   std::vector<Stage> rst, ost;
   std::vector<int> ritem, rfirst, oitem, ofirst;
   int ritems = 0, oitems = 0;
-  order_stages(run_lists, true, &rst, &ritem, &rfirst, &ritems);
-  order_stages(obj_lists, false, &ost, &oitem, &ofirst, &oitems);
+  std::vector<int> rank(count);
+  for (int p = 0; p < count; ++p) rank[p] = p;
+  std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) {
+    const int ka = probs[a].wt->fb.L * 64 + blur_radius(probs[a].blur);
+    const int kb = probs[b].wt->fb.L * 64 + blur_radius(probs[b].blur);
+    return ka < kb;
+  });
+  order_stages(run_lists, rank, true, &rst, &ritem, &rfirst, &ritems);
+  order_stages(obj_lists, rank, false, &ost, &oitem, &ofirst, &oitems);
 
   std::vector<unsigned char> blob;
   const size_t o_rst = put(blob, rst), o_ritem = put(blob, ritem), o_rfirst = put(blob, rfirst);
