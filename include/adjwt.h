@@ -327,7 +327,9 @@ int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* 
  * ADJWT_ERR_TIMEOUT in the device status word and the launch drains (a
  * test of the bounded waits; the other problems may have advanced, so reset
  * the batch before using it again).
- * adjwt_fista_batch_info: items per iteration, stages, resident CTAs. */
+ * adjwt_fista_batch_info: items per iteration, stages, resident CTAs.
+ * The launches of one batch share its counters and workspace: issue them on
+ * one stream (or otherwise serialise them). */
 typedef struct adjwt_fista_batch adjwt_fista_batch;
 size_t adjwt_fista_batch_workspace_size(int count, const adjwt_fista_problem* probs);
 int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, const adjwt_fista_problem* probs, float* const* x,
