@@ -130,10 +130,12 @@ int wt_analysis(const adjwt_wt_plan* plan, const float* image, float* coeffs, vo
 
 /* Level implementations.  A level of W (op 0), of W^* / W^dagger (op 1) or
  * of W^* with the FISTA prox epilogue (op 2, a kernel of its own: it also
- * reads and writes the iterate) runs either on the persistent TMA-staged
- * kernel, which takes the tiles a size rule gives it (levels of at least
- * 256 x 512; shared with the tiled kernel only from 1536 x 1536), with the
- * tiled kernel on the rest, or on the tiled kernel alone.  Results agree
+ * reads and writes the iterate) runs either on a persistent TMA-staged
+ * kernel or on the tiled kernel alone.  Size rule: for W the TMA kernel
+ * takes whole levels of at least 256 x 512 whose tiles need no fold (ZERO,
+ * PER) and, from 1536 x 1536, the interior tiles of any level, the tiled
+ * kernel doing the border; for W^* it takes every tile of levels of at least
+ * 1536 x 1536 (border windows completed in shared memory).  Results agree
  * within float32 rounding either way.  adjwt_wt_plan_set_tma(plan, op,
  * level, 0) forces the tiled kernel for that level, 1 restores the rule;
  * adjwt_wt_plan_uses_tma reports whether the TMA kernel runs there.
