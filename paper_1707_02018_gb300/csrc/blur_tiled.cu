@@ -1,19 +1,7 @@
-// Register-blocked tile kernel for the fused R^*(R u - b) without scratch, for
-// PSF radii up to kTiledMaxRadius (compile-time radius; the shorter axis is
-// zero-padded to the same radius, which leaves the operator unchanged).
-//
-// Same operator definitions as blur_kernels.cu.  A CTA owns a 64 x 64 output
-// tile and runs the separable passes in shared memory.  Every pass is a 1D
-// correlation executed by threads that each produce kRB consecutive outputs
-// along the filter direction from one sliding window held in registers
-// (kRB + 2R shared-memory loads for kRB * (2R + 1) FMAs):
-//   vertical passes:   lanes take consecutive columns (conflict-free rows),
-//   horizontal passes: lanes take consecutive rows (odd row pitches keep the
-//                      32 lanes on 32 banks).
-// The boundary extension is applied when the tile is gathered from global
-// memory; tiles that touch the border of a symmetric image switch to the
-// orientation-aware taps of R^* (see blur_kernels.cu) and refill the off-image
-// samples of R u - b from their mirror.
+// Fused R^*(R u - b) without scratch as one tiled kernel (one 64 x 64 output
+// tile per CTA; the tile body and its geometry are in blur_tile.cuh), for
+// PSF radii up to kTiledMaxRadius.  Used when the persistent TMA passes
+// (blur_tma.cu) cannot run or no scratch image is given.
 #include <algorithm>
 
 #include "adjwt_internal.h"

@@ -1,24 +1,10 @@
-// Multi-level 2D wavelet kernels: W (reconstruction), W^* (exact adjoint,
-// Eq. 4) and W^dagger (analysis), one launch per level.
-//
-// Analysis direction (W^* and W^dagger), one level, per axis:
-//     out[k] = sum_i f[i] z[2k+1-i],   z[e] = w(e) * y[src(e)]
-// with e the coordinate of the length N + 2L' extended signal, src(e) the
-// extension map of Sec. I-A (zero / half-point symmetric / periodic) and
-// w = 1/c for W^* (the weighted extension (E^dagger)^*, Eq. 2) or 1 for
-// W^dagger; f are the dual analysis filters (reversed synthesis filters,
-// Eq. 3 / Eq. 4) for W^* and the analysis filters for W^dagger.  The
-// extension is applied in the load path: each CTA gathers its extended tile
-// once into shared memory, then runs the column pass and the row pass there.
-//
-// Reconstruction W = E^dagger S, per axis:
-//     Ysyn(x) = sum_k a_lo[k] g_lo[x+2L'-2k-1] + a_hi[k] g_hi[x+2L'-2k-1]
-//     out[t]  = (1/c[t]) * sum_{x : ext(x) = t} Ysyn(x),  x in [-L', N+L')
-// (x is the extended coordinate shifted by L').  The fold E^dagger is a
-// gather: a CTA computes Ysyn over its own rows plus, at the image border,
-// the L' mirrored rows (symmetric case), so no atomics are needed.  The
-// periodic extension's far copies and tiny images (N <= 2L') go through a
-// per-pixel gather kernel.
+// Multi-level 2D wavelet launches: W (reconstruction), W^* (exact adjoint,
+// Eq. 4) and W^dagger (analysis).  Each level runs as its own launch of the
+// tiled kernels below (whose per-tile bodies are in wt_tiles.cuh), of the
+// persistent TMA kernels (wt_tma.cu) or both; the deepest tiled-only levels
+// can instead run as one level-chain launch (opt-in).  The per-pixel gather
+// kernel takes the periodic extension's far copies, tiny images (N <= 2L')
+// and symmetric levels whose mirror copies straddle a tile boundary.
 #include <algorithm>
 #include <type_traits>
 

@@ -372,7 +372,7 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 // Persistent TMA-staged W^* (+ the FISTA prox) / W^dagger for every tile of
 // a level.  The TMA unit's zero fill is the zero extension; a border tile's
 // window is completed after the copy from the extension map and the 1/c
-// weights (fix_window), and the last row / column tiles store only inside
+// weights (border_prefetch / border_apply), and the last row / column tiles store only inside
 // the bands (pad columns as zero).
 // A tile is kAR x kAC coefficients of each band; its input window is
 // (2 kAR + L - 2) x (2 kAC + L - 2) samples of the extended signal, staged by
