@@ -53,7 +53,10 @@ enum {
   ADJWT_ERR_CUDA = -5,        /* CUDA runtime error (text in last_error)    */
   ADJWT_ERR_NONFINITE = -6,   /* objective or step size not finite          */
   ADJWT_ERR_WORKSPACE = -7,   /* workspace missing, small or misaligned     */
-  ADJWT_ERR_TIMEOUT = -8      /* a bounded device wait gave up              */
+  ADJWT_ERR_TIMEOUT = -8,     /* a bounded device wait gave up              */
+  ADJWT_ERR_BOUNDS = -9       /* checked builds only (-DADJWT_BOUNDS_CHECK):
+                                 a device access fell outside its buffer; it
+                                 was skipped and recorded in the status word */
 };
 
 /* Boundary handling (Sec. I-A).  ZERO: zero-padded extension E_zpd.  SYM:

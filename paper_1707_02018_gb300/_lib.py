@@ -7,7 +7,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libadjwt.so")
+# ADJWT_LIBRARY selects another build of the same library (e.g. the checked
+# build made by build_ext.build(checked=True)); the default is the in-tree one.
+LIB_PATH = os.environ.get("ADJWT_LIBRARY") or os.path.join(HERE, "libadjwt.so")
 
 I64 = C.c_int64
 VP = C.c_void_p

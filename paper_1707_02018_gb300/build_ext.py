@@ -40,8 +40,22 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra=()):
+CHECKED_LIB = os.path.join(ROOT, "_build", "checked", "libadjwt_checked.so")
+
+
+def build(verbose=False, extra=(), checked=False):
+    """Build libadjwt.so in-tree; checked=True builds the bounds-checked
+    variant (-DADJWT_BOUNDS_CHECK) into _build/checked/ instead."""
+    global BUILD, LIB
+    if checked:
+        saved = BUILD, LIB
+        BUILD, LIB = os.path.join(ROOT, "_build", "checked", "obj"), CHECKED_LIB
+        try:
+            return build(verbose, tuple(extra) + ("-DADJWT_BOUNDS_CHECK",), False)
+        finally:
+            BUILD, LIB = saved
     os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), srcs))

@@ -57,6 +57,7 @@ struct TiledArgs {
   float* out;
   double* partials;
   int rows, cols, pitch, bc;  // bc: 0 zero, 1 sym, 3 per
+  int* status;  // device status word (checked builds record ADJWT_ERR_BOUNDS here)
   float pr[2 * kTiledMaxRadius + 1], pc[2 * kTiledMaxRadius + 1];  // padded to 2R+1
 };
 
@@ -150,6 +151,7 @@ __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in
       }
     }
     const int x = x0 + i0;
+    if (!in_bounds(a.status, y >= 0 && x >= 0 && x < a.pitch)) continue;
     float* dst = a.out ? a.out + (size_t)y * a.pitch + x : nullptr;
     const float* bb = bsub ? bsub + (size_t)y * a.pitch + x : nullptr;
     if (x + kRB <= a.cols) {
@@ -202,7 +204,7 @@ __device__ __forceinline__ void load_taps(const TiledArgs& a, float (&pr)[2 * R 
 template <int NR, int NC, bool CG = false>
 __device__ __forceinline__ void gather(const float* __restrict__ img, int rows, int cols, int pitch, int mode,
                                        int oy, int ox, float* __restrict__ dst, int sp,
-                                       const int* __restrict__ src_c) {
+                                       const int* __restrict__ src_c, int* status = nullptr) {
   constexpr int total = NR * NC;
   constexpr int U = 16;
   const bool inside = oy >= 0 && ox >= 0 && oy + NR <= rows && ox + NC <= cols;
@@ -216,10 +218,12 @@ __device__ __forceinline__ void gather(const float* __restrict__ img, int rows, 
       if (i < total) {
         const int rr = i / NC, cc = i - rr * NC;
         if (inside) {
-          v[u] = CG ? __ldcg(base + (size_t)rr * pitch + cc) : __ldg(base + (size_t)rr * pitch + cc);
+          if (in_bounds(status, oy + rr < rows && ox + cc < cols))
+            v[u] = CG ? __ldcg(base + (size_t)rr * pitch + cc) : __ldg(base + (size_t)rr * pitch + cc);
         } else {
           const int sr = ext_src(oy + rr, rows, mode), sc = src_c[cc];
-          if (sr >= 0 && sc >= 0) v[u] = CG ? __ldcg(img + (size_t)sr * pitch + sc) : __ldg(img + (size_t)sr * pitch + sc);
+          if (sr >= 0 && sc >= 0 && in_bounds(status, sr < rows && sc < cols))
+            v[u] = CG ? __ldcg(img + (size_t)sr * pitch + sc) : __ldg(img + (size_t)sr * pitch + sc);
         }
       }
     }
@@ -259,7 +263,7 @@ __device__ __forceinline__ void blur_normal_tile(const TiledArgs& a, int tile_y,
   for (int u = tid; u < G::VROWS; u += kNT) flip_r[u] = sym && odd_period(y0 - R + u, a.rows);
   for (int c = tid; c < G::VP; c += kNT) flip_c[c] = sym && odd_period(x0 - R + c, a.cols);
   __syncthreads();
-  gather<G::UR, G::UC, CG>(a.in, a.rows, a.cols, a.pitch, mode, y0 - 2 * R, x0 - 2 * R, A, G::UP, src_c);
+  gather<G::UR, G::UC, CG>(a.in, a.rows, a.cols, a.pitch, mode, y0 - 2 * R, x0 - 2 * R, A, G::UP, src_c, a.status);
   __syncthreads();
   float pr[2 * R + 1], pc[2 * R + 1];
   load_taps<R>(a, pr, pc, true);  // convolution = correlation with reversed taps

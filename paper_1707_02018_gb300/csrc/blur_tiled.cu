@@ -59,6 +59,7 @@ int launch_tiled_blur(const adjwt_blur_plan* p, const float* in, const float* b,
   a.b = b;
   a.out = out;
   a.partials = partials;
+  a.status = device_status_ptr();
   a.rows = p->rows;
   a.cols = p->cols;
   a.pitch = p->image_pitch;

@@ -106,6 +106,7 @@ struct Strips {
     using G = TG<R>;
     const int rr = c / G::BW, cc = c - rr * G::BW;
     const int sr = ext_near(y0 - R + rr, a.rows, mode), sc = ext_near(x0 - G::XA + cc, a.cols, mode);
+    if (!in_bounds(a.status, sr >= 0 && sr < a.rows && sc >= 0 && sc < a.cols)) return 0.0f;
     return __ldg(a.in + (size_t)sr * a.pitch + sc);
   }
 };

@@ -7,6 +7,20 @@
 
 namespace adjwt {
 
+// Checked builds (-DADJWT_BOUNDS_CHECK): the index arithmetic of the tile
+// bodies' global loads and stores is tested against the extents of their
+// buffers; an access outside them is skipped (a load reads zero) and
+// ADJWT_ERR_BOUNDS is recorded in the device status word (first writer
+// wins).  Release builds compile the test away.
+#ifdef ADJWT_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(int* status, bool ok) {
+  if (!ok && status) atomicCAS(status, 0, -9 /* ADJWT_ERR_BOUNDS */);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool in_bounds(int*, bool) { return true; }
+#endif
+
 __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
   int q = a / b;
   return (a % b != 0 && a < 0) ? q - 1 : q;

@@ -394,6 +394,7 @@ SynArgs syn_level(const adjwt_wt_plan* w, int j, const float* coeffs, float* out
   a.mode = w->bc;
   a.winv_r = L.ax[0].winv;
   a.winv_c = L.ax[1].winv;
+  a.status = device_status_ptr();
   for (int t = 0; t < w->fb.L; ++t) {
     a.g[0][t] = static_cast<float>(w->fb.rec_lo[t]);
     a.g[1][t] = static_cast<float>(w->fb.rec_hi[t]);
@@ -419,6 +420,7 @@ AnaArgs ana_level(const adjwt_fista_problem& pr, int j, const float* in_image, f
   a.winv_r = adjoint ? L.ax[0].winv : nullptr;
   a.winv_c = adjoint ? L.ax[1].winv : nullptr;
   a.out_pitch = L.band_pitch;
+  a.status = device_status_ptr();
   for (int b = 0; b < 4; ++b) {
     if (b > 0 || j == w->levels) {
       a.px[b] = x + L.off_band[b];
@@ -457,6 +459,7 @@ TiledArgs blur_args(const adjwt_fista_problem& pr, const float* u, float* g, dou
   a.cols = p->cols;
   a.pitch = p->image_pitch;
   a.bc = p->bc;
+  a.status = device_status_ptr();
   const int orr = R - p->kr / 2, oc = R - p->kc / 2;
   for (int t = 0; t < p->kr; ++t) a.pr[orr + t] = static_cast<float>(p->taps_r[t]);
   for (int t = 0; t < p->kc; ++t) a.pc[oc + t] = static_cast<float>(p->taps_c[t]);

@@ -248,6 +248,7 @@ SynArgs synth_args(const adjwt_wt_plan* p, int j, const float* coeffs, float* im
   a.mode = p->bc;
   a.winv_r = L.ax[0].winv;
   a.winv_c = L.ax[1].winv;
+  a.status = device_status_ptr();
   for (int t = 0; t < fb.L; ++t) {
     a.g[0][t] = static_cast<float>(fb.rec_lo[t]);
     a.g[1][t] = static_cast<float>(fb.rec_hi[t]);
@@ -329,6 +330,7 @@ int launch_wt_analysis(const adjwt_wt_plan* p, const float* image, float* coeffs
     a.winv_r = adjoint ? L.ax[0].winv : nullptr;
     a.winv_c = adjoint ? L.ax[1].winv : nullptr;
     a.out_pitch = L.band_pitch;
+    a.status = device_status_ptr();
     for (int b = 0; b < 4; ++b) {
       const bool final_band = (b > 0) || (j == p->levels);
       float* base = nullptr;

@@ -50,6 +50,7 @@ struct AnaArgs {
   double* l1;     // per-CTA partials (null = skip)
   float flo[kMaxTaps], fhi[kMaxTaps];
   int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;  // tiles left to the TMA kernel (see border_tile)
+  int* status;  // device status word (checked builds record ADJWT_ERR_BOUNDS here)
 };
 
 
@@ -170,7 +171,8 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
   float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
   float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
   float* slot = prox_slots + tid * kProxSlot;
-  if (has_prox && rower && k < a.nr && lbase < a.out_pitch) {
+  if (has_prox && rower && k < a.nr && lbase < a.out_pitch &&
+      in_bounds(a.status, !full || lbase + kAP <= a.out_pitch)) {
 #pragma unroll
     for (int hb = 0; hb < 2; ++hb) {
       if (!pxs[hb]) continue;
@@ -216,8 +218,11 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
     staged_copy<E * E, NT>(
         E * E,
         [&](int i) {
-          const int er = i / E;
-          return ld_level<CG>(src + (size_t)er * a.in_pitch + (i - er * E));
+          const int er = i / E, ec = i - er * E;
+          const int ir = e0r - sh + er, ic = e0c - sh + ec;  // image row / column (the tile is interior)
+          return in_bounds(a.status, ir >= 0 && ir < a.Nr && ic >= 0 && ic < a.Nc)
+                     ? ld_level<CG>(src + (size_t)er * a.in_pitch + ec)
+                     : 0.0f;
         },
         [&](int i, float v) {
           const int er = i / E;
@@ -244,8 +249,9 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
         [&](int i) {
           const int er = i / E, ec = i - er * E;
           const int sr = s_src[0][er], sc = s_src[1][ec];
-          return (sr >= 0 && sc >= 0) ? s_w[0][er] * s_w[1][ec] * ld_level<CG>(a.in + (size_t)sr * a.in_pitch + sc)
-                                      : 0.0f;
+          return (sr >= 0 && sc >= 0 && in_bounds(a.status, sr < a.Nr && sc < a.Nc))
+                     ? s_w[0][er] * s_w[1][ec] * ld_level<CG>(a.in + (size_t)sr * a.in_pitch + sc)
+                     : 0.0f;
         },
         [&](int i, float v) {
           const int er = i / E;
@@ -294,7 +300,7 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
       res[0][p] = lo;
       res[1][p] = hi;
     }
-    if (k < a.nr && lbase < a.out_pitch) {
+    if (k < a.nr && lbase < a.out_pitch && in_bounds(a.status, !full || lbase + kAP <= a.out_pitch)) {
       float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
       // prox bands: y and x from this thread's slot (copied at kernel start)
       float yv[2][kAP], xv[2][kAP];
@@ -372,6 +378,7 @@ struct SynArgs {
   // kernel; the grid then enumerates the other tiles of the tiles_r x tiles_c
   // grid (rows above, rows below, then the columns beside the rectangle)
   int in_r0, in_r1, in_c0, in_c1, tiles_r, tiles_c;
+  int* status;  // device status word (checked builds record ADJWT_ERR_BOUNDS here)
 };
 
 // ---------------------------------------------------------------- synthesis
@@ -495,7 +502,9 @@ __device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
         const int kk = half + 2 * r;
-        v[r] = (kk < nk[0] && lane < nk[1]) ? ld_level<CG>(src + (size_t)(2 * r) * a.band_pitch) : 0.0f;
+        const bool take = kk < nk[0] && lane < nk[1] &&
+                          in_bounds(a.status, ka[0] + kk < a.nr && ka[1] + lane < a.nc && ka[0] >= 0 && ka[1] >= 0);
+        v[r] = take ? ld_level<CG>(src + (size_t)(2 * r) * a.band_pitch) : 0.0f;
       }
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
@@ -536,6 +545,7 @@ __device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int
         pair_block<L, 1>(c0, c1, g0, g1, out);
       else
         pair_block<L, 0>(c0, c1, g0, g1, out);
+      if (!in_bounds(a.status, t0r + tt < a.Nr && t0c + 2 * kSP * (blk + 1) <= a.out_pitch)) continue;
       float4* dst = reinterpret_cast<float4*>(a.out + (size_t)(t0r + tt) * a.out_pitch + t0c + 2 * kSP * blk);
       dst[0] = make_float4(out[0], out[1], out[2], out[3]);
       dst[1] = make_float4(out[4], out[5], out[6], out[7]);
@@ -568,6 +578,7 @@ __device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int
         } else if (k < 0 || k >= a.nr || l < 0 || l >= a.nc) {
           return 0.0f;
         }
+        if (!in_bounds(a.status, k >= 0 && k < a.nr && l >= 0 && l < a.nc)) return 0.0f;
         return ld_level<CG>(a.band[b] + (size_t)k * a.band_pitch + l);
       },
       [&](int i, float v) {
@@ -658,8 +669,10 @@ __device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int
       if (tc < a.Nc) {
         s = Y[tt][tc - xa[1]];
         if (sym) {
-          if (tc < Lp) s += Y[tt][-1 - tc - xa[1]];
-          if (tc >= a.Nc - Lp) s += Y[tt][2 * a.Nc - 1 - tc - xa[1]];
+          if (tc < Lp && in_bounds(a.status, -1 - tc - xa[1] >= 0 && -1 - tc - xa[1] < nx[1]))
+            s += Y[tt][-1 - tc - xa[1]];
+          if (tc >= a.Nc - Lp && in_bounds(a.status, 2 * a.Nc - 1 - tc - xa[1] < nx[1]))
+            s += Y[tt][2 * a.Nc - 1 - tc - xa[1]];
         }
         s *= s_wc[c4 + u];
       }
@@ -668,7 +681,8 @@ __device__ __forceinline__ void synthesis_tile(const SynArgs& a, int tile_y, int
     const bool ppd_row = ppd && (tr < Lp || tr >= a.Nr - Lp);
     float* dst = a.out + (size_t)tr * a.out_pitch + t0c + c4;
     if (!ppd && t0c + c4 + 4 <= a.Nc) {
-      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      if (in_bounds(a.status, t0c + c4 + 4 <= a.out_pitch))
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -733,7 +747,7 @@ __device__ __forceinline__ void synthesis_gather_pixel(const SynArgs& a, int tr,
   }
   if (a.winv_r) acc *= __ldg(a.winv_r + tr);
   if (a.winv_c) acc *= __ldg(a.winv_c + tc);
-  a.out[(size_t)tr * a.out_pitch + tc] = acc;
+  if (in_bounds(a.status, tr >= 0 && tr < a.Nr && tc >= 0 && tc < a.Nc)) a.out[(size_t)tr * a.out_pitch + tc] = acc;
 }
 
 }  // namespace

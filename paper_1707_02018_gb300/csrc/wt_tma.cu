@@ -526,7 +526,9 @@ __device__ __forceinline__ float border_far(const AnaTmaArgs& a, const AnaBorder
   using G = AG<L>;
   const int r = cell / G::EC, c = cell - r * G::EC;
   const int sr = ana_src<L>(a, b.e0r + r, a.Nr), sc = ana_src<L>(a, b.e0c + c, a.Nc);
-  return (sr >= 0 && sc >= 0) ? __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+  return (sr >= 0 && sc >= 0 && in_bounds(a.status, sr < a.Nr && sc < a.Nc))
+             ? __ldg(a.in + (size_t)sr * a.in_pitch + sc)
+             : 0.0f;
 }
 
 // Before the copy has landed: the tables, and (periodic extensions) the far
@@ -556,12 +558,13 @@ __device__ __forceinline__ void border_apply(const AnaTmaArgs& a, const AnaBorde
     for (int i = threadIdx.x; i < b.total; i += kNT) {
       const int cell = border_cell<L>(b, i), r = cell / G::EC, c = cell - r * G::EC;
       const int wr = t.win[r], wc = t.win[G::ER + c];
-      float v;
+      float v = 0.0f;
       if (wr >= 0 && wc >= 0) {
-        v = S[wr * G::BC + wc];
+        if (in_bounds(a.status, wr < G::ER && wc < G::EC)) v = S[wr * G::BC + wc];
       } else {
         const int sr = t.img[r], sc = t.img[G::ER + c];
-        v = (sr >= 0 && sc >= 0) ? __ldg(a.in + (size_t)sr * a.in_pitch + sc) : 0.0f;
+        if (sr >= 0 && sc >= 0 && in_bounds(a.status, sr < a.Nr && sc < a.Nc))
+          v = __ldg(a.in + (size_t)sr * a.in_pitch + sc);
       }
       S[r * G::BC + c] = v;
     }
