@@ -151,6 +151,7 @@ __device__ __forceinline__ void hpass_store(const float* __restrict__ in, int in
       }
     }
     const int x = x0 + i0;
+    if (x >= a.cols) continue;  // a block past the last column of the last tile: nothing to store
     if (!in_bounds(a.status, y >= 0 && x >= 0 && x < a.pitch)) continue;
     float* dst = a.out ? a.out + (size_t)y * a.pitch + x : nullptr;
     const float* bb = bsub ? bsub + (size_t)y * a.pitch + x : nullptr;
