@@ -806,6 +806,41 @@ def batched_vs_plain(adj, torch, tol=1e-4, check_every=10, ref_iters=5000, max_i
             captures += 1
     batched = time.perf_counter() - t0
     batched_iters = it
+    graph_reached = not active
+    # engine: `check_every` iterations of every active problem per launch,
+    # then the objective launch; rebuilt over the remaining problems when a
+    # quarter of them have converged (creation time included)
+    for pr in probs:
+        pr["fista"].reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    active = list(range(P))
+    batch = adj.FistaBatch([probs[i]["fista"] for i in active])
+    batch.reset()
+    in_batch, it_e, rebuilds = list(active), 0, 0
+    while it_e < max_iters and active:
+        batch.run(check_every)
+        it_e += check_every
+        F = batch.objective().cpu().numpy()
+        rel = {i: (F[k] - fstar[i]) / fstar[i] for k, i in enumerate(in_batch)}
+        active = [i for i in active if rel[i] > tol]
+        if active and len(active) <= 0.75 * len(in_batch):
+            # the new batch continues from each problem's state: x, y as they
+            # are; the momentum t restarts at the value the engine had reached
+            keep = [probs[i]["fista"] for i in active]
+            saved = [(f.x.clone(), f.y.clone()) for f in keep]
+            batch = adj.FistaBatch(keep)
+            batch.reset()
+            for f, (xs, ys) in zip(keep, saved):
+                f.x.copy_(xs)
+                f.y.copy_(ys)
+            batch.set_momentum(it_e)
+            in_batch = list(active)
+            rebuilds += 1
+    torch.cuda.synchronize()
+    engine_s = time.perf_counter() - t0
+    engine_iters = it_e
+    engine_reached = not active
     # plain
     plain, iters = 0.0, []
     for i, pr in enumerate(probs):
@@ -824,7 +859,9 @@ def batched_vs_plain(adj, torch, tol=1e-4, check_every=10, ref_iters=5000, max_i
         iters.append(k)
     return {"problems": P, "sizes": [pr["n"] for pr in probs], "plain_sec": plain, "batched_sec": batched,
             "speedup": plain / batched, "plain_iterations": iters, "batched_iterations": batched_iters,
-            "reached": not active and max(iters) < max_iters, "graph_build_sec": build, "graph_captures": captures,
+            "engine_sec": engine_s, "engine_speedup": plain / engine_s, "engine_iterations": engine_iters,
+            "engine_reached": engine_reached, "engine_rebuilds": rebuilds,
+            "reached": graph_reached and max(iters) < max_iters, "graph_build_sec": build, "graph_captures": captures,
             "tol": tol, "check_every": check_every, "F_star_iterations": ref_iters,
             "mix": "sizes U{128..1024}, levels U{3..6}, db2/db4/cdf97, sigma U[0.8,3], SYM"}
 

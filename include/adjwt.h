@@ -322,7 +322,9 @@ int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* 
  * memory once); later calls allocate nothing.  Errors: INVALID_ARG, SHAPE
  * (an unsupported problem), ALIGN, WORKSPACE, CUDA.
  * adjwt_fista_batch_reset: t_1 = 1 for every problem (the caller zeroes or
- * sets x and y, with y = x).
+ * sets x and y, with y = x).  adjwt_fista_batch_set_iteration: the momentum
+ * every problem has after k iterations from t_1 = 1 (to continue the runs of
+ * a rebuilt batch whose problems kept their x and y); 0 <= k <= 1e8.
  * adjwt_fista_batch_run: iters iterations of every problem, one launch
  * (plus a memset of its counters) on `stream`.
  * adjwt_fista_batch_objective: objectives_dev[i] (DEVICE doubles) =
@@ -341,6 +343,7 @@ int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, const adjwt_fis
                              float* const* y, void* ws, size_t ws_bytes);
 void adjwt_fista_batch_destroy(adjwt_fista_batch* batch);
 int adjwt_fista_batch_reset(const adjwt_fista_batch* batch, adjwt_stream_t stream);
+int adjwt_fista_batch_set_iteration(const adjwt_fista_batch* batch, int64_t k, adjwt_stream_t stream);
 int adjwt_fista_batch_run(const adjwt_fista_batch* batch, int iters, adjwt_stream_t stream);
 int adjwt_fista_batch_objective(const adjwt_fista_batch* batch, double* objectives_dev, adjwt_stream_t stream);
 int adjwt_fista_batch_wait_selftest(const adjwt_fista_batch* batch, adjwt_stream_t stream);

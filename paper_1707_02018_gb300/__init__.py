@@ -437,6 +437,11 @@ class FistaBatch:
                 f.y.zero_()
         _lib.check(lib().adjwt_fista_batch_reset(self._h, _stream(stream)))
 
+    def set_momentum(self, k, stream=None):
+        """Momentum of every problem as after k iterations from t_1 = 1 (x and
+        y untouched): continues runs that a rebuilt batch takes over."""
+        _lib.check(lib().adjwt_fista_batch_set_iteration(self._h, int(k), _stream(stream)))
+
     def run(self, iters, stream=None):
         _lib.check(lib().adjwt_fista_batch_run(self._h, int(iters), _stream(stream)))
 

@@ -65,6 +65,7 @@ PROTOTYPES = {
                                            C.POINTER(VP), VP, SZ]),
     "adjwt_fista_batch_destroy": (None, [VP]),
     "adjwt_fista_batch_reset": (C.c_int, [VP, VP]),
+    "adjwt_fista_batch_set_iteration": (C.c_int, [VP, I64, VP]),
     "adjwt_fista_batch_run": (C.c_int, [VP, C.c_int, VP]),
     "adjwt_fista_batch_objective": (C.c_int, [VP, VP, VP]),
     "adjwt_fista_batch_wait_selftest": (C.c_int, [VP, VP]),

@@ -314,11 +314,11 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
   }
 }
 
-__global__ void k_batch_reset(double* const* mom, int count) {
+__global__ void k_batch_reset(double* const* mom, int count, double t) {
   pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) {
-    mom[i][0] = 1.0;
+    mom[i][0] = t;
     mom[i][1] = 0.0;
   }
 }
@@ -747,13 +747,31 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
 
 extern "C" void adjwt_fista_batch_destroy(adjwt_fista_batch* b) { delete b; }
 
-extern "C" int adjwt_fista_batch_reset(const adjwt_fista_batch* b, adjwt_stream_t stream) {
-  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_reset: batch is NULL");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
+int set_momentum(const adjwt_fista_batch* b, double t, cudaStream_t s) {
   const unsigned nb = static_cast<unsigned>((b->count + 127) / 128);
-  ADJWT_TRACED("fista_batch_reset", 0, s, pdl_launch(k_batch_reset, nb, 128, 0, s, b->mom_ptrs, b->count));
+  ADJWT_TRACED("fista_batch_reset", 0, s, pdl_launch(k_batch_reset, nb, 128, 0, s, b->mom_ptrs, b->count, t));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
+}
+}  // namespace
+
+extern "C" int adjwt_fista_batch_reset(const adjwt_fista_batch* b, adjwt_stream_t stream) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_reset: batch is NULL");
+  return set_momentum(b, 1.0, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int adjwt_fista_batch_set_iteration(const adjwt_fista_batch* b, int64_t k, adjwt_stream_t stream) {
+  if (!b) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_set_iteration: batch is NULL");
+  if (k < 0 || k > 100000000) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_fista_batch_set_iteration: k outside 0..1e8");
+  // t_{k+1} after k iterations from t_1 = 1, rounded as the device momentum stage does
+  double t = 1.0, t1 = 0.0;
+  float beta = 0.0f;
+  for (int64_t i = 0; i < k; ++i) {
+    fista_momentum(t, &t1, &beta);
+    t = t1;
+  }
+  return set_momentum(b, t, static_cast<cudaStream_t>(stream));
 }
 
 namespace {

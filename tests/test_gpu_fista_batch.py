@@ -145,3 +145,33 @@ def test_batch_rejects_what_it_cannot_run(adj):
     with pytest.raises(adj.AdjwtError) as e:
         adj.FistaBatch([f])
     assert e.value.code == -2
+
+
+def test_rebuilt_batch_continues_the_runs(adj):
+    """A batch rebuilt over a subset of the problems, with their x and y kept
+    and the momentum set to where the first batch left it, continues the same
+    FISTA sequences: the iterates after 6 + 4 iterations are bit-identical to
+    10 iterations in one batch."""
+    probs = _problems(adj)
+    fs = [p["fista"] for p in probs]
+    whole = adj.FistaBatch(fs)
+    whole.reset()
+    whole.run(10)
+    torch.cuda.synchronize()
+    want = [f.x.clone() for f in fs]
+    whole.reset()
+    whole.run(6)
+    sub = [0, 2, 5, 7]
+    keep = [fs[i] for i in sub]
+    saved = [(f.x.clone(), f.y.clone()) for f in keep]
+    part = adj.FistaBatch(keep)
+    part.reset()
+    for f, (x, y) in zip(keep, saved):
+        f.x.copy_(x)
+        f.y.copy_(y)
+    part.set_momentum(6)
+    part.run(4)
+    torch.cuda.synchronize()
+    for i, f in zip(sub, keep):
+        assert torch.equal(f.x, want[i]), i
+    assert adj.device_status() == 0
