@@ -121,3 +121,30 @@ def test_blur_tma_and_tiled_paths(adj, bc, kr, kc):
         assert_close(to_host_image(adj.blur_adjoint(plan, du), rows, cols), oblur.blur_adjoint(u, pr, pc, bc),
                      what="R^* " + what)
     assert adj.device_status() == 0
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("taps", [(15, 3.0, 15, 3.0), (9, 1.5, 5, 1.0), (25, 4.0, 25, 4.0), (3, 0.8, 3, 0.8)],
+                         ids=["g15", "g9x5", "g25", "g3"])
+def test_normal_palindromic_taps(adj, bc, taps):
+    """R^*(R u - b) with Gaussian (palindromic) taps of radii 1 to 12, the
+    case in which the symmetric boundary's R^* needs no orientation flips:
+    shapes spanning several 32 x 128 tiles with ragged last rows and columns,
+    images narrower than a tile and smaller than the PSF, with and without b;
+    g element by element and 1/2 ||R u - b||^2 against the oracle."""
+    kr, sr, kc, sc = taps
+    pr, pc = oblur.gaussian_psf(kr, sr), oblur.gaussian_psf(kc, sc)
+    for rows, cols in [(200, 300), (131, 257), (64, 128), (13, 600), (257, 40), (33, 129), (4, 6), (1, 1)]:
+        plan = adj.BlurPlan(rows, cols, pr, pc, bc)
+        u = random_vector((rows, cols), 3 * rows + cols)
+        b = random_vector((rows, cols), 5 * rows + cols)
+        du, db = image_dev(plan, u), image_dev(plan, b)
+        what = f"{bc} {kr}x{kc} {rows}x{cols}"
+        gw, hw = oblur.blur_normal(u, b, pr, pc, bc)
+        g, h = adj.blur_normal(plan, du, db, want_norm=True)
+        assert_close(to_host_image(g, rows, cols), gw, what="R^*(Ru-b) " + what)
+        assert abs(float(h) - hw) <= 1e-5 * hw, what
+        g0 = adj.blur_normal(plan, du, None)
+        assert_close(to_host_image(g0, rows, cols), oblur.blur_normal(u, np.zeros_like(u), pr, pc, bc)[0],
+                     what="R^*R u " + what)
+    assert adj.device_status() == 0
