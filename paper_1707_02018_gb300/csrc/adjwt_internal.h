@@ -89,6 +89,11 @@ int* device_status_ptr();
 // box_rows x box_cols box; out-of-range elements read as zero.
 int make_tmap_2d_f32(CUtensorMap* map, const float* base, int rows, int cols, int pitch_floats, int box_rows,
                      int box_cols);
+// The same with the 128-byte swizzle (box rows of 128 bytes; the shared-memory
+// box must start 1024-byte aligned): 16-byte chunk c of box row r lies at
+// chunk position c ^ (r mod 8).
+int make_tmap_2d_f32_sw(CUtensorMap* map, const float* base, int rows, int cols, int pitch_floats, int box_rows,
+                        int box_cols, bool swizzle128);
 int sm_count();
 
 // ---------------------------------------------------------------- tracing

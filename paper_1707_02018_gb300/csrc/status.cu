@@ -77,6 +77,11 @@ int* device_status_ptr() {
 
 int make_tmap_2d_f32(CUtensorMap* map, const float* base, int rows, int cols, int pitch_floats, int box_rows,
                      int box_cols) {
+  return make_tmap_2d_f32_sw(map, base, rows, cols, pitch_floats, box_rows, box_cols, false);
+}
+
+int make_tmap_2d_f32_sw(CUtensorMap* map, const float* base, int rows, int cols, int pitch_floats, int box_rows,
+                        int box_cols, bool swizzle128) {
   auto fn = encode_fn();
   if (!fn) return fail(ADJWT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
@@ -84,7 +89,8 @@ int make_tmap_2d_f32(CUtensorMap* map, const float* base, int rows, int cols, in
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ADJWT_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string(r) + ")");
   return ADJWT_OK;

@@ -19,6 +19,7 @@
 //   row pass:    a thread makes 16 consecutive pixels of one row (lanes on
 //                rows, odd pitch) and stores them as float4.
 #include <algorithm>
+#include <cstring>
 
 #include "adjwt_internal.h"
 #include "device_common.cuh"
@@ -398,13 +399,37 @@ struct AG {
   static constexpr int BUF = up32(ER * BC);
   static constexpr int NW = 2 * kAP + L - 2;      // register window per thread
   static constexpr int VP = EC | 1;               // odd pitch of the column-pass output
-  // prox variant: each row-pass thread's slot of next-tile prox state (x and y
-  // of its two bands, 8 values each), padded to 36 floats so that the 16-byte
-  // slot reads of a quarter warp fall on distinct banks
-  static constexpr int kSlot = 36;
+  // Output tiles (and, with the prox, the state y and x of the prox bands)
+  // are staged as 16 x 32 boxes of 128-byte rows under the 128-byte swizzle:
+  // the outputs of a band in the window buffer the column pass has consumed
+  // (from a 1024-byte boundary inside it), y and x of every prox band in P.
+  static constexpr int OUT0 = 0;                        // staging of buffer 0 (floats, 256-float aligned)
+  static constexpr int OUT1 = (BUF + 255) / 256 * 256;  // staging of buffer 1
+  static constexpr int V0 = 2 * BUF;
+  static constexpr int P0 = (V0 + 2 * kAR * VP + 255) / 256 * 256;
+  static_assert(OUT1 + 4 * 2 * kAR * 32 <= 2 * BUF, "four staged bands fit in window buffer 1");
+  static_assert(4 * 2 * kAR * 32 <= BUF, "four staged bands fit in window buffer 0");
   static constexpr size_t smem_bytes(bool prox) {
-    return 128 + (size_t)(2 * BUF + 2 * kAR * VP + (prox ? (kAC / kAP) * 32 * kSlot : 0)) * 4;
+    return 1024 + (size_t)(prox ? P0 + 8 * 2 * kAR * 32 : V0 + 2 * kAR * VP) * 4;
   }
+};
+
+constexpr int kOB = kAR * 32;   // floats per staged 16 x 32 box
+constexpr int kOBand = 2 * kOB; // one band's 16 x 64 tile
+
+// Float offset of coefficient (r, c), c < 64, in a band tile staged as two
+// 16 x 32 boxes under the 128-byte swizzle (16-byte chunk c/4 of row r at
+// chunk position (c/4) xor (r mod 8)).  A quarter warp on 8 consecutive rows
+// reading the same 16-byte column chunk hits 8 distinct bank groups.
+__device__ __forceinline__ int sw_off(int r, int c) {
+  return (c >> 5) * kOB + r * 32 + ((((c >> 2) & 7) ^ (r & 7)) << 2) + (c & 3);
+}
+
+// Tensor maps of the output bands (16 x 32 boxes, 128-byte swizzle) over the
+// band_rows x out_pitch bands: for band i, m[2 i] is y of a prox band or the
+// plain destination, m[2 i + 1] is x of a prox band.
+struct AnaOutMaps {
+  CUtensorMap m[8];
 };
 
 struct AnaTmaArgs {
@@ -596,27 +621,29 @@ __device__ __forceinline__ void border_apply(const AnaTmaArgs& a, const AnaBorde
 
 template <int L, bool PROX>
 __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
-    k_ana_tma(const __grid_constant__ CUtensorMap map, const AnaTmaArgs a) {
+    k_ana_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ AnaOutMaps om, const AnaTmaArgs a) {
   pdl_entry();
   using G = AG<L>;
   constexpr int Lp = L - 1;
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
+  __shared__ uint64_t pbar;  // prox state of the current tile
   __shared__ double red[kNT / 32];
   __shared__ BorderTables<L> tabs;  // border tiles
-  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
-  float* V = buf0 + 2 * G::BUF;  // [2][kAR][VP]
+  float* buf0 = reinterpret_cast<float*>(dyn + ((1024 - (smem_u32(dyn) & 1023)) & 1023));
+  float* V = buf0 + G::V0;  // [2][kAR][VP]
+  float* P = buf0 + G::P0;  // prox: y, x of band i at P + (2 i) kOBand, P + (2 i + 1) kOBand
   const int tid = threadIdx.x;
-  float* slot = V + 2 * kAR * G::VP + tid * G::kSlot;  // prox: this thread's next-tile state (y, x per band)
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&pbar, 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  uint32_t phase = 0, pending = 0;
+  uint32_t phase = 0, pending = 0, pphase = 0, ppending = 0;
   auto tile_origin = [&](int t, int& k0, int& l0) {
     const int ty = t / a.ntx;
     k0 = (a.ty0 + ty) * kAR;
@@ -632,70 +659,54 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
     }
     pending |= 1u << b;
   };
+  // prox variant: y and x of every prox band of tile t into P (two boxes each;
+  // boxes past the band read as zero)
+  int nprox = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) nprox += a.px[i] != nullptr;
+  auto issue_prox = [&](int t) {
+    int k0, l0;
+    tile_origin(t, k0, l0);
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&pbar, nprox * 2 * kOBand * 4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!a.px[i]) continue;
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+          tma_load_2d(P + 2 * i * kOBand + bx * kOB, &om.m[2 * i], &pbar, l0 + 32 * bx, k0);
+          tma_load_2d(P + (2 * i + 1) * kOBand + bx * kOB, &om.m[2 * i + 1], &pbar, l0 + 32 * bx, k0);
+        }
+      }
+    }
+    ppending = 1;
+  };
+  auto drain = [&]() {
+    for (int bb = 0; bb < 2; ++bb)
+      if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
+    if (PROX && ppending) mbar_wait(&pbar, pphase & 1);
+    if (tid == 0) bulk_wait_all();
+  };
 
   float l1 = 0.0f;
   const float beta = PROX && a.beta_dev ? static_cast<float>(*a.beta_dev) : a.beta;
   // row-pass thread: (vertical filter f, coefficient row kk), 8-coefficient block = warp
   const int warp = tid >> 5, lane = tid & 31, f = lane >> 4, kk = lane & 15;
   const bool rower = warp < kAC / kAP;
-  auto pick = [&](float* const (&arr)[4], int bnd) -> float* {
-    return bnd == 0 ? arr[0] : (bnd == 1 ? arr[1] : (bnd == 2 ? arr[2] : arr[3]));
-  };
-  float* pxs[2] = {pick(a.px, f), pick(a.px, f + 2)};
-  float* pys[2] = {pick(a.py, f), pick(a.py, f + 2)};
-  // prox variant: a thread copies the prox state it will need for a tile
-  // (its 8 coefficients of y and x in both of its bands) into its own slot
-  // one tile ahead; only the thread itself reads the slot, so no barrier
-  // (cells past the last band row or the row pitch read as zero)
-  auto prefetch_prox = [&](int tt) {
-    int pk0, pl0;
-    tile_origin(tt, pk0, pl0);
-    const bool pv = pk0 + kk < a.nr;
-    const int pc = pl0 + kAP * warp;
-    const size_t prow = pv ? (size_t)(pk0 + kk) * a.out_pitch + pc : 0;
-#pragma unroll
-    for (int hb = 0; hb < 2; ++hb) {
-      if (!pxs[hb]) continue;
-#pragma unroll
-      for (int q = 0; q < kAP / 4; ++q) {
-        const bool in = pv && pc + 4 * q + 4 <= a.out_pitch;
-        cp_async16(slot + hb * 16 + 4 * q, pys[hb] + (in ? prow + 4 * q : 0), in ? 16u : 0u);
-        cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + (in ? prow + 4 * q : 0), in ? 16u : 0u);
-      }
-    }
-    cp_async_commit();
-  };
   int t = blockIdx.x, b = 0;
-  if (t < a.ntiles) issue(t, 0);
-  if (PROX && rower && t < a.ntiles) prefetch_prox(t);
+  if (t < a.ntiles) {
+    issue(t, 0);
+    if (PROX) issue_prox(t);
+  }
   for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
     int k0, l0;
     tile_origin(t, k0, l0);
-    if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
     const bool rvalid = k0 + kk < a.nr;     // the last row tile may be partial
     const int lbase = l0 + kAP * warp;      // and the last column tile
-    const size_t row = rvalid ? (size_t)(k0 + kk) * a.out_pitch + lbase : 0;
     // border tile: tables (and far off-image cells) fetched while the copy is in flight
     const AnaBorder bd = ana_border<L>(a, k0, l0);
     float fv[kFixRegs];
     if (bd.any) border_prefetch<L>(a, bd, tabs, fv);
-    // this tile's prox state from the slot, then the next tile's requested
-    float yv[2][kAP], xv[2][kAP];
-    if (PROX && rower) {
-      cp_async_wait_all();
-#pragma unroll
-      for (int hb = 0; hb < 2; ++hb) {
-        if (!pxs[hb]) continue;
-#pragma unroll
-        for (int q = 0; q < kAP / 4; ++q) {
-          const float4 y4 = reinterpret_cast<const float4*>(slot + hb * 16)[q];
-          const float4 x4 = reinterpret_cast<const float4*>(slot + hb * 16 + 8)[q];
-          yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
-          xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
-        }
-      }
-      if (t + gridDim.x < a.ntiles) prefetch_prox(t + gridDim.x);
-    }
     bool ok = mbar_wait(&bar[b], (phase >> b) & 1);
     if (ok) {
       phase ^= 1u << b;
@@ -703,10 +714,14 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
     }
     if (!__syncthreads_and(ok)) {
       if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
-      for (int bb = 0; bb < 2; ++bb)
-        if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
-      if (PROX) cp_async_wait_all();
+      drain();
       return;
+    }
+    // every thread is past the previous tile: the other window buffer (whose
+    // staged outputs the bulk stores have read) takes the next tile's copy
+    if (t + gridDim.x < a.ntiles) {
+      if (tid == 0) bulk_wait_read();
+      issue(t + gridDim.x, b ^ 1);
     }
     if (bd.any) border_apply<L>(a, bd, tabs, fv, buf0 + b * G::BUF + a.d_c);
     const float* S = buf0 + b * G::BUF + a.d_c;
@@ -731,8 +746,20 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
         v1[p * G::VP] = hi;
       }
     }
-    __syncthreads();
-    // row pass + store / prox epilogue
+    bool pok = true;
+    if (PROX && tid == 0) pok = mbar_wait(&pbar, pphase & 1);
+    if (!__syncthreads_and(pok)) {
+      if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
+      drain();
+      return;
+    }
+    if (PROX) {
+      pphase ^= 1;
+      ppending = 0;
+    }
+    // outputs staged in this tile's window buffer (the column pass has consumed it)
+    float* D = buf0 + (b ? G::OUT1 : G::OUT0);
+    // row pass + prox epilogue into the staged tiles
     if (rower) {
       const float* src = V + (f * kAR + kk) * G::VP + 2 * kAP * warp;
       float w[G::NW];
@@ -750,47 +777,72 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
         res[0][p] = lo;
         res[1][p] = hi;
       }
-      float* dst[2] = {pick(a.dst, f), pick(a.dst, f + 2)};
       // pad columns (band index >= nc, inside the pitch) are written as zero
 #pragma unroll
       for (int p = 0; p < kAP; ++p)
         if (lbase + p >= a.nc) res[0][p] = res[1][p] = 0.0f;
+      const int o0 = sw_off(kk, kAP * warp), o1 = sw_off(kk, kAP * warp + 4);
 #pragma unroll
       for (int hb = 0; hb < 2; ++hb) {
-        if (!rvalid) break;
-        if (PROX && pxs[hb]) {
+        const int band = f + 2 * hb;
+        if (PROX && a.px[band]) {
+          float* Y = P + 2 * band * kOBand;
+          float* X = Y + kOBand;
+          const float4 y4[2] = {*reinterpret_cast<const float4*>(Y + o0), *reinterpret_cast<const float4*>(Y + o1)};
+          const float4 x4[2] = {*reinterpret_cast<const float4*>(X + o0), *reinterpret_cast<const float4*>(X + o1)};
+          const float yv[kAP] = {y4[0].x, y4[0].y, y4[0].z, y4[0].w, y4[1].x, y4[1].y, y4[1].z, y4[1].w};
+          const float xv[kAP] = {x4[0].x, x4[0].y, x4[0].z, x4[0].w, x4[1].x, x4[1].y, x4[1].z, x4[1].w};
           float xn[kAP], yn[kAP];
 #pragma unroll
           for (int p = 0; p < kAP; ++p) {
-            const float v = yv[hb][p] - a.step * res[hb][p];
+            const float v = yv[p] - a.step * res[hb][p];
             const float mag = fabsf(v) - a.thresh;
             float x = mag > 0.0f ? copysignf(mag, v) : 0.0f;
-            float y = fmaf(beta, x - xv[hb][p], x);
+            float y = fmaf(beta, x - xv[p], x);
             if (lbase + p >= a.nc) x = y = 0.0f;
             xn[p] = x;
             yn[p] = y;
-            if (a.l1) l1 += fabsf(x);
+            if (a.l1 && rvalid) l1 += fabsf(x);
           }
-#pragma unroll
-          for (int q = 0; q < kAP / 4; ++q) {
-            if (lbase + 4 * q + 4 > a.out_pitch) break;
-            reinterpret_cast<float4*>(pxs[hb] + row)[q] =
-                make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
-            reinterpret_cast<float4*>(pys[hb] + row)[q] =
-                make_float4(yn[4 * q], yn[4 * q + 1], yn[4 * q + 2], yn[4 * q + 3]);
-          }
-        } else if (dst[hb]) {
-#pragma unroll
-          for (int q = 0; q < kAP / 4; ++q) {
-            if (lbase + 4 * q + 4 > a.out_pitch) break;
-            reinterpret_cast<float4*>(dst[hb] + row)[q] =
-                make_float4(res[hb][4 * q], res[hb][4 * q + 1], res[hb][4 * q + 2], res[hb][4 * q + 3]);
-          }
+          *reinterpret_cast<float4*>(X + o0) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+          *reinterpret_cast<float4*>(X + o1) = make_float4(xn[4], xn[5], xn[6], xn[7]);
+          *reinterpret_cast<float4*>(Y + o0) = make_float4(yn[0], yn[1], yn[2], yn[3]);
+          *reinterpret_cast<float4*>(Y + o1) = make_float4(yn[4], yn[5], yn[6], yn[7]);
+        } else if (a.dst[band]) {
+          float* Db = D + band * kOBand;
+          *reinterpret_cast<float4*>(Db + o0) = make_float4(res[hb][0], res[hb][1], res[hb][2], res[hb][3]);
+          *reinterpret_cast<float4*>(Db + o1) = make_float4(res[hb][4], res[hb][5], res[hb][6], res[hb][7]);
         }
       }
     }
-    __syncthreads();  // V and this staging buffer are rewritten next
+    fence_proxy_async();  // the staged tiles -> the bulk stores
+    __syncthreads();
+    if (tid == 0) {
+      // rows past the band and columns past the pitch are not written
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool prox = PROX && a.px[i];
+        if (!prox && !a.dst[i]) continue;
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+          if (l0 + 32 * bx >= a.out_pitch) continue;
+          if (prox) {
+            tma_store_2d(&om.m[2 * i], P + 2 * i * kOBand + bx * kOB, l0 + 32 * bx, k0);
+            tma_store_2d(&om.m[2 * i + 1], P + (2 * i + 1) * kOBand + bx * kOB, l0 + 32 * bx, k0);
+          } else {
+            tma_store_2d(&om.m[2 * i], D + i * kOBand + bx * kOB, l0 + 32 * bx, k0);
+          }
+        }
+      }
+      bulk_commit();
+    }
+    // the next tile's prox state goes into P once the stores have read it
+    if (PROX && t + gridDim.x < a.ntiles) {
+      if (tid == 0) bulk_wait_read();
+      issue_prox(t + gridDim.x);
+    }
   }
+  if (tid == 0) bulk_wait_all();  // the staged outputs are in global memory before the CTA exits
   if (a.l1) {
     const double tot = block_sum<kNT>((double)l1, red);
     if (tid == 0) a.l1[blockIdx.x] = tot;
@@ -817,8 +869,8 @@ void ana_range(int N, int n, int T, int mode, int L, bool weighted, int* lo, int
 }
 
 template <int L, bool PROX>
-int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, const char* name, int level,
-                  int* ncta) {
+int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps& om, cudaStream_t s,
+                  const char* name, int level, int* ncta) {
   using G = AG<L>;
   const size_t smem = G::smem_bytes(PROX);
   auto kern = k_ana_tma<L, PROX>;
@@ -831,17 +883,17 @@ int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, c
   }
   const int grid = std::min(a.ntiles, sm_count() * occ);
   *ncta = grid;
-  ADJWT_TRACED(name, level, s, pdl_launch(kern, grid, kNT, smem, s, map, a));
+  ADJWT_TRACED(name, level, s, pdl_launch(kern, grid, kNT, smem, s, map, om, a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
 
 template <int L>
-int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, cudaStream_t s, const char* name, int level,
-                 int* ncta) {
+int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps& om, cudaStream_t s,
+                 const char* name, int level, int* ncta) {
   const bool prox = a.px[0] || a.px[1] || a.px[2] || a.px[3];
-  return prox ? launch_ana_lp<L, true>(a, map, s, name, level, ncta)
-              : launch_ana_lp<L, false>(a, map, s, name, level, ncta);
+  return prox ? launch_ana_lp<L, true>(a, map, om, s, name, level, ncta)
+              : launch_ana_lp<L, false>(a, map, om, s, name, level, ncta);
 }
 
 }  // namespace
@@ -898,13 +950,27 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
     a.flo[t] = flo[t];
     a.fhi[t] = fhi[t];
   }
+  // output bands (and prox state) move as 16 x 32 boxes: band_rows x out_pitch tensors
+  AnaOutMaps om;
+  std::memset(&om, 0, sizeof(om));
+  for (int b = 0; b < 4; ++b) {
+    float* first = px[b] ? py[b] : dst[b];
+    if (first) {
+      int rc = make_tmap_2d_f32_sw(&om.m[2 * b], first, L.ax[0].n, out_pitch, out_pitch, kAR, 32, true);
+      if (rc) return rc;
+    }
+    if (px[b]) {
+      int rc = make_tmap_2d_f32_sw(&om.m[2 * b + 1], px[b], L.ax[0].n, out_pitch, out_pitch, kAR, 32, true);
+      if (rc) return rc;
+    }
+  }
   switch (Lf) {
 #define ADJWT_L(LL)                                                                                        \
   case LL: {                                                                                               \
     CUtensorMap map;                                                                                       \
     int rc = make_tmap_2d_f32(&map, in, L.ax[0].N, L.ax[1].N, in_pitch, AG<LL>::ER, AG<LL>::BC);           \
     if (rc) return rc;                                                                                     \
-    return launch_ana_l<LL>(a, map, s, name, j, ncta);                                                     \
+    return launch_ana_l<LL>(a, map, om, s, name, j, ncta);                                                 \
   }
     ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
 #undef ADJWT_L
