@@ -436,6 +436,9 @@ struct AnaTmaArgs {
   int sh;                 // image index of extended sample e is e - sh
   int d_c;                // window column start minus its 16-byte-aligned start
   int ty0, tx0, ntx, ntiles;
+  // tiles whose window needs no border completion: rows [ir0, ir1), columns
+  // [ic0, ic1) (tile units; nty tile rows).  The others are numbered first.
+  int nty, ir0, ir1, ic0, ic1;
   int out_pitch;
   // border tiles: the level input and its extension (fix = 0 under ZERO,
   // where the box's zero fill is the whole extension)
@@ -644,10 +647,33 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   __syncthreads();
 
   uint32_t phase = 0, pending = 0, pphase = 0, ppending = 0;
+  // Tile t: the border tiles (whose windows need completing, the slow ones)
+  // come first, so that every CTA takes at most one and starts with it; then
+  // the interior tiles row by row.
   auto tile_origin = [&](int t, int& k0, int& l0) {
-    const int ty = t / a.ntx;
+    const int iw = a.ic1 - a.ic0, nb = a.ntiles - iw * (a.ir1 - a.ir0);
+    int ty, tx;
+    if (t >= nb) {
+      const int u = t - nb, q = u / iw;
+      ty = a.ir0 + q;
+      tx = a.ic0 + (u - q * iw);
+    } else {
+      const int ntop = a.ir0 * a.ntx, nbot = (a.nty - a.ir1) * a.ntx;
+      if (t < ntop) {
+        ty = t / a.ntx;
+        tx = t - ty * a.ntx;
+      } else if (t < ntop + nbot) {
+        const int j = t - ntop, q = j / a.ntx;
+        ty = a.ir1 + q;
+        tx = j - q * a.ntx;
+      } else {
+        const int j = t - ntop - nbot, side = a.ic0 + (a.ntx - a.ic1), q = j / side, k = j - q * side;
+        ty = a.ir0 + q;
+        tx = k < a.ic0 ? k : a.ic1 + (k - a.ic0);
+      }
+    }
     k0 = (a.ty0 + ty) * kAR;
-    l0 = (a.tx0 + t - ty * a.ntx) * kAC;
+    l0 = (a.tx0 + tx) * kAC;
   };
   auto issue = [&](int t, int b) {
     int k0, l0;
@@ -923,7 +949,8 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
   a.ty0 = 0;
   a.tx0 = 0;
   a.ntx = (out_pitch + kAC - 1) / kAC;
-  a.ntiles = a.ntx * ((L.ax[0].n + kAR - 1) / kAR);
+  a.nty = (L.ax[0].n + kAR - 1) / kAR;
+  a.ntiles = a.ntx * a.nty;
   a.out_pitch = out_pitch;
   a.in = in;
   a.in_pitch = in_pitch;
@@ -935,6 +962,26 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
   a.fix = p->bc != kZero;
   a.winv_r = adjoint ? L.ax[0].winv : nullptr;
   a.winv_c = adjoint ? L.ax[1].winv : nullptr;
+  // interior tiles per axis: windows [x, x + E) inside [guard, N - guard)
+  // (the test of ana_border; under ZERO without weights every tile)
+  auto interior = [&](int N, int ntile, int T, int E, bool weighted, int* lo, int* hi) {
+    const int guard = weighted ? Lp : 0;
+    *lo = *hi = 0;
+    bool found = false;
+    for (int t = 0; t < ntile; ++t) {
+      const int x = 2 * t * T + 1 - Lp - a.sh;
+      const bool in = (!a.fix && !weighted) || (x >= guard && x + E <= N - guard);
+      if (in && !found) {
+        *lo = t;
+        found = true;
+      }
+      if (in) *hi = t + 1;
+    }
+  };
+  const int ER = 2 * kAR + Lf - 2, EC = 2 * kAC + Lf - 2;
+  interior(a.Nr, a.nty, kAR, ER, a.winv_r != nullptr, &a.ir0, &a.ir1);
+  interior(a.Nc, a.ntx, kAC, EC, a.winv_c != nullptr, &a.ic0, &a.ic1);
+  if (a.ir1 <= a.ir0 || a.ic1 <= a.ic0) a.ir0 = a.ir1 = a.ic0 = a.ic1 = 0;  // no interior tile
   for (int b = 0; b < 4; ++b) {
     a.dst[b] = dst[b];
     a.px[b] = px[b];
