@@ -58,6 +58,7 @@ struct TmaBlurArgs {
   int* status;         // device status word (timeouts)
   int rows, cols, pitch, bc;  // bc: 0 zero, 1 sym, 3 per
   int sym_taps;        // both tap vectors palindromic: R^* needs no orientation flips
+  int ir0, ir1, ic0, ic1;  // tiles whose window stays inside the image (walked after the others)
   float pr[2 * kTmaMaxRadius + 1], pc[2 * kTmaMaxRadius + 1];  // taps as given, padded to 2R+1
 };
 
@@ -247,8 +248,16 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   __syncthreads();
 
   uint32_t phase = 0, pending = 0;  // per buffer: parity of the next wait, copy in flight
+  const int tiles_y = (a.rows + kTH - 1) / kTH;
+  auto origin = [&](int t, int& y0, int& x0) {  // border tiles first (see border_first_tile)
+    int ty, tx;
+    border_first_tile(t, tiles_x, tiles_y, a.ir0, a.ir1, a.ic0, a.ic1, &ty, &tx);
+    y0 = ty * kTH;
+    x0 = tx * kTW;
+  };
   auto issue = [&](int t, int b) {
-    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
+    int y0, x0;
+    origin(t, y0, x0);
     if (tid == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&bar[b], G::BH * G::BW * 4);
@@ -265,7 +274,8 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   int t = blockIdx.x, b = 0;
   if (t < ntiles) issue(t, 0);
   for (; t < ntiles; t += gridDim.x, b ^= 1) {
-    const int ty = t / tiles_x, y0 = ty * kTH, x0 = (t - ty * tiles_x) * kTW;
+    int y0, x0;
+    origin(t, y0, x0);
     if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
     // off-image cells of a border window: fetch them while the copy is in flight
     const bool edge = border(x0, y0);
@@ -340,12 +350,35 @@ int launch_r(const TmaBlurArgs& a, cudaStream_t s, int* nparts) {
   }
   const int ntiles = ((a.cols + kTW - 1) / kTW) * ((a.rows + kTH - 1) / kTH);
   const int grid = std::min(ntiles, sm_count() * occ);
+  // interior tiles: windows inside the image (zero extension: no tile needs completing)
+  TmaBlurArgs b = a;
+  const int tx_n = (a.cols + kTW - 1) / kTW, ty_n = (a.rows + kTH - 1) / kTH;
+  b.ir0 = b.ic0 = 0;
+  b.ir1 = ty_n;
+  b.ic1 = tx_n;
+  if (a.bc != 0) {
+    auto range = [](int n, int T, int lo_halo, int hi_halo, int N, int* lo, int* hi) {
+      *lo = *hi = 0;
+      bool found = false;
+      for (int t = 0; t < n; ++t) {
+        const bool in = t * T - lo_halo >= 0 && t * T + T + hi_halo <= N;
+        if (in && !found) {
+          *lo = t;
+          found = true;
+        }
+        if (in) *hi = t + 1;
+      }
+    };
+    range(ty_n, kTH, R, R, a.rows, &b.ir0, &b.ir1);
+    range(tx_n, kTW, G::XA, G::XA, a.cols, &b.ic0, &b.ic1);
+    if (b.ir1 <= b.ir0 || b.ic1 <= b.ic0) b.ir0 = b.ir1 = b.ic0 = b.ic1 = 0;
+  }
   CUtensorMap map;
   int rc = make_tmap_2d_f32(&map, a.in, a.rows, a.cols, a.pitch, G::BH, G::BW);
   if (rc) return rc;
   if (nparts) *nparts = grid;
   const char* name = ADJ ? "blur_adjoint" : (a.out ? "blur" : "blur_residual");
-  ADJWT_TRACED(name, 0, s, pdl_launch(kern, grid, kPT, smem, s, map, a));
+  ADJWT_TRACED(name, 0, s, pdl_launch(kern, grid, kPT, smem, s, map, b));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }

@@ -42,6 +42,36 @@ __device__ __forceinline__ int ext_src(int x, int N, int mode) {
   return pos_mod(x, N);
 }
 
+// Tile t of an nty x ntx grid in "border first" order: the tiles outside the
+// interior rectangle [ir0, ir1) x [ic0, ic1) come first (the rows above, the
+// rows below, then the columns beside it), then the interior row by row.
+// Persistent kernels whose border tiles cost more walk tiles in this order,
+// so that each CTA takes at most one border tile and starts with it.  An
+// empty rectangle (ir1 <= ir0 or ic1 <= ic0) must be passed as all zeros.
+__device__ __forceinline__ void border_first_tile(int t, int ntx, int nty, int ir0, int ir1, int ic0, int ic1,
+                                                  int* ty, int* tx) {
+  const int iw = ic1 - ic0, nb = ntx * nty - iw * (ir1 - ir0);
+  if (t >= nb) {
+    const int u = t - nb, q = u / iw;
+    *ty = ir0 + q;
+    *tx = ic0 + (u - q * iw);
+    return;
+  }
+  const int ntop = ir0 * ntx, nbot = (nty - ir1) * ntx;
+  if (t < ntop) {
+    *ty = t / ntx;
+    *tx = t - *ty * ntx;
+  } else if (t < ntop + nbot) {
+    const int j = t - ntop, q = j / ntx;
+    *ty = ir1 + q;
+    *tx = j - q * ntx;
+  } else {
+    const int j = t - ntop - nbot, side = ic0 + (ntx - ic1), q = j / side, k = j - q * side;
+    *ty = ir0 + q;
+    *tx = k < ic0 ? k : ic1 + (k - ic0);
+  }
+}
+
 // Block-wide float64 sum; every thread passes its value, thread 0 gets the total.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* scratch /* NT/32 doubles */) {

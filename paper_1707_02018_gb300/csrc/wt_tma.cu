@@ -651,27 +651,8 @@ __global__ void __launch_bounds__(kNT, PROX ? 2 : 3)
   // come first, so that every CTA takes at most one and starts with it; then
   // the interior tiles row by row.
   auto tile_origin = [&](int t, int& k0, int& l0) {
-    const int iw = a.ic1 - a.ic0, nb = a.ntiles - iw * (a.ir1 - a.ir0);
     int ty, tx;
-    if (t >= nb) {
-      const int u = t - nb, q = u / iw;
-      ty = a.ir0 + q;
-      tx = a.ic0 + (u - q * iw);
-    } else {
-      const int ntop = a.ir0 * a.ntx, nbot = (a.nty - a.ir1) * a.ntx;
-      if (t < ntop) {
-        ty = t / a.ntx;
-        tx = t - ty * a.ntx;
-      } else if (t < ntop + nbot) {
-        const int j = t - ntop, q = j / a.ntx;
-        ty = a.ir1 + q;
-        tx = j - q * a.ntx;
-      } else {
-        const int j = t - ntop - nbot, side = a.ic0 + (a.ntx - a.ic1), q = j / side, k = j - q * side;
-        ty = a.ir0 + q;
-        tx = k < a.ic0 ? k : a.ic1 + (k - a.ic0);
-      }
-    }
+    border_first_tile(t, a.ntx, a.nty, a.ir0, a.ir1, a.ic0, a.ic1, &ty, &tx);
     k0 = (a.ty0 + ty) * kAR;
     l0 = (a.tx0 + tx) * kAC;
   };
