@@ -471,6 +471,14 @@ int adjwt_trace_get(int i, const char** name, int* tag, float* ms);
  * record `last` (first <= last, same stream): one multi-kernel call, launch
  * gaps included.  INVALID_ARG for indices outside the records. */
 int adjwt_trace_span(int first, int last, float* ms);
+/* What the armed pool records: level 1 (the default) every kernel; level 2
+ * only whole operator calls, one record each, named "op:wt_synth" (W),
+ * "op:blur_normal" (R^*(R u - b)), "op:wt_adjoint_prox" (W^* with the FISTA
+ * prox, or W^dagger for the variant), "op:momentum" (fista_step_device) and
+ * "op:conv_gradient".  No events then sit between the kernels of one
+ * operator, so programmatic dependent launch overlaps them as it does
+ * untraced.  INVALID_ARG for other levels. */
+int adjwt_trace_set_level(int level);
 
 #ifdef __cplusplus
 }

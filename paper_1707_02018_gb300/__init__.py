@@ -549,6 +549,11 @@ def trace_enable(capacity):
     _lib.check(lib().adjwt_trace_enable(int(capacity)))
 
 
+def trace_level(level):
+    """1: time every kernel (default); 2: time whole operator calls only ("op:..." records)."""
+    _lib.check(lib().adjwt_trace_set_level(int(level)))
+
+
 def trace_reset():
     _lib.check(lib().adjwt_trace_reset())
 

@@ -103,6 +103,7 @@ PROTOTYPES = {
     "adjwt_trace_count": (C.c_int, []),
     "adjwt_trace_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "adjwt_trace_span": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float)]),
+    "adjwt_trace_set_level": (C.c_int, [C.c_int]),
     "adjwt_fp32_fma_peak": (C.c_int, [C.POINTER(C.c_double), VP]),
 }
 

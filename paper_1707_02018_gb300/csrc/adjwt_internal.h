@@ -97,13 +97,20 @@ int make_tmap_2d_f32_sw(CUtensorMap* map, const float* base, int rows, int cols,
 int sm_count();
 
 // ---------------------------------------------------------------- tracing
-int trace_begin(const char* name, int tag, cudaStream_t s);
+int trace_begin(const char* name, int tag, cudaStream_t s);     // level 1: one kernel
+int trace_op_begin(const char* name, int tag, cudaStream_t s);  // level 2: one operator call
 void trace_end(int id, cudaStream_t s);
 #define ADJWT_TRACED(name, tag, stream, ...)                      \
   do {                                                            \
     const int tr_id_ = ::adjwt::trace_begin(name, tag, stream);   \
     __VA_ARGS__;                                                  \
     ::adjwt::trace_end(tr_id_, stream);                           \
+  } while (0)
+#define ADJWT_TRACED_OP(name, tag, stream, ...)                     \
+  do {                                                              \
+    const int tr_op_ = ::adjwt::trace_op_begin(name, tag, stream);  \
+    __VA_ARGS__;                                                    \
+    ::adjwt::trace_end(tr_op_, stream);                             \
   } while (0)
 
 // ---------------------------------------------------------------- filters

@@ -319,8 +319,11 @@ extern "C" int conv_gradient(int batch, int64_t n, int k, const float* s, const 
   rc = check_ws(ws, ws_bytes, need, "conv_gradient");
   if (rc) return rc;
   float* partials = static_cast<float*>(ws);
-  if (conv_fused_supported(k))
-    return launch_conv_fused(batch, n, k, s, h, x, nullptr, r, grad_h, grad_s, partials, stream);
+  if (conv_fused_supported(k)) {
+    ADJWT_TRACED_OP("op:conv_gradient", 0, stream,
+                    rc = launch_conv_fused(batch, n, k, s, h, x, nullptr, r, grad_h, grad_s, partials, stream));
+    return rc;
+  }
   // long channels: residual into r (or the workspace), then the adjoint
   float* rbuf = r ? r : reinterpret_cast<float*>(static_cast<char*>(ws) + adjwt_conv_adjoint_workspace_size(batch, n, k));
   rc = launch_conv_residual(batch, n, k, h, s, x, rbuf, stream);

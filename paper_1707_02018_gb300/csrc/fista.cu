@@ -158,9 +158,10 @@ void fista_momentum(double t, double* t_next, float* beta) {
 int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* ws, double* objective_out,
                     cudaStream_t s) {
   const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
-  int rc = launch_wt_synth(pr->wt, st->y, W.u, W.ll0, W.ll1, s);
+  int rc = 0;
+  ADJWT_TRACED_OP("op:wt_synth", 0, s, rc = launch_wt_synth(pr->wt, st->y, W.u, W.ll0, W.ll1, s));
   if (rc) return rc;
-  rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr);
+  ADJWT_TRACED_OP("op:blur_normal", 0, s, rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr));
   if (rc) return rc;
   double t1 = 0.0;
   float beta = 0.0f;
@@ -173,7 +174,9 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
   prox.beta = beta;
   prox.l1_partials = objective_out ? W.part_a : nullptr;
   int l1_slots = 0;
-  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0, W.ll1, s, &l1_slots);
+  ADJWT_TRACED_OP("op:wt_adjoint_prox", 0, s,
+                  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0,
+                                          W.ll1, s, &l1_slots));
   if (rc) return rc;
   st->t = t1;
   st->k += 1;
@@ -192,11 +195,15 @@ int fista_step_impl(const adjwt_fista_problem* pr, adjwt_fista_state* st, void* 
 int fista_step_device_impl(const adjwt_fista_problem* pr, float* x, float* y, void* ws, double* objective_dev,
                            cudaStream_t s) {
   const FistaWs W = layout_ws(pr, static_cast<char*>(ws));
-  ADJWT_TRACED("momentum", 0, s, pdl_launch(k_momentum, 1, 32, 0, s, W.momentum));
+  cudaError_t me = cudaSuccess;
+  ADJWT_TRACED_OP("op:momentum", 0, s,
+                  ADJWT_TRACED("momentum", 0, s, me = pdl_launch(k_momentum, 1, 32, 0, s, W.momentum)));
+  ADJWT_CUDA_CHECK(me);
   ADJWT_CUDA_CHECK(cudaGetLastError());
-  int rc = launch_wt_synth(pr->wt, y, W.u, W.ll0, W.ll1, s);
+  int rc = 0;
+  ADJWT_TRACED_OP("op:wt_synth", 0, s, rc = launch_wt_synth(pr->wt, y, W.u, W.ll0, W.ll1, s));
   if (rc) return rc;
-  rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr);
+  ADJWT_TRACED_OP("op:blur_normal", 0, s, rc = launch_blur_normal(pr->blur, W.u, pr->b, W.g, nullptr, W.bv, s, nullptr));
   if (rc) return rc;
   ProxArgs prox{};
   prox.x = x;
@@ -206,7 +213,9 @@ int fista_step_device_impl(const adjwt_fista_problem* pr, float* x, float* y, vo
   prox.beta_dev = W.momentum + 1;
   prox.l1_partials = objective_dev ? W.part_a : nullptr;
   int l1_slots = 0;
-  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0, W.ll1, s, &l1_slots);
+  ADJWT_TRACED_OP("op:wt_adjoint_prox", 0, s,
+                  rc = launch_wt_analysis(pr->wt, W.g, nullptr, pr->gradient == ADJWT_GRAD_ADJOINT, prox, W.ll0,
+                                          W.ll1, s, &l1_slots));
   if (rc) return rc;
   if (objective_dev) return objective_async(pr, x, W, true, l1_slots, s, objective_dev);
   return ADJWT_OK;

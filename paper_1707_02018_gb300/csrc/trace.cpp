@@ -1,8 +1,11 @@
-// Optional per-kernel timing.  When armed, every kernel this library launches
-// is bracketed by a pair of CUDA events recorded on the launch stream, so a
-// caller can read each kernel's device time afterwards without a profiler.
-// Disarmed (the default) it costs one branch per launch.  Tracing is meant
-// for one host thread at a time.
+// Optional device timing without a profiler.  When armed at level 1 (the
+// default) every kernel this library launches is bracketed by a pair of CUDA
+// events recorded on the launch stream; at level 2 only whole operator calls
+// of the FISTA step and the channel gradient are (W, R^*(R u - b), W^* with
+// the prox, the momentum update, the channel gradient), so that the events
+// leave the launches inside an operator back to back (programmatic dependent
+// launch overlaps them as in an untraced call).  Disarmed it costs one branch
+// per launch.  Tracing is meant for one host thread at a time.
 #include <vector>
 
 #include "adjwt_internal.h"
@@ -19,17 +22,21 @@ struct Rec {
 std::vector<Rec> g_pool;
 int g_used = 0;
 bool g_on = false;
+int g_level = 1;  // 1: every kernel; 2: whole operator calls
 
-}  // namespace
-
-int trace_begin(const char* name, int tag, cudaStream_t s) {
-  if (!g_on || g_used >= static_cast<int>(g_pool.size())) return -1;
+int record(int level, const char* name, int tag, cudaStream_t s) {
+  if (!g_on || g_level != level || g_used >= static_cast<int>(g_pool.size())) return -1;
   Rec& r = g_pool[g_used];
   r.name = name;
   r.tag = tag;
   if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
   return g_used++;
 }
+
+}  // namespace
+
+int trace_begin(const char* name, int tag, cudaStream_t s) { return record(1, name, tag, s); }
+int trace_op_begin(const char* name, int tag, cudaStream_t s) { return record(2, name, tag, s); }
 
 void trace_end(int id, cudaStream_t s) {
   if (id >= 0) cudaEventRecord(g_pool[id].b, s);
@@ -56,6 +63,12 @@ extern "C" int adjwt_trace_enable(int capacity) {
     ADJWT_CUDA_CHECK(cudaEventCreate(&r.b));
   }
   g_on = true;
+  return ADJWT_OK;
+}
+
+extern "C" int adjwt_trace_set_level(int level) {
+  if (level != 1 && level != 2) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_trace_set_level: level must be 1 or 2");
+  g_level = level;
   return ADJWT_OK;
 }
 

@@ -340,3 +340,12 @@ def test_level_chain_range(lib):
     rc, h = _plan(lib, 64, 64, 2, WAV["db2"], 0)
     assert lib.adjwt_wt_plan_chain_start(h, 3, C.byref(C.c_int())) == -1
     lib.adjwt_wt_plan_destroy(h)
+
+
+def test_trace_level_validation(lib):
+    """adjwt_trace_set_level takes 1 (every kernel) or 2 (whole operator calls)
+    and rejects anything else before any device work."""
+    assert lib.adjwt_trace_set_level(0) == -1
+    assert lib.adjwt_trace_set_level(3) == -1
+    assert lib.adjwt_trace_set_level(2) == 0
+    assert lib.adjwt_trace_set_level(1) == 0
