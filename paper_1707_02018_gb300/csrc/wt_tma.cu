@@ -49,7 +49,13 @@ struct SG {
   static constexpr int BUF = 4 * BAND;               // floats per staging buffer (4 bands)
   static constexpr int NKC = kTW / 2 + L / 2;       // coefficient columns of the column pass (max)
   static constexpr int GP = (NKC + 1) | 1;          // odd pitch of the column-pass output
-  static constexpr size_t smem_bytes() { return 128 + (size_t)(2 * BUF + 2 * kTH * GP) * 4; }
+  // the output tile is staged as four 32 x 32 boxes (128-byte rows, 128-byte
+  // swizzle) in the staging buffer the column pass has consumed, from a
+  // 1024-byte boundary inside it
+  static constexpr int OUT0 = 0;
+  static constexpr int OUT1 = (BUF + 255) / 256 * 256;
+  static_assert(kTH * kTW <= BUF && OUT1 + kTH * kTW <= 2 * BUF, "the staged output tile fits");
+  static constexpr size_t smem_bytes() { return 1024 + (size_t)(2 * BUF + 2 * kTH * GP) * 4; }
 };
 
 struct SynTmaArgs {
@@ -92,12 +98,13 @@ template <int L>
 __global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CUtensorMap m0,
                                                       const __grid_constant__ CUtensorMap m1,
                                                       const __grid_constant__ CUtensorMap m2,
-                                                      const __grid_constant__ CUtensorMap m3, const SynTmaArgs a) {
+                                                      const __grid_constant__ CUtensorMap m3,
+                                                      const __grid_constant__ CUtensorMap mo, const SynTmaArgs a) {
   pdl_entry();
   using G = SG<L>;
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
-  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));
+  float* buf0 = reinterpret_cast<float*>(dyn + ((1024 - (smem_u32(dyn) & 1023)) & 1023));
   float* Gf = buf0 + 2 * G::BUF;  // [2][kTH][GP]
   const int tid = threadIdx.x;
 
@@ -135,7 +142,6 @@ __global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CU
   for (; t < a.ntiles; t += gridDim.x, b ^= 1) {
     int t0r, t0c;
     tile_origin(t, t0r, t0c);
-    if (t + gridDim.x < a.ntiles) issue(t + gridDim.x, b ^ 1);
     // PER: band cells of the box past the band end (zero-filled by the copy)
     // take their circularly wrapped values.  For full tiles the overhang is at
     // most kWrapCols columns and kWrapRows rows (one wrap); the cells are
@@ -177,6 +183,7 @@ __global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CU
       if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
       for (int bb = 0; bb < 2; ++bb)
         if (pending & (1u << bb)) mbar_wait(&bar[bb], (phase >> bb) & 1);
+      if (tid == 0) bulk_wait_all();
       return;
     }
     float* S = buf0 + b * G::BUF;
@@ -215,7 +222,15 @@ __global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CU
       for (int o = 0; o < 2 * kP; ++o) g[o * G::GP] = out[o];
     }
     __syncthreads();
-    // row pass: warp = 16-pixel block, lane = row
+    // the column pass has consumed this staging buffer; the other one (whose
+    // staged output tile the previous tile's bulk stores have read) takes the
+    // next tile's copies
+    if (t + gridDim.x < a.ntiles) {
+      if (tid == 0) bulk_wait_read();
+      issue(t + gridDim.x, b ^ 1);
+    }
+    float* St = buf0 + (b ? G::OUT1 : G::OUT0);
+    // row pass: warp = 16-pixel block, lane = row; results staged for the bulk stores
     {
       const int warp = tid >> 5, r = tid & 31;
       if (warp < kTW / (2 * kP)) {
@@ -231,14 +246,25 @@ __global__ void __launch_bounds__(kNT, 3) k_synth_tma(const __grid_constant__ CU
           pairs<L, 1>(c0, c1, a, out);
         else
           pairs<L, 0>(c0, c1, a, out);
-        float4* dst = reinterpret_cast<float4*>(a.out + (size_t)(t0r + r) * a.out_pitch + t0c + 2 * kP * warp);
+        // 16-byte chunk c of row r of box x/32 at chunk position c xor (r mod 8):
+        // a quarter warp (8 consecutive rows, same chunk) hits 8 distinct bank groups
 #pragma unroll
-        for (int q = 0; q < kP / 2; ++q)
-          dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        for (int q = 0; q < kP / 2; ++q) {
+          const int col = 2 * kP * warp + 4 * q;
+          float* d = St + (col >> 5) * (kTH * 32) + r * 32 + ((((col >> 2) & 7) ^ (r & 7)) << 2);
+          *reinterpret_cast<float4*>(d) = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        }
       }
     }
-    __syncthreads();  // Gf and this staging buffer are rewritten next
+    fence_proxy_async();  // the staged tile -> the bulk stores
+    __syncthreads();      // also: Gf is rewritten next
+    if (tid == 0) {
+#pragma unroll
+      for (int bx = 0; bx < kTW / 32; ++bx) tma_store_2d(&mo, St + bx * (kTH * 32), t0c + 32 * bx, t0r);
+      bulk_commit();
+    }
   }
+  if (tid == 0) bulk_wait_all();  // the output is in global memory before the CTA exits
 }
 
 // Interior tile range [lo, hi) along one axis (tile size T): tiles whose
@@ -274,7 +300,7 @@ void interior_range(int N, int n, int T, int mode, int L, bool weighted, int* lo
 }
 
 template <int L>
-int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[4], cudaStream_t s, int level) {
+int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[5], cudaStream_t s, int level) {
   using G = SG<L>;
   const size_t smem = G::smem_bytes();
   ADJWT_CUDA_CHECK(set_smem(k_synth_tma<L>, smem));
@@ -286,7 +312,7 @@ int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[4], cudaStream_t s, 
   }
   const int grid = std::min(a.ntiles, sm_count() * occ);
   ADJWT_TRACED("wt_synth_tma", level, s,
-               pdl_launch(k_synth_tma<L>, grid, kNT, smem, s, maps[0], maps[1], maps[2], maps[3], a));
+               pdl_launch(k_synth_tma<L>, grid, kNT, smem, s, maps[0], maps[1], maps[2], maps[3], maps[4], a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
@@ -352,12 +378,15 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
   case LL: {                                                                                            \
     if (a.wrap && (last_r + SG<LL>::BR - L.ax[0].n > kWrapRows || last_c + SG<LL>::BC - L.ax[1].n > kWrapCols)) \
       return fail(ADJWT_ERR_SHAPE, "TMA reconstruction: periodic overhang above the staged bound");     \
-    CUtensorMap maps[4];                                                                                \
+    CUtensorMap maps[5];                                                                                \
     for (int b = 0; b < 4; ++b) {                                                                       \
       int rc = make_tmap_2d_f32(&maps[b], band[b], L.ax[0].n, L.ax[1].n, L.band_pitch, SG<LL>::BR,      \
                                 SG<LL>::BC);                                                            \
       if (rc) return rc;                                                                                \
     }                                                                                                   \
+    /* the output: 32 x 32 boxes, 128-byte swizzle */                                                   \
+    int rc = make_tmap_2d_f32_sw(&maps[4], out, L.ax[0].N, out_pitch, out_pitch, kTH, 32, true);        \
+    if (rc) return rc;                                                                                  \
     return launch_l<LL>(a, maps, s, j);                                                                 \
   }
       ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
