@@ -45,8 +45,14 @@ struct TG {
   static constexpr int BUF = up32(BH * BW);   // floats per staging buffer (128-byte multiple)
   static constexpr int VC = kTW + 2 * R;      // columns of the vertical-pass output
   static constexpr int TP = VC | 1;           // odd pitch of T
+  // the output tile is staged as four 32 x 32 boxes (128-byte rows, 128-byte
+  // swizzle) in the staging buffer the vertical pass has consumed, from a
+  // 1024-byte boundary inside it
+  static constexpr int OUT0 = 0;
+  static constexpr int OUT1 = (BUF + 255) / 256 * 256;
+  static_assert(kTH * kTW <= BUF && OUT1 + kTH * kTW <= 2 * BUF, "the staged output tile fits");
   static constexpr size_t smem_bytes() {
-    return 128 + (size_t)(2 * BUF + kTH * TP) * 4 + BH + BW;
+    return 1024 + (size_t)(2 * BUF + kTH * TP) * 4 + BH + BW;
   }
 };
 
@@ -147,7 +153,7 @@ __device__ __forceinline__ void vertical(const float* __restrict__ S, float* __r
 template <int R, bool ADJ, bool FLIP>
 __device__ __forceinline__ void horizontal(const float* __restrict__ T, const TmaBlurArgs& a, int x0, int y0,
                                            const float (&w)[2 * R + 1], const unsigned char* __restrict__ flip_c,
-                                           float& sq) {
+                                           float& sq, float* __restrict__ St) {
   using G = TG<R>;
   constexpr int K = 2 * R + 1, NW = kRB + 2 * R;
   const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
@@ -198,27 +204,28 @@ __device__ __forceinline__ void horizontal(const float* __restrict__ T, const Tm
       if (full || x + o < a.cols) sq = fmaf(acc[o], acc[o], sq);
   }
   if (!a.out) return;
-  float* dst = a.out + (size_t)y * a.pitch + x;
-  if (full) {
+  // staged for the bulk stores (which write only the pixels inside the image):
+  // 16-byte chunk c of row r of box x/32 at chunk position c xor (r mod 8), so
+  // a quarter warp (8 consecutive rows, same chunk) hits 8 distinct bank groups
 #pragma unroll
-    for (int q = 0; q < kRB / 4; ++q)
-      reinterpret_cast<float4*>(dst)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-  } else {
-#pragma unroll
-    for (int o = 0; o < kRB; ++o)
-      if (x + o < a.cols) dst[o] = acc[o];
+  for (int q = 0; q < kRB / 4; ++q) {
+    const int col = kRB * warp + 4 * q;
+    float* d = St + (col >> 5) * (kTH * 32) + r * 32 + ((((col >> 2) & 7) ^ (r & 7)) << 2);
+    *reinterpret_cast<float4*>(d) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
   }
 }
 
 template <int R, bool ADJ>
-__global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid_constant__ CUtensorMap map, const TmaBlurArgs a) {
+__global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid_constant__ CUtensorMap map,
+                                                                           const __grid_constant__ CUtensorMap mo,
+                                                                           const TmaBlurArgs a) {
   pdl_entry();
   using G = TG<R>;
   constexpr int K = 2 * R + 1;
   extern __shared__ unsigned char dyn[];
   __shared__ uint64_t bar[2];
   __shared__ double red[kPT / 32];
-  float* buf0 = reinterpret_cast<float*>(dyn + ((128 - (smem_u32(dyn) & 127)) & 127));  // buffer b at buf0 + b * BUF
+  float* buf0 = reinterpret_cast<float*>(dyn + ((1024 - (smem_u32(dyn) & 1023)) & 1023));  // buffer b at buf0 + b * BUF
   float* T = buf0 + 2 * G::BUF;
   unsigned char* flip_r = reinterpret_cast<unsigned char*>(T + kTH * G::TP);
   unsigned char* flip_c = flip_r + G::BH;
@@ -276,7 +283,6 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   for (; t < ntiles; t += gridDim.x, b ^= 1) {
     int y0, x0;
     origin(t, y0, x0);
-    if (t + gridDim.x < ntiles) issue(t + gridDim.x, b ^ 1);
     // off-image cells of a border window: fetch them while the copy is in flight
     const bool edge = border(x0, y0);
     const bool fill = edge && a.bc != 0;
@@ -300,6 +306,7 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
     if (!__syncthreads_and(ok)) {
       if (tid == 0) record_status(a.status, ADJWT_ERR_TIMEOUT);
       drain();
+      if (tid == 0) bulk_wait_all();
       return;
     }
     float* S = buf0 + b * G::BUF;
@@ -315,6 +322,16 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
       }
       __syncthreads();
     }
+    // the vertical pass consumes this staging buffer; the other one (whose
+    // staged output tile the previous tile's bulk stores have read) then
+    // takes the next tile's copy
+    auto next = [&]() {
+      if (t + gridDim.x < ntiles) {
+        if (tid == 0) bulk_wait_read();
+        issue(t + gridDim.x, b ^ 1);
+      }
+    };
+    float* St = buf0 + (b ? G::OUT1 : G::OUT0);
     const bool flip = ADJ && sym && edge && !a.sym_taps;
     if (flip) {
       for (int i = tid; i < G::BH; i += kPT) flip_r[i] = odd_period(y0 - R + i, a.rows);
@@ -322,14 +339,25 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
       __syncthreads();
       vertical<R, true>(S, T, wr, flip_r);
       __syncthreads();
-      horizontal<R, ADJ, true>(T, a, x0, y0, wc, flip_c, sq);
+      next();
+      horizontal<R, ADJ, true>(T, a, x0, y0, wc, flip_c, sq, St);
     } else {
       vertical<R, false>(S, T, wr, nullptr);
       __syncthreads();
-      horizontal<R, ADJ, false>(T, a, x0, y0, wc, nullptr, sq);
+      next();
+      horizontal<R, ADJ, false>(T, a, x0, y0, wc, nullptr, sq, St);
     }
-    __syncthreads();  // T and this staging buffer are rewritten next
+    fence_proxy_async();  // the staged tile -> the bulk stores
+    __syncthreads();      // also: T is rewritten next
+    if (a.out && tid == 0) {
+      // boxes wholly past the last column are skipped; the others are clipped to the image
+#pragma unroll
+      for (int bx = 0; bx < kTW / 32; ++bx)
+        if (x0 + 32 * bx < a.cols) tma_store_2d(&mo, St + bx * (kTH * 32), x0 + 32 * bx, y0);
+      bulk_commit();
+    }
   }
+  if (tid == 0) bulk_wait_all();  // the output is in global memory before the CTA exits
   if (!ADJ && a.partials) {
     const double tot = block_sum<kPT>((double)sq, red);
     if (tid == 0) a.partials[blockIdx.x] = 0.5 * tot;
@@ -373,12 +401,17 @@ int launch_r(const TmaBlurArgs& a, cudaStream_t s, int* nparts) {
     range(tx_n, kTW, G::XA, G::XA, a.cols, &b.ic0, &b.ic1);
     if (b.ir1 <= b.ir0 || b.ic1 <= b.ic0) b.ir0 = b.ir1 = b.ic0 = b.ic1 = 0;
   }
-  CUtensorMap map;
+  CUtensorMap map, mo;
   int rc = make_tmap_2d_f32(&map, a.in, a.rows, a.cols, a.pitch, G::BH, G::BW);
   if (rc) return rc;
+  mo = map;
+  if (a.out) {  // the output: 32 x 32 boxes, 128-byte swizzle, clipped to rows x cols
+    rc = make_tmap_2d_f32_sw(&mo, a.out, a.rows, a.cols, a.pitch, kTH, 32, true);
+    if (rc) return rc;
+  }
   if (nparts) *nparts = grid;
   const char* name = ADJ ? "blur_adjoint" : (a.out ? "blur" : "blur_residual");
-  ADJWT_TRACED(name, 0, s, pdl_launch(kern, grid, kPT, smem, s, map, b));
+  ADJWT_TRACED(name, 0, s, pdl_launch(kern, grid, kPT, smem, s, map, mo, b));
   ADJWT_CUDA_CHECK(cudaGetLastError());
   return ADJWT_OK;
 }
