@@ -16,7 +16,11 @@
 // Per tile: a vertical pass (a thread filters 16 rows of one column from a
 // register window, lanes on consecutive columns) writes an odd-pitch buffer
 // T; a horizontal pass (lanes on the 32 rows, a warp per 16-column block)
-// produces 16 consecutive outputs per thread and stores them as float4.
+// produces 16 consecutive outputs per thread into the output tile, staged as
+// four 32 x 32 boxes under the 128-byte swizzle in the staging buffer the
+// vertical pass has consumed; one thread writes them with TMA stores clipped
+// to the image.  Border tiles (whose windows are completed by the threads)
+// are walked first (border_first_tile).
 #include <algorithm>
 
 #include "adjwt_internal.h"

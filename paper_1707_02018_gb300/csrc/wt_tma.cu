@@ -17,7 +17,11 @@
 //                16 consecutive rows of one coefficient column from a
 //                register window (lanes on consecutive columns);
 //   row pass:    a thread makes 16 consecutive pixels of one row (lanes on
-//                rows, odd pitch) and stores them as float4.
+//                rows, odd pitch) into the output tile, staged as four
+//                32 x 32 boxes under the 128-byte swizzle in the staging
+//                buffer the column pass has consumed; one thread then writes
+//                them with TMA stores, and the next tile's copy goes into the
+//                other buffer once the stores of the tile before have read it.
 #include <algorithm>
 #include <cstring>
 
@@ -402,8 +406,8 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 // Persistent TMA-staged W^* (+ the FISTA prox) / W^dagger for every tile of
 // a level.  The TMA unit's zero fill is the zero extension; a border tile's
 // window is completed after the copy from the extension map and the 1/c
-// weights (border_prefetch / border_apply), and the last row / column tiles store only inside
-// the bands (pad columns as zero).
+// weights (border_prefetch / border_apply); border tiles are walked first
+// (border_first_tile), so that no CTA takes two of them.
 // A tile is kAR x kAC coefficients of each band; its input window is
 // (2 kAR + L - 2) x (2 kAC + L - 2) samples of the extended signal, staged by
 // the TMA unit into one of two buffers while the previous tile is filtered:
@@ -411,9 +415,12 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
 //                with both analysis filters from a register window;
 //   row pass:    lanes on (vertical filter, coefficient row), a warp per
 //                8-coefficient block; both horizontal filters, then the
-//                plain store or the prox epilogue (float4 stores), whose
-//                state x, y each thread copied with cp.async into its own
-//                shared-memory slot one tile earlier.
+//                plain result or the prox epilogue.  Every output band tile
+//                (16 x 64) is staged as two 16 x 32 boxes under the 128-byte
+//                swizzle and written by TMA stores (rows past the band and
+//                columns past the pitch are clipped; pad columns are staged
+//                as zero); the prox state y, x of the tile comes in the same
+//                way, one tile ahead, and is updated in place.
 namespace {
 
 constexpr int kAR = 16;    // coefficient rows per tile
