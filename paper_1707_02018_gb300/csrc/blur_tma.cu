@@ -219,7 +219,10 @@ __device__ __forceinline__ void horizontal(const float* __restrict__ T, const Tm
   }
 }
 
-template <int R, bool ADJ>
+// FLIPS: R^* of a symmetric image with taps that are not palindromic, the one
+// case that needs the orientation-aware taps at border tiles; the other
+// instantiations carry no code for them (a smaller loop body).
+template <int R, bool ADJ, bool FLIPS>
 __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid_constant__ CUtensorMap map,
                                                                            const __grid_constant__ CUtensorMap mo,
                                                                            const TmaBlurArgs a) {
@@ -238,7 +241,6 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   const int tiles_x = (a.cols + kTW - 1) / kTW;
   const int ntiles = tiles_x * ((a.rows + kTH - 1) / kTH);
   const int mode = a.bc == 3 ? 2 : a.bc;
-  const bool sym = a.bc == 1;
   // taps: R is a convolution (reversed taps), R^* a correlation (taps as given)
   float wr[K], wc[K];
 #pragma unroll
@@ -336,8 +338,9 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
       }
     };
     float* St = buf0 + (b ? G::OUT1 : G::OUT0);
-    const bool flip = ADJ && sym && edge && !a.sym_taps;
-    if (flip) {
+    const bool flip = FLIPS && edge;
+    if constexpr (FLIPS) {
+      if (flip) {
       for (int i = tid; i < G::BH; i += kPT) flip_r[i] = odd_period(y0 - R + i, a.rows);
       for (int i = tid; i < G::VC; i += kPT) flip_c[i] = odd_period(x0 - R + i, a.cols);
       __syncthreads();
@@ -345,7 +348,9 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
       __syncthreads();
       next();
       horizontal<R, ADJ, true>(T, a, x0, y0, wc, flip_c, sq, St);
-    } else {
+      }
+    }
+    if (!flip) {
       vertical<R, false>(S, T, wr, nullptr);
       __syncthreads();
       next();
@@ -368,11 +373,12 @@ __global__ void __launch_bounds__(kPT, (R <= 8 ? 3 : 2)) k_blur_tma(const __grid
   }
 }
 
-template <int R, bool ADJ>
+template <int R, bool ADJ, bool FLIPS = false>
 int launch_r(const TmaBlurArgs& a, cudaStream_t s, int* nparts) {
+  if (ADJ && !FLIPS && a.bc == 1 && !a.sym_taps) return launch_r<R, true, true>(a, s, nparts);
   using G = TG<R>;
   const size_t smem = G::smem_bytes();
-  auto kern = k_blur_tma<R, ADJ>;
+  auto kern = k_blur_tma<R, ADJ, FLIPS>;
   ADJWT_CUDA_CHECK(set_smem(kern, smem));
   static int occ = 0;  // resident CTAs per SM (same on every device of one process)
   if (!occ) {
