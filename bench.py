@@ -1046,7 +1046,8 @@ def ours(args):
                        "issue": ("CUDA graph of the step (three fista_step_device lanes + conv_gradient), "
                                  "replayed once per step" if graph is not None else "call by call on four streams"),
                        "bytes_per_step": bytes_step,
-                       "level_kernels": {pr["bc"]: {"tma": pr["wt"].tma_levels(), "autotuned": AUTOTUNE}
+                       "level_kernels": {pr["bc"]: {"tma": pr["wt"].tma_levels(), "tma_ctas": pr["wt"].tma_ctas(),
+                                                    "autotuned": AUTOTUNE}
                                          for pr in probs}},
             "roofline": roof, "hbm_rooflines": hbm_roofs, "kernels": kernels,
             "fp32_fma_peak_tflops": fma_tflops, "h2d_pinned_copy": h2d_rate,

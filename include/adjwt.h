@@ -142,19 +142,28 @@ int wt_analysis(const adjwt_wt_plan* plan, const float* image, float* coeffs, vo
  * within float32 rounding either way.  adjwt_wt_plan_set_tma(plan, op,
  * level, 0) forces the tiled kernel for that level, 1 restores the rule;
  * adjwt_wt_plan_uses_tma reports whether the TMA kernel runs there.
+ * adjwt_wt_plan_set_tma_ctas(plan, op, level, c) caps the persistent TMA
+ * kernel of that level at c resident CTAs per SM (c = 1..3; 0, the default:
+ * as many as fit), which trades latency hiding for longer per-CTA copy
+ * pipelines; adjwt_wt_plan_tma_ctas reads the setting.
  * adjwt_wt_plan_autotune measures: for every level the rule makes eligible
  * it times `reps` whole transforms (W, W^*, then W^* with the prox on
- * scratch iterates) with the level one way and the other, keeps the tiled
- * kernel only if it is at least 3 % faster, and stores the choices for the
- * plan's size class (rows, cols, levels, wavelet, boundary, current device);
+ * scratch iterates) with the level on each of four candidates (the tiled
+ * kernel alone; the TMA kernel with as many CTAs per SM as fit, with one,
+ * with two), keeps another candidate than the default (the TMA kernel, as
+ * many CTAs as fit) only if it is at least 3 % faster, and stores the
+ * choices for the plan's size class (rows, cols, levels, wavelet, boundary,
+ * current device);
  * plans created later for that class start from them, and autotuning such a
  * class again only applies them (*from_cache = 1; from_cache may be NULL).
  * It allocates and frees its own device buffers and synchronises the
  * stream.  These calls change the plan: make them before the plan is used
  * on other streams.  Errors: INVALID_ARG (op outside 0..2, reps outside
- * 1..1000), SHAPE (level outside 1..levels), CUDA. */
+ * 1..1000, ctas outside 0..3, NULL), SHAPE (level outside 1..levels), CUDA. */
 int adjwt_wt_plan_set_tma(adjwt_wt_plan* plan, int op, int level, int enabled);
 int adjwt_wt_plan_uses_tma(const adjwt_wt_plan* plan, int op, int level, int* uses);
+int adjwt_wt_plan_set_tma_ctas(adjwt_wt_plan* plan, int op, int level, int ctas);
+int adjwt_wt_plan_tma_ctas(const adjwt_wt_plan* plan, int op, int level, int* ctas);
 int adjwt_wt_plan_autotune(adjwt_wt_plan* plan, int reps, int* from_cache, adjwt_stream_t stream);
 
 /* Level chain (no counterpart in the paper: a launch schedule).  The deepest

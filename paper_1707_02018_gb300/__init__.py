@@ -90,6 +90,22 @@ class WtPlan:
         (enabled) or on the tiled kernel alone."""
         _lib.check(lib().adjwt_wt_plan_set_tma(self._h, self.LEVEL_OPS[op], int(level), int(enabled)))
 
+    def set_tma_ctas(self, op, level, ctas):
+        """Cap the TMA kernel of `level` at `ctas` resident CTAs per SM (1..3; 0 = as many as fit)."""
+        _lib.check(lib().adjwt_wt_plan_set_tma_ctas(self._h, self.LEVEL_OPS[op], int(level), int(ctas)))
+
+    def tma_ctas(self):
+        """{"synth", "analysis", "prox": [...]}: per level 1..J, the CTA cap of the TMA kernel (0 = none)."""
+        out = {}
+        for name, op in self.LEVEL_OPS.items():
+            v = C.c_int()
+            row = []
+            for j in range(1, self.levels + 1):
+                _lib.check(lib().adjwt_wt_plan_tma_ctas(self._h, op, j, C.byref(v)))
+                row.append(v.value)
+            out[name] = row
+        return out
+
     def tma_levels(self):
         """{"synth", "analysis", "prox": [...]}: per level 1..J, whether the TMA kernel runs."""
         out = {}
@@ -117,8 +133,9 @@ class WtPlan:
         return out
 
     def autotune(self, reps=5, stream=None):
-        """Measure the TMA / tiled choice per level (see include/adjwt.h); True
-        if the choices came from an earlier tuning of the same size class."""
+        """Measure each level's implementation (tiled kernel, or TMA kernel with
+        as many CTAs per SM as fit, one or two; see include/adjwt.h); True if
+        the choices came from an earlier tuning of the same size class."""
         fc = C.c_int()
         _lib.check(lib().adjwt_wt_plan_autotune(self._h, int(reps), C.byref(fc), _stream(stream)))
         return bool(fc.value)

@@ -72,6 +72,8 @@ PROTOTYPES = {
     "adjwt_fista_batch_info": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "adjwt_wt_plan_set_tma": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
     "adjwt_wt_plan_uses_tma": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "adjwt_wt_plan_set_tma_ctas": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
+    "adjwt_wt_plan_tma_ctas": (C.c_int, [VP, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "adjwt_wt_plan_set_level_chain": (C.c_int, [VP, C.c_int]),
     "adjwt_wt_plan_chain_start": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int)]),
     "adjwt_wt_plan_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int), VP]),

@@ -154,6 +154,9 @@ struct adjwt_wt_plan {
   // TMA kernel takes the tiles the size rule gives it (set by
   // adjwt_wt_plan_set_tma / adjwt_wt_plan_autotune)
   unsigned char tma_off[3][adjwt::kMaxLevels] = {};
+  // resident CTAs per SM of the persistent TMA kernel per operator and level
+  // (0: as many as fit); the autotuner's second axis
+  unsigned char tma_ctas[3][adjwt::kMaxLevels] = {};
   // the deepest run of tiled-only levels runs as one level-chain launch only
   // when switched on (adjwt_wt_plan_set_level_chain); off by default
   bool chain_off = true;

@@ -1,13 +1,18 @@
-// Per-level choice between the two implementations of a wavelet level: the
-// persistent TMA-staged kernels (which take the tiles a size rule gives them,
-// the tiled kernel doing the rest) and the tiled kernels alone, separately
-// for W, for W^* (and W^dagger), and for W^* with the FISTA prox epilogue
-// (a different kernel: it also reads and writes the iterate).  The choice is
-// measured: adjwt_wt_plan_autotune times whole transforms with each eligible
-// level switched one way and the other (greedy, level by level, the other
-// levels at their current setting) and keeps the faster, then stores the
-// result for the plan's size class (rows, cols, levels, wavelet, boundary,
-// device), which every plan created later for that class applies.
+// Per-level choice of how a wavelet level runs, separately for W, for W^*
+// (and W^dagger), and for W^* with the FISTA prox epilogue (a different
+// kernel: it also reads and writes the iterate).  The candidates form a small
+// grid over tile shape and pipeline: the tiled kernels alone (32 x 32 output
+// tiles, one tile per CTA, no copy pipeline), or the persistent TMA-staged
+// kernels (32 x 128 output tiles for W, 16 x 64 coefficient tiles for W^*,
+// the next tile's copy in flight) with as many resident CTAs per SM as fit,
+// or with one or two (more tiles per CTA go through its pipeline, fewer CTAs
+// hide each other's latency).  The choice is measured: adjwt_wt_plan_autotune
+// times whole transforms with each eligible level set to each candidate
+// (greedy, level by level, the other levels at their current setting) and
+// keeps the fastest (the default, the TMA kernel with as many CTAs as fit,
+// unless another candidate wins by 3 %), then stores the result for the
+// plan's size class (rows, cols, levels, wavelet, boundary, device), which
+// every plan created later for that class applies.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -23,6 +28,7 @@ using Key = std::tuple<int, int, int, int, int, int>;  // device, rows, cols, le
 constexpr int kOps = 3;  // W, W^* / W^dagger, W^* with the prox epilogue
 struct Choice {
   unsigned char off[kOps][kMaxLevels];
+  unsigned char ctas[kOps][kMaxLevels];
 };
 std::mutex g_mu;
 std::map<Key, Choice> g_cache;
@@ -75,7 +81,10 @@ void apply_tuning_cache(adjwt_wt_plan* p) {
   auto it = g_cache.find(k);
   if (it == g_cache.end()) return;
   for (int op = 0; op < kOps; ++op)
-    for (int j = 0; j < kMaxLevels; ++j) p->tma_off[op][j] = it->second.off[op][j];
+    for (int j = 0; j < kMaxLevels; ++j) {
+      p->tma_off[op][j] = it->second.off[op][j];
+      p->tma_ctas[op][j] = it->second.ctas[op][j];
+    }
 }
 
 }  // namespace adjwt
@@ -95,6 +104,23 @@ extern "C" int adjwt_wt_plan_uses_tma(const adjwt_wt_plan* p, int op, int level,
   if (op < 0 || op >= kOps) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_uses_tma: op must be 0, 1 or 2");
   if (level < 1 || level > p->levels) return fail(ADJWT_ERR_SHAPE, "adjwt_wt_plan_uses_tma: level out of range");
   *uses = adjwt::uses(p, op, level) ? 1 : 0;
+  return ADJWT_OK;
+}
+
+extern "C" int adjwt_wt_plan_set_tma_ctas(adjwt_wt_plan* p, int op, int level, int ctas) {
+  if (!p) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_set_tma_ctas: plan is NULL");
+  if (op < 0 || op >= kOps) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_set_tma_ctas: op must be 0, 1 or 2");
+  if (level < 1 || level > p->levels) return fail(ADJWT_ERR_SHAPE, "adjwt_wt_plan_set_tma_ctas: level out of range");
+  if (ctas < 0 || ctas > 3) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_set_tma_ctas: ctas must be 0..3");
+  p->tma_ctas[op][level - 1] = static_cast<unsigned char>(ctas);
+  return ADJWT_OK;
+}
+
+extern "C" int adjwt_wt_plan_tma_ctas(const adjwt_wt_plan* p, int op, int level, int* ctas) {
+  if (!p || !ctas) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_tma_ctas: NULL argument");
+  if (op < 0 || op >= kOps) return fail(ADJWT_ERR_INVALID_ARG, "adjwt_wt_plan_tma_ctas: op must be 0, 1 or 2");
+  if (level < 1 || level > p->levels) return fail(ADJWT_ERR_SHAPE, "adjwt_wt_plan_tma_ctas: level out of range");
+  *ctas = p->tma_ctas[op][level - 1];
   return ADJWT_OK;
 }
 
@@ -171,26 +197,32 @@ extern "C" int adjwt_wt_plan_autotune(adjwt_wt_plan* p, int reps, int* from_cach
     ADJWT_CUDA_CHECK(cudaEventElapsedTime(ms, d.e0, d.e1));
     return ADJWT_OK;
   };
+  // candidates: (tiled only) and (TMA kernel, CTAs per SM: as many as fit, 1, 2)
+  constexpr int kCand = 4;
+  const unsigned char cand_off[kCand] = {0, 1, 0, 0}, cand_ctas[kCand] = {0, 0, 1, 2};
   for (int op = 0; op < kOps; ++op)
     for (int j = 1; j <= p->levels; ++j) {
       if (!eligible(p, op, j)) continue;
-      float on = 0.0f, off = 0.0f;
-      p->tma_off[op][j - 1] = 0;
-      int rc = time_op(op, &on);
-      if (!rc) {
-        p->tma_off[op][j - 1] = 1;
-        rc = time_op(op, &off);
+      float ms[kCand] = {};
+      int rc = ADJWT_OK;
+      for (int c = 0; c < kCand && !rc; ++c) {
+        p->tma_off[op][j - 1] = cand_off[c];
+        p->tma_ctas[op][j - 1] = cand_ctas[c];
+        rc = time_op(op, &ms[c]);
       }
-      if (rc) {
-        p->tma_off[op][j - 1] = 0;
-        return rc;
-      }
-      // the tiled kernel must win by 3 %: timing noise keeps the TMA kernel
-      p->tma_off[op][j - 1] = off < 0.97f * on ? 1 : 0;
+      int best = 0;  // the default must be beaten by 3 %: timing noise keeps it
+      for (int c = 1; c < kCand && !rc; ++c)
+        if (ms[c] < 0.97f * ms[0] && ms[c] < ms[best]) best = c;
+      p->tma_off[op][j - 1] = rc ? 0 : cand_off[best];
+      p->tma_ctas[op][j - 1] = rc ? 0 : cand_ctas[best];
+      if (rc) return rc;
     }
   Choice c{};
   for (int op = 0; op < kOps; ++op)
-    for (int j = 0; j < kMaxLevels; ++j) c.off[op][j] = p->tma_off[op][j];
+    for (int j = 0; j < kMaxLevels; ++j) {
+      c.off[op][j] = p->tma_off[op][j];
+      c.ctas[op][j] = p->tma_ctas[op][j];
+    }
   std::lock_guard<std::mutex> lock(g_mu);
   g_cache[key] = c;
   return ADJWT_OK;

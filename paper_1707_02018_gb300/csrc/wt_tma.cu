@@ -304,7 +304,7 @@ void interior_range(int N, int n, int T, int mode, int L, bool weighted, int* lo
 }
 
 template <int L>
-int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[5], cudaStream_t s, int level) {
+int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[5], cudaStream_t s, int level, int ctas) {
   using G = SG<L>;
   const size_t smem = G::smem_bytes();
   ADJWT_CUDA_CHECK(set_smem(k_synth_tma<L>, smem));
@@ -314,7 +314,7 @@ int launch_l(const SynTmaArgs& a, const CUtensorMap (&maps)[5], cudaStream_t s, 
     ADJWT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_synth_tma<L>, kNT, smem));
     occ = std::max(v, 1);
   }
-  const int grid = std::min(a.ntiles, sm_count() * occ);
+  const int grid = std::min(a.ntiles, sm_count() * (ctas > 0 ? std::min(ctas, occ) : occ));
   ADJWT_TRACED("wt_synth_tma", level, s,
                pdl_launch(k_synth_tma<L>, grid, kNT, smem, s, maps[0], maps[1], maps[2], maps[3], maps[4], a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
@@ -391,7 +391,7 @@ int launch_synth_tma(const adjwt_wt_plan* p, int j, const float* const band[4], 
     /* the output: 32 x 32 boxes, 128-byte swizzle */                                                   \
     int rc = make_tmap_2d_f32_sw(&maps[4], out, L.ax[0].N, out_pitch, out_pitch, kTH, 32, true);        \
     if (rc) return rc;                                                                                  \
-    return launch_l<LL>(a, maps, s, j);                                                                 \
+    return launch_l<LL>(a, maps, s, j, p->tma_ctas[0][j - 1]);                                          \
   }
       ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
 #undef ADJWT_L
@@ -916,7 +916,7 @@ void ana_range(int N, int n, int T, int mode, int L, bool weighted, int* lo, int
 
 template <int L, bool PROX>
 int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps& om, cudaStream_t s,
-                  const char* name, int level, int* ncta) {
+                  const char* name, int level, int ctas, int* ncta) {
   using G = AG<L>;
   const size_t smem = G::smem_bytes(PROX);
   auto kern = k_ana_tma<L, PROX>;
@@ -927,7 +927,7 @@ int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps&
     ADJWT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kNT, smem));
     occ = std::max(v, 1);
   }
-  const int grid = std::min(a.ntiles, sm_count() * occ);
+  const int grid = std::min(a.ntiles, sm_count() * (ctas > 0 ? std::min(ctas, occ) : occ));
   *ncta = grid;
   ADJWT_TRACED(name, level, s, pdl_launch(kern, grid, kNT, smem, s, map, om, a));
   ADJWT_CUDA_CHECK(cudaGetLastError());
@@ -936,10 +936,10 @@ int launch_ana_lp(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps&
 
 template <int L>
 int launch_ana_l(const AnaTmaArgs& a, const CUtensorMap& map, const AnaOutMaps& om, cudaStream_t s,
-                 const char* name, int level, int* ncta) {
+                 const char* name, int level, int ctas, int* ncta) {
   const bool prox = a.px[0] || a.px[1] || a.px[2] || a.px[3];
-  return prox ? launch_ana_lp<L, true>(a, map, om, s, name, level, ncta)
-              : launch_ana_lp<L, false>(a, map, om, s, name, level, ncta);
+  return prox ? launch_ana_lp<L, true>(a, map, om, s, name, level, ctas, ncta)
+              : launch_ana_lp<L, false>(a, map, om, s, name, level, ctas, ncta);
 }
 
 }  // namespace
@@ -1037,7 +1037,7 @@ int launch_ana_tma(const adjwt_wt_plan* p, int j, bool adjoint, const float* in,
     CUtensorMap map;                                                                                       \
     int rc = make_tmap_2d_f32(&map, in, L.ax[0].N, L.ax[1].N, in_pitch, AG<LL>::ER, AG<LL>::BC);           \
     if (rc) return rc;                                                                                     \
-    return launch_ana_l<LL>(a, map, om, s, name, j, ncta);                                                 \
+    return launch_ana_l<LL>(a, map, om, s, name, j, p->tma_ctas[px[1] ? 2 : 1][j - 1], ncta);              \
   }
     ADJWT_L(2) ADJWT_L(4) ADJWT_L(8) ADJWT_L(10)
 #undef ADJWT_L

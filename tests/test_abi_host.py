@@ -349,3 +349,21 @@ def test_trace_level_validation(lib):
     assert lib.adjwt_trace_set_level(3) == -1
     assert lib.adjwt_trace_set_level(2) == 0
     assert lib.adjwt_trace_set_level(1) == 0
+
+
+def test_tma_cta_cap_validation(lib):
+    """adjwt_wt_plan_set_tma_ctas / adjwt_wt_plan_tma_ctas: caps 0..3 per op and
+    level are stored and read back; bad op, level or cap are rejected on the host."""
+    rc, h = _plan(lib, 64, 64, 3, WAV["db2"], 3)   # PER: no boundary tables to upload
+    assert rc == 0
+    try:
+        v = C.c_int(-1)
+        assert lib.adjwt_wt_plan_tma_ctas(h, 2, 1, C.byref(v)) == 0 and v.value == 0
+        assert lib.adjwt_wt_plan_set_tma_ctas(h, 2, 1, 1) == 0
+        assert lib.adjwt_wt_plan_tma_ctas(h, 2, 1, C.byref(v)) == 0 and v.value == 1
+        assert lib.adjwt_wt_plan_set_tma_ctas(h, 3, 1, 1) == -1       # op
+        assert lib.adjwt_wt_plan_set_tma_ctas(h, 0, 4, 1) == -2       # level (SHAPE)
+        assert lib.adjwt_wt_plan_set_tma_ctas(h, 0, 1, 4) == -1       # cap
+        assert lib.adjwt_wt_plan_tma_ctas(h, 0, 1, None) == -1
+    finally:
+        lib.adjwt_wt_plan_destroy(h)

@@ -111,11 +111,47 @@ def test_autotune_and_its_cache(adj):
     img = random_vector((rows, cols), 29)
     got = adj.wt_synth_adjoint(plan, image_dev(plan, img))
     assert_close(plan.unpack(got).cpu().numpy(), owt.wt_adjoint(img, J, w, mode), what="W^* after autotune")
+    caps = plan.tma_ctas()
     again = adj.WtPlan(rows, cols, J, w, mode)
     assert again.tma_levels() == chosen        # applied at creation
+    assert again.tma_ctas() == caps
     assert again.autotune(reps=3) is True      # and not measured again
     assert again.tma_levels() == chosen
-    print("\nautotune 1600x1664 J3 cdf97 sym:", chosen)
+    print("\nautotune 1600x1664 J3 cdf97 sym:", chosen, caps)
+
+
+@pytest.mark.parametrize("mode", ["sym", "per"])
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_tma_cta_cap_gives_the_same_operators(adj, mode, ctas):
+    """The TMA kernels capped at 1 or 2 resident CTAs per SM (every CTA then
+    walks more tiles through its copy pipeline) give bit-identical W, W^* and
+    FISTA iterates with the prox epilogue (each tile's arithmetic does not
+    depend on which CTA runs it; the default path is held to the oracle by
+    the tests above)."""
+    from oracle import blur as oblur
+    rows, cols, J, w = 2048, 2048, 3, "cdf97"
+    plan = adj.WtPlan(rows, cols, J, w, mode)
+    assert plan.tma_levels()["synth"][0] and plan.tma_levels()["prox"][0]
+    x = plan.pack(random_vector(plan.logical_size, 31))
+    img = image_dev(plan, random_vector((rows, cols), 37))
+    p = oblur.gaussian_psf(9, 1.5)
+    bl = adj.BlurPlan(rows, cols, p, p, mode)
+    b = image_dev(plan, piecewise_smooth_image(rows, cols, 41))
+
+    def run():
+        f = adj.Fista(plan, bl, b, 1e-3, 1.0)
+        f.step()
+        f.step()
+        return adj.wt_synth(plan, x).clone(), adj.wt_synth_adjoint(plan, img).clone(), f.x.clone()
+
+    want = run()
+    for op in ("synth", "analysis", "prox"):
+        plan.set_tma_ctas(op, 1, ctas)
+    assert plan.tma_ctas()["prox"][0] == ctas
+    got = run()
+    for g_, w_, what in zip(got, want, ("W", "W^*", "FISTA x_2")):
+        assert torch.equal(g_, w_), what
+    assert adj.device_status() == 0
 
 
 @pytest.mark.parametrize("mode", ["sym", "per", "zero"])
