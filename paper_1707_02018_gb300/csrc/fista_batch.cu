@@ -34,6 +34,7 @@
 
 #include "adjwt_internal.h"
 #include "blur_tile.cuh"
+#include "blur_window_tile.cuh"
 #include "device_common.cuh"
 #include "tma.cuh"
 #include "wt_tiles.cuh"
@@ -44,20 +45,30 @@ namespace {
 constexpr int kEngineThreads = 256;
 constexpr int kEngineMaxRadius = 12;
 
-enum StageKind : int { kMom = 0, kSyn = 1, kBlur = 2, kAna = 3, kSum = 4, kL1 = 5, kGat = 6 };
+// kBlur: the fused 64 x 64 blur tile (gathered windows); kBlurW: the 32 x 64
+// tile from TMA-staged windows (problems whose R^* needs no orientation-aware
+// taps: every boundary but the symmetric one with non-palindromic taps)
+enum StageKind : int { kMom = 0, kSyn = 1, kBlur = 2, kAna = 3, kSum = 4, kL1 = 5, kGat = 6, kBlurW = 7 };
 constexpr int kGatherPixels = kEngineThreads;  // pixels per item of a per-pixel gather level
 
 // One stage of one problem's iteration.
 struct Stage {
   int kind;
-  int param;       // filter length L (kSyn, kAna, kL1) or padded blur radius (kBlur)
+  int param;       // filter length L (kSyn, kAna, kL1) or padded blur radius (kBlur, kBlurW)
   int problem;
   int args;        // index into the argument array of its kind
   int ntiles, tiles_c;
   int prev;        // stage waited on (-1: none)
   int prev_tiles;  // its tiles
   int prev_lag;    // 1: prev belongs to the previous iteration
-  int part;        // first partial slot of its tiles (kBlur, kAna with prox, kL1), else -1
+  int part;        // first partial slot of its tiles (kBlur, kBlurW, kAna with prox, kL1), else -1
+};
+
+// Arguments of a kBlurW stage: the tensor maps over u and b (boxes of
+// WG<R>) live in device memory next to the tile arguments.
+struct BlurWinArgs {  // aligned as its tensor maps
+  CUtensorMap umap, bmap;
+  TiledArgs a;
 };
 
 struct ProbDev {
@@ -76,6 +87,7 @@ struct EngineArgs {
   const SynArgs* syn;
   const AnaArgs* ana;
   const TiledArgs* blur;
+  const BlurWinArgs* blurw;
   const ProbDev* prob;
   double* objectives;      // objective launch: one per problem
   int* counters;           // [0] next item, [1] abort flag, [2 + stage] tiles done
@@ -172,6 +184,12 @@ __device__ __noinline__ float engine_ana(const AnaArgs& a, int ty, int tx, unsig
   analysis_tile<L, true, kEngineThreads>(a, ty, tx, l1, *reinterpret_cast<AnaSmem<L>*>(dyn),
                                          reinterpret_cast<float*>(dyn + kProxOffset));
   return l1;
+}
+
+template <int R>
+__device__ __noinline__ float engine_blur_window(const TiledArgs& a, const CUtensorMap* umap, const CUtensorMap* bmap,
+                                                 int ty, int tx, unsigned char* dyn) {
+  return blur_window_tile<R>(a, umap, bmap, ty, tx, dyn);
 }
 
 template <int R>
@@ -284,6 +302,22 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         }
         break;
       }
+      case kBlurW: {
+        if (st != cur_st) {
+          copy_block_args(&s_args.blur, &e.blurw[S.args].a);
+          __syncthreads();
+        }
+        const BlurWinArgs* w = &e.blurw[S.args];
+        float sq = 0.0f;
+        with_R(S.param, [&](auto Rc) {
+          sq = engine_blur_window<decltype(Rc)::value>(s_args.blur, &w->umap, &w->bmap, ty, tx, dyn);
+        });
+        if (S.part >= 0) {
+          const double tot = block_sum<kEngineThreads>((double)sq, red);
+          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = 0.5 * tot;
+        }
+        break;
+      }
       case kL1: {
         const L1Args la = l1args[S.args];
         const int64_t i0 = (int64_t)tile * kL1Chunk;
@@ -337,7 +371,22 @@ struct ProbWs {
   int nblur, nl1;
 };
 
-int blur_tiles(const adjwt_blur_plan* b) { return ((b->cols + kT - 1) / kT) * ((b->rows + kT - 1) / kT); }
+// Whether a problem's blur stage takes the TMA-window tile: not under the
+// symmetric boundary with non-palindromic taps (R^* would need
+// orientation-aware taps at the border).
+bool blur_window_ok(const adjwt_blur_plan* b) {
+  if (b->bc != kSym) return true;
+  for (int t = 0; t < b->kr; ++t)
+    if (b->taps_r[t] != b->taps_r[b->kr - 1 - t]) return false;
+  for (int t = 0; t < b->kc; ++t)
+    if (b->taps_c[t] != b->taps_c[b->kc - 1 - t]) return false;
+  return true;
+}
+int blur_tiles_c(const adjwt_blur_plan* b) { return blur_window_ok(b) ? (b->cols + kWW - 1) / kWW : (b->cols + kT - 1) / kT; }
+int blur_tiles(const adjwt_blur_plan* b) {
+  const int th = blur_window_ok(b) ? kWH : kT;
+  return blur_tiles_c(b) * ((b->rows + th - 1) / th);
+}
 int l1_tiles(const adjwt_wt_plan* w) { return static_cast<int>((w->num_coeffs + kL1Chunk - 1) / kL1Chunk); }
 
 ProbWs prob_ws(const adjwt_fista_problem& pr) {
@@ -446,6 +495,9 @@ AnaArgs ana_level(const adjwt_fista_problem& pr, int j, const float* in_image, f
   a.tiles_r = (L.ax[0].n + kTile - 1) / kTile;
   return a;
 }
+
+// kBlurW arguments: the tile arguments and the tensor maps over u and b.
+int window_args(const adjwt_fista_problem& pr, const float* u, float* g, double* partials, BlurWinArgs* out);
 
 TiledArgs blur_args(const adjwt_fista_problem& pr, const float* u, float* g, double* partials) {
   const adjwt_blur_plan* p = pr.blur;
@@ -579,9 +631,37 @@ size_t put(std::vector<unsigned char>& blob, const std::vector<T>& v) {
   return off;
 }
 
-size_t engine_smem(int rmax) {
-  size_t blur = 0;
+int window_args(const adjwt_fista_problem& pr, const float* u, float* g, double* partials, BlurWinArgs* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->a = blur_args(pr, u, g, partials);
+  const adjwt_blur_plan* b = pr.blur;
+  int uh, uw, vh, vw;
+  window_boxes(blur_radius(b), &uh, &uw, &vh, &vw);
+  int rc = make_tmap_2d_f32(&out->umap, u, b->rows, b->cols, b->image_pitch, uh, uw);
+  if (!rc) rc = make_tmap_2d_f32(&out->bmap, pr.b, b->rows, b->cols, b->image_pitch, vh, vw);
+  return rc;
+}
+
+size_t window_smem(int rmax) {
   switch (rmax) {
+    case 2: return WG<2>::smem_bytes();
+    case 3: return WG<3>::smem_bytes();
+    case 4: return WG<4>::smem_bytes();
+    case 5: return WG<5>::smem_bytes();
+    case 6: return WG<6>::smem_bytes();
+    case 7: return WG<7>::smem_bytes();
+    case 8: return WG<8>::smem_bytes();
+    case 9: return WG<9>::smem_bytes();
+    default: return WG<12>::smem_bytes();
+  }
+}
+
+// rmax_w / rmax_t: the largest padded radius of the problems whose blur stage
+// takes the window tile / the gathered tile (0: none)
+size_t engine_smem(int rmax_w, int rmax_t) {
+  const int rmax = rmax_t;
+  size_t blur = 0;
+  if (rmax) switch (rmax) {
     case 2: blur = blur_tile_smem<2>(); break;
     case 3: blur = blur_tile_smem<3>(); break;
     case 4: blur = blur_tile_smem<4>(); break;
@@ -592,7 +672,7 @@ size_t engine_smem(int rmax) {
     case 9: blur = blur_tile_smem<9>(); break;
     default: blur = blur_tile_smem<12>(); break;
   }
-  return std::max({kProxOffset + kProxSlotBytes, sizeof(SynSmem<10>), blur});
+  return std::max({kProxOffset + kProxSlotBytes, sizeof(SynSmem<10>), blur, rmax_w ? window_smem(rmax_w) : size_t{0}});
 }
 
 }  // namespace
@@ -633,12 +713,13 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   std::vector<SynArgs> syn;
   std::vector<AnaArgs> ana;
   std::vector<TiledArgs> blr;
+  std::vector<BlurWinArgs> blw;
   std::vector<L1Args> l1;
   std::vector<ProbDev> pdev;
   std::vector<double*> moms;
   std::vector<StageList> run_lists(count), obj_lists(count);
   char* base = static_cast<char*>(ws);
-  int rmax = 2;
+  int rmax_w = 0, rmax_t = 0;
   for (int p = 0; p < count; ++p) {
     const adjwt_fista_problem& pr = probs[p];
     const adjwt_wt_plan* w = pr.wt;
@@ -653,8 +734,20 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     pdev.push_back(ProbDev{mom, parts, pw.nblur, pw.nl1, pr.lambda});
     moms.push_back(mom);
     const int J = w->levels, Lf = w->fb.L, R = blur_radius(pr.blur);
-    rmax = std::max(rmax, R);
-    const int btc = (pr.blur->cols + kT - 1) / kT;
+    const bool win = blur_window_ok(pr.blur);
+    (win ? rmax_w : rmax_t) = std::max(win ? rmax_w : rmax_t, R);
+    const int btc = blur_tiles_c(pr.blur);
+    // the blur stage: kBlurW (TMA windows) or kBlur (gathered windows)
+    auto blur_stage = [&](float* gout, double* parts_out, int part) -> Stage {
+      if (win) {
+        BlurWinArgs wa;
+        if (window_args(pr, u, gout, parts_out, &wa)) return Stage{-1};
+        blw.push_back(wa);
+        return make_stage(kBlurW, R, p, static_cast<int>(blw.size()) - 1, pw.nblur, btc, part);
+      }
+      blr.push_back(blur_args(pr, u, gout, parts_out));
+      return make_stage(kBlur, R, p, static_cast<int>(blr.size()) - 1, pw.nblur, btc, part);
+    };
     // iteration: MOM, W levels J..1 on y, R^*(R u - b), W^* + prox levels 1..J
     auto& rl = run_lists[p].st;
     rl.push_back(make_stage(kMom, 0, p, 0, 1, 1, -1));
@@ -663,8 +756,11 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
       rl.push_back(syn_stage(w, j, a, Lf, p, static_cast<int>(syn.size())));
       syn.push_back(a);
     }
-    rl.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, -1));
-    blr.push_back(blur_args(pr, u, g, nullptr));
+    rl.push_back(blur_stage(g, nullptr, -1));
+    if (rl.back().kind < 0) {
+      delete B;
+      return fail(ADJWT_ERR_CUDA, "adjwt_fista_batch_create: tensor map encoding failed");
+    }
     for (int j = 1; j <= J; ++j) {
       const AnaArgs a = ana_level(pr, j, g, x[p], y[p], ll, mom + 1);
       rl.push_back(make_stage(kAna, Lf, p, static_cast<int>(ana.size()), a.tiles_c * a.tiles_r, a.tiles_c, -1));
@@ -677,8 +773,11 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
       ol.push_back(syn_stage(w, j, a, Lf, p, static_cast<int>(syn.size())));
       syn.push_back(a);
     }
-    ol.push_back(make_stage(kBlur, R, p, static_cast<int>(blr.size()), pw.nblur, btc, 0));
-    blr.push_back(blur_args(pr, u, nullptr, parts));
+    ol.push_back(blur_stage(nullptr, parts, 0));
+    if (ol.back().kind < 0) {
+      delete B;
+      return fail(ADJWT_ERR_CUDA, "adjwt_fista_batch_create: tensor map encoding failed");
+    }
     ol.push_back(make_stage(kL1, 0, p, static_cast<int>(l1.size()), pw.nl1, pw.nl1, pw.nblur));
     l1.push_back(L1Args{x[p], w->num_coeffs});
     ol.push_back(make_stage(kSum, 0, p, 0, 1, 1, -1));
@@ -689,8 +788,8 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   std::vector<int> rank(count);
   for (int p = 0; p < count; ++p) rank[p] = p;
   std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) {
-    const int ka = probs[a].wt->fb.L * 64 + blur_radius(probs[a].blur);
-    const int kb = probs[b].wt->fb.L * 64 + blur_radius(probs[b].blur);
+    const int ka = probs[a].wt->fb.L * 128 + blur_window_ok(probs[a].blur) * 64 + blur_radius(probs[a].blur);
+    const int kb = probs[b].wt->fb.L * 128 + blur_window_ok(probs[b].blur) * 64 + blur_radius(probs[b].blur);
     return ka < kb;
   });
   order_stages(run_lists, rank, true, &rst, &ritem, &rfirst, &ritems);
@@ -700,6 +799,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   const size_t o_rst = put(blob, rst), o_ritem = put(blob, ritem), o_rfirst = put(blob, rfirst);
   const size_t o_ost = put(blob, ost), o_oitem = put(blob, oitem), o_ofirst = put(blob, ofirst);
   const size_t o_syn = put(blob, syn), o_ana = put(blob, ana), o_blr = put(blob, blr), o_l1 = put(blob, l1);
+  const size_t o_blw = put(blob, blw);
   const size_t o_prob = put(blob, pdev), o_mom = put(blob, moms);
   const size_t nctr = kCtrDone + std::max(rst.size(), ost.size());
   const size_t o_ctr = static_cast<size_t>(round_up(static_cast<int64_t>(blob.size()), 256));
@@ -722,6 +822,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     L.args.syn = reinterpret_cast<const SynArgs*>(d + o_syn);
     L.args.ana = reinterpret_cast<const AnaArgs*>(d + o_ana);
     L.args.blur = reinterpret_cast<const TiledArgs*>(d + o_blr);
+    L.args.blurw = reinterpret_cast<const BlurWinArgs*>(d + o_blw);
     L.args.prob = reinterpret_cast<const ProbDev*>(d + o_prob);
     L.args.counters = reinterpret_cast<int*>(d + o_ctr);
     L.args.status = device_status_ptr();
@@ -731,7 +832,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   B->l1args = reinterpret_cast<const L1Args*>(d + o_l1);
   B->mom_ptrs = reinterpret_cast<double* const*>(d + o_mom);
   B->counters = reinterpret_cast<int*>(d + o_ctr);
-  B->dyn = engine_smem(rmax);
+  B->dyn = engine_smem(rmax_w, rmax_t);
   e = set_smem(k_fista_engine, B->dyn);
   int per_sm = 0;
   if (e == cudaSuccess)

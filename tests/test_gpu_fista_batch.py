@@ -10,7 +10,7 @@ import torch
 
 from oracle import blur as oblur
 from oracle import fista as ofista
-from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_vector
+from synthetic_inputs import gaussian_noise, piecewise_smooth_image, random_taps, random_vector
 from tests.gpu_util import image_dev, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -27,6 +27,9 @@ MIX = [
     (128, 128, 4, "db2", "per", 7, 1.2, "per", "adjoint"),
     (90, 150, 3, "db4", "sym", 13, 2.0, "zero", "adjoint"),
     (120, 120, 3, "cdf97", "sym", 19, 3.0, "sym", "adjoint"),
+    # non-palindromic taps under the symmetric boundary: the gathered-window
+    # blur stage (the others take the TMA-window stage)
+    (100, 84, 2, "db4", "sym", 7, None, "sym", "adjoint"),
 ]
 LAM = 1e-3
 
@@ -41,7 +44,7 @@ def adj():
 def _problems(adj):
     out = []
     for i, (rows, cols, J, w, mode, k, sigma, bbc, grad) in enumerate(MIX):
-        p = oblur.gaussian_psf(k, sigma)
+        p = oblur.gaussian_psf(k, sigma) if sigma is not None else random_taps(k, 77 + i)
         img = piecewise_smooth_image(rows, cols, 900 + i)
         b = oblur.blur(img, p, p, bbc) + gaussian_noise((rows, cols), 950 + i)
         prob = ofista.Problem(rows, cols, J, w, mode, p, p, bbc, b, LAM, gradient=grad)
@@ -56,7 +59,7 @@ def _problems(adj):
 
 
 def test_batch_iterates_and_objectives_match_the_oracle(adj):
-    """8 mixed problems, 6 iterations in one launch, then 4 more in a second:
+    """9 mixed problems, 6 iterations in one launch, then 4 more in a second:
     every iterate within 1e-4 (relative L2) of the float64 oracle after each
     launch, and the batched objective F(x_k) within 1e-5."""
     probs = _problems(adj)
