@@ -1280,6 +1280,22 @@ def reference(args, budget_s=150.0):
     }))
 
 
+def engine_sample(count, seed=8100):
+    """The batched engine alone on `count` problems of the batching mix: run(2),
+    run(5), objective(); prints the objectives and the device status."""
+    import torch
+    import paper_1707_02018_gb300 as adj
+    probs = cfg4_problems(adj, torch, count, seed=seed)
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    batch.reset()
+    batch.run(2)
+    batch.run(5)
+    F = batch.objective()
+    torch.cuda.synchronize()
+    print(json.dumps({"engine_sample": count, "objectives": [float(v) for v in F.cpu()],
+                      "device_status": adj.device_status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1290,11 +1306,17 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-4 solve")
     ap.add_argument("--autotune", action="store_true", help="measure the TMA / tiled kernel choice per wavelet level")
     ap.add_argument("--no-graph", action="store_true", help="time the step issued call by call, not a CUDA graph")
+    ap.add_argument("--engine-sample", type=int, default=0, metavar="P",
+                    help="only run the batched engine on P problems of the batching mix (two launches of the "
+                         "iteration, then the objective launch) and exit: the profiling target of the engine")
     args = ap.parse_args()
     global AUTOTUNE
     AUTOTUNE = args.autotune
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.engine_sample:
+        engine_sample(args.engine_sample)
+        return
     if args.impl == "reference":
         reference(args)
     else:
