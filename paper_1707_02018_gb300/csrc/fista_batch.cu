@@ -78,10 +78,19 @@ struct ProbDev {
   double lambda;
 };
 
+// Per item of one iteration: its stage's record and its tile, so that taking
+// an item costs one dependent load (made while the previous item runs).
+struct __align__(16) Item {
+  int kind, param, problem, args, tiles_c, part;  // its stage's (Stage)
+  int st;    // its stage
+  int tile;  // its tile within the stage
+  int prev;  // the stage it waits on (-1: none)
+  int pt2;   // that stage's tiles * 2, + 1 if it belongs to the previous iteration
+  int pad[2];
+};
+
 struct EngineArgs {
-  const Stage* stages;
-  const int* item_stage;   // per item of one iteration: its stage
-  const int* stage_first;  // per stage: its first item within the iteration
+  const Item* items;       // per item of one iteration
   int items_per_iter;
   int iters;
   const SynArgs* syn;
@@ -111,12 +120,15 @@ __device__ __forceinline__ bool engine_wait(const int* ctr, int target, const in
   }
 }
 
+// Argument block into shared memory by warps 1.. (thread 0 is meanwhile in
+// the item's dependency wait).
 template <typename T>
 __device__ __forceinline__ void copy_block_args(T* dst, const T* src) {
   static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += kEngineThreads) d[i] = s[i];
+  for (int i = static_cast<int>(threadIdx.x) - 32; i < (int)(sizeof(T) / 4); i += kEngineThreads - 32)
+    if (i >= 0) d[i] = s[i];
 }
 
 template <typename Fn>
@@ -203,53 +215,78 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
   pdl_entry();
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ StageArgs s_args;
-  __shared__ int s_word[2];
+  __shared__ int s_word[2];  // [0] the item to run, [1] whether it may run
+  __shared__ Item s_item;
   __shared__ double red[kEngineThreads / 32];
   __shared__ int s_border;
   const int tid = threadIdx.x;
   int* abort_flag = e.counters + 1;
   const int total = e.items_per_iter * e.iters;
-  // thread 0 holds the next ticket while the current item runs (taken one
-  // ahead: the smallest unfinished ticket is always some CTA's current item,
-  // whose dependencies all have smaller tickets, so the launch still makes
-  // progress)
-  int next = tid == 0 ? atomicAdd(&e.counters[0], 1) : 0;
+  // Thread 0 holds two tickets ahead and loads the next item's record while
+  // the current one runs, so that an item starts after one round trip: its
+  // dependency wait, beside the copy of its argument block.  The smallest
+  // unfinished ticket is still always some CTA's current item, whose
+  // dependencies all have smaller tickets, so the launch makes progress.
+  int n1 = 0, n2 = 0;
+  Item nxt{};
+  if (tid == 0) {
+    const int t0 = atomicAdd(&e.counters[0], 1);
+    n1 = atomicAdd(&e.counters[0], 1);
+    if (t0 < total) s_item = e.items[t0 % e.items_per_iter];
+    s_word[0] = t0;
+  }
+  __syncthreads();
   int cur_st = -1;  // stage whose argument block is in s_args
   for (;;) {
+    const int item = s_word[0];
+    if (item >= total) break;
+    const Item I = s_item;
+    const int st = I.st;
     if (tid == 0) {
-      int item = next, st = 0;
+      if (n1 < total) nxt = e.items[n1 % e.items_per_iter];
+      n2 = atomicAdd(&e.counters[0], 1);
       int ab;
       asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
-      if (ab || item >= total) item = -1;
-      if (item >= 0) next = atomicAdd(&e.counters[0], 1);
-      if (item >= 0) {
-        const int it = item / e.items_per_iter;
-        st = e.item_stage[item - it * e.items_per_iter];
-        const Stage& S = e.stages[st];
-        int target = (it + 1 - S.prev_lag) * S.prev_tiles;
-        if (e.stall && item == 0) target = S.prev_tiles;  // a previous iteration that never ran
-        if (S.prev >= 0 && target > 0 && !engine_wait(&e.counters[kCtrDone + S.prev], target, abort_flag)) {
-          record_status(e.status, ADJWT_ERR_TIMEOUT);
-          atomicExch(abort_flag, 1);
-          item = -1;
-        }
+      int go = ab ? 0 : 1;
+      const int it = item / e.items_per_iter, pt = I.pt2 >> 1;
+      int target = (it + 1 - (I.pt2 & 1)) * pt;
+      if (e.stall && item == 0) target = pt;  // a previous iteration that never ran
+      if (go && I.prev >= 0 && target > 0 && !engine_wait(&e.counters[kCtrDone + I.prev], target, abort_flag)) {
+        record_status(e.status, ADJWT_ERR_TIMEOUT);
+        atomicExch(abort_flag, 1);
+        go = 0;
       }
-      s_word[0] = item;
-      s_word[1] = st;
+      s_word[1] = go;
+    }
+    if (st != cur_st) {
+      switch (I.kind) {
+        case kSyn:
+        case kGat:
+          copy_block_args(&s_args.syn, &e.syn[I.args]);
+          break;
+        case kAna:
+          copy_block_args(&s_args.ana, &e.ana[I.args]);
+          break;
+        case kBlur:
+          copy_block_args(&s_args.blur, &e.blur[I.args]);
+          break;
+        case kBlurW:
+          copy_block_args(&s_args.blur, &e.blurw[I.args].a);
+          break;
+        default:
+          break;
+      }
     }
     __syncthreads();
-    const int item = s_word[0], st = s_word[1];
-    if (item < 0) break;
-    const int it = item / e.items_per_iter;
-    const Stage S = e.stages[st];
-    const int tile = item - it * e.items_per_iter - e.stage_first[st];
-    const int ty = tile / S.tiles_c, tx = tile - ty * S.tiles_c;
-    switch (S.kind) {
+    if (!s_word[1]) break;
+    const int tile = I.tile;
+    const int ty = tile / I.tiles_c, tx = tile - ty * I.tiles_c;
+    switch (I.kind) {
       case kMom:
         if (tid == 0) {
           // device-resident momentum (the method cited in Sec. I-B):
           // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, beta_k = (t_k - 1) / t_{k+1}
-          double* m = e.prob[S.problem].mom;
+          double* m = e.prob[I.problem].mom;
           const double t = __ldcg(m);
           const double t1 = 0.5 * (1.0 + sqrt(__dadd_rn(1.0, __dmul_rn(4.0 * t, t))));
           m[1] = (t - 1.0) / t1;
@@ -257,90 +294,75 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const Engine
         }
         break;
       case kSyn:
-        if (st != cur_st) {
-          copy_block_args(&s_args.syn, &e.syn[S.args]);
-          __syncthreads();
-        }
-        with_L(S.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
+        with_L(I.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
         break;
       case kGat: {
-        if (st != cur_st) {
-          copy_block_args(&s_args.syn, &e.syn[S.args]);
-          __syncthreads();
-        }
         const int64_t idx = (int64_t)tile * kGatherPixels + tid;
         if (idx < (int64_t)s_args.syn.Nr * s_args.syn.Nc) {
           const int tr = static_cast<int>(idx / s_args.syn.Nc);
           const int tc = static_cast<int>(idx - (int64_t)tr * s_args.syn.Nc);
-          with_L(S.param, [&](auto Lc) { engine_gat<decltype(Lc)::value>(s_args.syn, tr, tc); });
+          with_L(I.param, [&](auto Lc) { engine_gat<decltype(Lc)::value>(s_args.syn, tr, tc); });
         }
         break;
       }
       case kAna: {
-        if (st != cur_st) {
-          copy_block_args(&s_args.ana, &e.ana[S.args]);
-          __syncthreads();
-        }
         float l1 = 0.0f;
-        with_L(S.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
-        if (S.part >= 0) {
+        with_L(I.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
+        if (I.part >= 0) {
           const double tot = block_sum<kEngineThreads>((double)l1, red);
-          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = tot;
+          if (tid == 0) e.prob[I.problem].parts[I.part + tile] = tot;
         }
         break;
       }
       case kBlur: {
-        if (st != cur_st) {
-          copy_block_args(&s_args.blur, &e.blur[S.args]);
-          __syncthreads();
-        }
         float sq = 0.0f;
-        with_R(S.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
-        if (S.part >= 0) {
+        with_R(I.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
+        if (I.part >= 0) {
           const double tot = block_sum<kEngineThreads>((double)sq, red);
-          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = 0.5 * tot;
+          if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
         }
         break;
       }
       case kBlurW: {
-        if (st != cur_st) {
-          copy_block_args(&s_args.blur, &e.blurw[S.args].a);
-          __syncthreads();
-        }
-        const BlurWinArgs* w = &e.blurw[S.args];
+        const BlurWinArgs* w = &e.blurw[I.args];
         float sq = 0.0f;
-        with_R(S.param, [&](auto Rc) {
+        with_R(I.param, [&](auto Rc) {
           sq = engine_blur_window<decltype(Rc)::value>(s_args.blur, &w->umap, &w->bmap, ty, tx, dyn);
         });
-        if (S.part >= 0) {
+        if (I.part >= 0) {
           const double tot = block_sum<kEngineThreads>((double)sq, red);
-          if (tid == 0) e.prob[S.problem].parts[S.part + tile] = 0.5 * tot;
+          if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
         }
         break;
       }
       case kL1: {
-        const L1Args la = l1args[S.args];
+        const L1Args la = l1args[I.args];
         const int64_t i0 = (int64_t)tile * kL1Chunk;
         float acc = 0.0f;
         for (int64_t i = i0 + tid; i < la.n && i < i0 + kL1Chunk; i += kEngineThreads) acc += fabsf(__ldcg(la.x + i));
         const double tot = block_sum<kEngineThreads>((double)acc, red);
-        if (tid == 0) e.prob[S.problem].parts[S.part + tile] = tot;
+        if (tid == 0) e.prob[I.problem].parts[I.part + tile] = tot;
         break;
       }
       case kSum:
         if (tid == 0) {
           // F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1, partials added in a fixed order
-          const ProbDev pd = e.prob[S.problem];
+          const ProbDev pd = e.prob[I.problem];
           double r = 0.0, l1 = 0.0;
           for (int i = 0; i < pd.nblur; ++i) r += __ldcg(pd.parts + i);
           for (int i = 0; i < pd.nl1; ++i) l1 += __ldcg(pd.parts + pd.nblur + i);
-          e.objectives[S.problem] = r + pd.lambda * l1;
+          e.objectives[I.problem] = r + pd.lambda * l1;
         }
         break;
       default:
         break;
     }
     cur_st = st;
+    if (tid == 0) {
+      s_word[0] = n1;
+      s_item = nxt;
+      n1 = n2;
+    }
     // every write of the tile happens before its count is published: block
     // barrier, then a release add by one thread (cumulative over the barrier)
     __syncthreads();
@@ -562,7 +584,7 @@ struct StageList {
 // filter length and blur radius, so that consecutive items run the same
 // stage body and the instruction cache keeps it).
 void order_stages(const std::vector<StageList>& per, const std::vector<int>& rank, bool wrap, std::vector<Stage>* out,
-                  std::vector<int>* item_stage, std::vector<int>* first, int* items) {
+                  std::vector<Item>* items) {
   size_t smax = 0;
   for (const auto& l : per) smax = std::max(smax, l.st.size());
   std::vector<std::vector<int>> gidx(per.size());
@@ -591,13 +613,24 @@ void order_stages(const std::vector<StageList>& per, const std::vector<int>& ran
       S.prev_tiles = S.prev >= 0 ? (*out)[S.prev].ntiles : 0;
     }
   }
-  item_stage->clear();
-  first->clear();
+  items->clear();
   for (size_t i = 0; i < out->size(); ++i) {
-    first->push_back(static_cast<int>(item_stage->size()));
-    for (int t = 0; t < (*out)[i].ntiles; ++t) item_stage->push_back(static_cast<int>(i));
+    const Stage& S = (*out)[i];
+    for (int t = 0; t < S.ntiles; ++t) {
+      Item it{};
+      it.kind = S.kind;
+      it.param = S.param;
+      it.problem = S.problem;
+      it.args = S.args;
+      it.tiles_c = S.tiles_c;
+      it.part = S.part;
+      it.st = static_cast<int>(i);
+      it.tile = t;
+      it.prev = S.prev;
+      it.pt2 = S.prev_tiles * 2 + S.prev_lag;
+      items->push_back(it);
+    }
   }
-  *items = static_cast<int>(item_stage->size());
 }
 
 Stage make_stage(int kind, int param, int problem, int args, int ntiles, int tiles_c, int part) {
@@ -783,8 +816,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     ol.push_back(make_stage(kSum, 0, p, 0, 1, 1, -1));
   }
   std::vector<Stage> rst, ost;
-  std::vector<int> ritem, rfirst, oitem, ofirst;
-  int ritems = 0, oitems = 0;
+  std::vector<Item> ritem, oitem;
   std::vector<int> rank(count);
   for (int p = 0; p < count; ++p) rank[p] = p;
   std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) {
@@ -792,12 +824,11 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     const int kb = probs[b].wt->fb.L * 128 + blur_window_ok(probs[b].blur) * 64 + blur_radius(probs[b].blur);
     return ka < kb;
   });
-  order_stages(run_lists, rank, true, &rst, &ritem, &rfirst, &ritems);
-  order_stages(obj_lists, rank, false, &ost, &oitem, &ofirst, &oitems);
+  order_stages(run_lists, rank, true, &rst, &ritem);
+  order_stages(obj_lists, rank, false, &ost, &oitem);
 
   std::vector<unsigned char> blob;
-  const size_t o_rst = put(blob, rst), o_ritem = put(blob, ritem), o_rfirst = put(blob, rfirst);
-  const size_t o_ost = put(blob, ost), o_oitem = put(blob, oitem), o_ofirst = put(blob, ofirst);
+  const size_t o_ritem = put(blob, ritem), o_oitem = put(blob, oitem);
   const size_t o_syn = put(blob, syn), o_ana = put(blob, ana), o_blr = put(blob, blr), o_l1 = put(blob, l1);
   const size_t o_blw = put(blob, blw);
   const size_t o_prob = put(blob, pdev), o_mom = put(blob, moms);
@@ -812,12 +843,10 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     return cuda_fail(e, "adjwt_fista_batch_create");
   }
   char* d = static_cast<char*>(B->dev);
-  auto fill = [&](BatchLaunch& L, size_t ost_, size_t oitem_, size_t ofirst_, int nst, int items) {
+  auto fill = [&](BatchLaunch& L, size_t oitem_, int nst, int items) {
     L.nstages = nst;
     L.items = items;
-    L.args.stages = reinterpret_cast<const Stage*>(d + ost_);
-    L.args.item_stage = reinterpret_cast<const int*>(d + oitem_);
-    L.args.stage_first = reinterpret_cast<const int*>(d + ofirst_);
+    L.args.items = reinterpret_cast<const Item*>(d + oitem_);
     L.args.items_per_iter = items;
     L.args.syn = reinterpret_cast<const SynArgs*>(d + o_syn);
     L.args.ana = reinterpret_cast<const AnaArgs*>(d + o_ana);
@@ -827,8 +856,8 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     L.args.counters = reinterpret_cast<int*>(d + o_ctr);
     L.args.status = device_status_ptr();
   };
-  fill(B->run, o_rst, o_ritem, o_rfirst, static_cast<int>(rst.size()), ritems);
-  fill(B->obj, o_ost, o_oitem, o_ofirst, static_cast<int>(ost.size()), oitems);
+  fill(B->run, o_ritem, static_cast<int>(rst.size()), static_cast<int>(ritem.size()));
+  fill(B->obj, o_oitem, static_cast<int>(ost.size()), static_cast<int>(oitem.size()));
   B->l1args = reinterpret_cast<const L1Args*>(d + o_l1);
   B->mom_ptrs = reinterpret_cast<double* const*>(d + o_mom);
   B->counters = reinterpret_cast<int*>(d + o_ctr);
