@@ -211,7 +211,7 @@ __device__ __noinline__ float engine_blur(const TiledArgs& a, int ty, int tx, un
   return sq;
 }
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_fista_engine(const EngineArgs e, const L1Args* l1args) {
+__global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const EngineArgs e, const L1Args* l1args) {
   pdl_entry();
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ StageArgs s_args;

@@ -110,9 +110,11 @@ __device__ __forceinline__ void border_tile(int r0, int r1, int c0, int c1, int 
 constexpr int kAP = 8;
 // prox epilogue: each row-pass thread's prox state (y and x of its two bands,
 // 8 values each) is copied into its own dynamic-shared-memory slot at kernel
-// start, so the loads overlap the window gather and both passes; 36-float
-// slots put a quarter warp's 16-byte reads on distinct banks
-constexpr int kProxSlot = 36;
+// start, so the loads overlap the window gather and both passes.  A slot is
+// eight 16-byte chunks; chunk c of thread t sits at position c xor (t mod 8),
+// which puts a quarter warp's 16-byte reads of one chunk on distinct banks.
+constexpr int kProxSlot = 32;
+__device__ __forceinline__ float* prox_chunk(float* slot, int c) { return slot + 4 * (c ^ (threadIdx.x & 7)); }
 constexpr int kProxRowers = 2 * (kTile / kAP) * 32;
 constexpr size_t kProxSlotBytes = (size_t)kProxRowers * kProxSlot * sizeof(float);
 
@@ -179,23 +181,23 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
       if (full) {
 #pragma unroll
         for (int q = 0; q < kAP / 4; ++q) {
-          cp_async16(slot + hb * 16 + 4 * q, pys[hb] + row + 4 * q, 16u);
-          cp_async16(slot + hb * 16 + 8 + 4 * q, pxs[hb] + row + 4 * q, 16u);
+          cp_async16(prox_chunk(slot, hb * 4 + q), pys[hb] + row + 4 * q, 16u);
+          cp_async16(prox_chunk(slot, hb * 4 + 2 + q), pxs[hb] + row + 4 * q, 16u);
         }
       } else if constexpr (CG) {
         // state written earlier in the same launch: read at L2, never through L1
 #pragma unroll
         for (int p = 0; p < kAP; ++p) {
           const bool in = lbase + p < a.nc;
-          slot[hb * 16 + p] = in ? __ldcg(pys[hb] + row + p) : 0.0f;
-          slot[hb * 16 + 8 + p] = in ? __ldcg(pxs[hb] + row + p) : 0.0f;
+          prox_chunk(slot, hb * 4 + p / 4)[p % 4] = in ? __ldcg(pys[hb] + row + p) : 0.0f;
+          prox_chunk(slot, hb * 4 + 2 + p / 4)[p % 4] = in ? __ldcg(pxs[hb] + row + p) : 0.0f;
         }
       } else {
 #pragma unroll
         for (int p = 0; p < kAP; ++p) {
           const bool in = lbase + p < a.nc;
-          cp_async4(slot + hb * 16 + p, pys[hb] + row + (in ? p : 0), in ? 4u : 0u);
-          cp_async4(slot + hb * 16 + 8 + p, pxs[hb] + row + (in ? p : 0), in ? 4u : 0u);
+          cp_async4(prox_chunk(slot, hb * 4 + p / 4) + p % 4, pys[hb] + row + (in ? p : 0), in ? 4u : 0u);
+          cp_async4(prox_chunk(slot, hb * 4 + 2 + p / 4) + p % 4, pxs[hb] + row + (in ? p : 0), in ? 4u : 0u);
         }
       }
     }
@@ -310,8 +312,8 @@ __device__ __forceinline__ void analysis_tile(const AnaArgs& a, int tile_y, int 
         if (!pxs[hb]) continue;
 #pragma unroll
         for (int q = 0; q < kAP / 4; ++q) {
-          const float4 y4 = reinterpret_cast<const float4*>(slot + hb * 16)[q];
-          const float4 x4 = reinterpret_cast<const float4*>(slot + hb * 16 + 8)[q];
+          const float4 y4 = *reinterpret_cast<const float4*>(prox_chunk(slot, hb * 4 + q));
+          const float4 x4 = *reinterpret_cast<const float4*>(prox_chunk(slot, hb * 4 + 2 + q));
           yv[hb][4 * q] = y4.x; yv[hb][4 * q + 1] = y4.y; yv[hb][4 * q + 2] = y4.z; yv[hb][4 * q + 3] = y4.w;
           xv[hb][4 * q] = x4.x; xv[hb][4 * q + 1] = x4.y; xv[hb][4 * q + 2] = x4.z; xv[hb][4 * q + 3] = x4.w;
         }
