@@ -6,7 +6,9 @@
 //     MOM, W level J, ..., W level 1, R^*(R u - b), W^* level 1 (+prox), ..., W^* level J (+prox)
 // (MOM advances the device-resident momentum t_k, beta_k).  A stage is cut
 // into tiles: the tiled level bodies of wt_tiles.cuh (32 x 32 outputs) and
-// the fused blur body of blur_tile.cuh (64 x 64).  An item is one tile.  The
+// the blur bodies (32 x 64 TMA windows, blur_window_tile.cuh, or gathered
+// 64 x 64 tiles, blur_tile.cuh).  An item is one tile, or two to four
+// consecutive tiles of a stage with many (tiles_per_item).  The
 // items of an iteration are numbered stage-major across problems (stage
 // slot s of every problem before slot s + 1 of any), iteration after
 // iteration; CTAs take the next item number from a counter.
@@ -59,7 +61,7 @@ struct Stage {
   int args;        // index into the argument array of its kind
   int ntiles, tiles_c;
   int prev;        // stage waited on (-1: none)
-  int prev_tiles;  // its tiles
+  int prev_items;  // its items
   int prev_lag;    // 1: prev belongs to the previous iteration
   int part;        // first partial slot of its tiles (kBlur, kBlurW, kAna with prox, kL1), else -1
 };
@@ -83,10 +85,11 @@ struct ProbDev {
 struct __align__(16) Item {
   int kind, param, problem, args, tiles_c, part;  // its stage's (Stage)
   int st;    // its stage
-  int tile;  // its tile within the stage
+  int tile;  // its first tile within the stage
   int prev;  // the stage it waits on (-1: none)
-  int pt2;   // that stage's tiles * 2, + 1 if it belongs to the previous iteration
-  int pad[2];
+  int pt2;   // that stage's items * 2, + 1 if it belongs to the previous iteration
+  int ntl;   // its tiles (consecutive)
+  int pad;
 };
 
 struct EngineArgs {
@@ -120,15 +123,16 @@ __device__ __forceinline__ bool engine_wait(const int* ctr, int target, const in
   }
 }
 
-// Argument block into shared memory by warps 1.. (thread 0 is meanwhile in
-// the item's dependency wait).
+// Argument block into shared memory by warps 1 .. 6 (meanwhile thread 0 is
+// in the item's dependency wait and warp 7 publishes the previous item).
 template <typename T>
 __device__ __forceinline__ void copy_block_args(T* dst, const T* src) {
   static_assert(sizeof(T) % 4 == 0, "argument blocks are whole words");
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
-  for (int i = static_cast<int>(threadIdx.x) - 32; i < (int)(sizeof(T) / 4); i += kEngineThreads - 32)
-    if (i >= 0) d[i] = s[i];
+  const int i0 = static_cast<int>(threadIdx.x) - 32;
+  if (i0 >= 0 && i0 < kEngineThreads - 64)
+    for (int i = i0; i < (int)(sizeof(T) / 4); i += kEngineThreads - 64) d[i] = s[i];
 }
 
 template <typename Fn>
@@ -245,17 +249,19 @@ __global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const Engine
     if (tid == 0) {
       if (n1 < total) nxt = e.items[n1 % e.items_per_iter];
       n2 = atomicAdd(&e.counters[0], 1);
-      int ab;
-      asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
-      int go = ab ? 0 : 1;
       const int it = item / e.items_per_iter, pt = I.pt2 >> 1;
       int target = (it + 1 - (I.pt2 & 1)) * pt;
       if (e.stall && item == 0) target = pt;  // a previous iteration that never ran
-      if (go && I.prev >= 0 && target > 0 && !engine_wait(&e.counters[kCtrDone + I.prev], target, abort_flag)) {
+      // the abort flag and the first poll of the dependency are in flight together
+      int ab;
+      asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(ab) : "l"(abort_flag) : "memory");
+      int go = 1;
+      if (I.prev >= 0 && target > 0 && !engine_wait(&e.counters[kCtrDone + I.prev], target, abort_flag)) {
         record_status(e.status, ADJWT_ERR_TIMEOUT);
         atomicExch(abort_flag, 1);
         go = 0;
       }
+      if (ab) go = 0;
       s_word[1] = go;
     }
     if (st != cur_st) {
@@ -279,7 +285,9 @@ __global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const Engine
     }
     __syncthreads();
     if (!s_word[1]) break;
-    const int tile = I.tile;
+    for (int q = 0; q < I.ntl; ++q) {
+    if (q > 0) __syncthreads();  // the previous tile is done with shared memory
+    const int tile = I.tile + q;
     const int ty = tile / I.tiles_c, tx = tile - ty * I.tiles_c;
     switch (I.kind) {
       case kMom:
@@ -357,6 +365,7 @@ __global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const Engine
       default:
         break;
     }
+    }
     cur_st = st;
     if (tid == 0) {
       s_word[0] = n1;
@@ -364,9 +373,12 @@ __global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const Engine
       n1 = n2;
     }
     // every write of the tile happens before its count is published: block
-    // barrier, then a release add by one thread (cumulative over the barrier)
+    // barrier, then a release add by one thread (cumulative over the
+    // barrier).  The first thread of warp 7 makes it, so that its fence runs
+    // beside thread 0's work on the next item.
     __syncthreads();
-    if (tid == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(e.counters + kCtrDone + st) : "memory");
+    if (tid == kEngineThreads - 32)
+      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(e.counters + kCtrDone + st) : "memory");
   }
 }
 
@@ -578,6 +590,20 @@ struct StageList {
   std::vector<Stage> st;  // in stage order, prev = index within the same problem's list (-1: none)
 };
 
+// Tiles per item: a stage with many tiles hands them out several at a time
+// (consecutive tiles, one item), so that the per-item costs (ticket,
+// dependency wait, argument copy, publishing) are shared; stages of fewer
+// than 2 x kMinItems tiles keep one tile per item to stay spread over CTAs.
+constexpr int kMinItems = 64;
+int tiles_per_item(const Stage& S) {
+  const int gmax = S.kind == kSyn ? 4 : (S.kind == kMom || S.kind == kSum) ? 1 : 2;
+  return std::max(1, std::min(gmax, S.ntiles / kMinItems));
+}
+int stage_items(const Stage& S) {
+  const int g = tiles_per_item(S);
+  return (S.ntiles + g - 1) / g;
+}
+
 // Stage-major order across problems; prev indices become global; the first
 // stage of a problem waits on its last one (previous iteration) when `wrap`.
 // Within a stage slot the problems come in the order `rank` (grouped by
@@ -610,13 +636,14 @@ void order_stages(const std::vector<StageList>& per, const std::vector<int>& ran
         S.prev = -1;
         S.prev_lag = 0;
       }
-      S.prev_tiles = S.prev >= 0 ? (*out)[S.prev].ntiles : 0;
+      S.prev_items = S.prev >= 0 ? stage_items((*out)[S.prev]) : 0;
     }
   }
   items->clear();
   for (size_t i = 0; i < out->size(); ++i) {
     const Stage& S = (*out)[i];
-    for (int t = 0; t < S.ntiles; ++t) {
+    const int g = tiles_per_item(S);
+    for (int t = 0; t < S.ntiles; t += g) {
       Item it{};
       it.kind = S.kind;
       it.param = S.param;
@@ -627,7 +654,8 @@ void order_stages(const std::vector<StageList>& per, const std::vector<int>& ran
       it.st = static_cast<int>(i);
       it.tile = t;
       it.prev = S.prev;
-      it.pt2 = S.prev_tiles * 2 + S.prev_lag;
+      it.pt2 = S.prev_items * 2 + S.prev_lag;
+      it.ntl = std::min(g, S.ntiles - t);
       items->push_back(it);
     }
   }
@@ -907,8 +935,9 @@ extern "C" int adjwt_fista_batch_set_iteration(const adjwt_fista_batch* b, int64
 namespace {
 int engine_launch(const adjwt_fista_batch* b, const BatchLaunch& L, int iters, double* objectives, int stall,
                   cudaStream_t s, const char* name) {
-  if ((int64_t)L.items * iters > 0x7fffffff)
-    return fail(ADJWT_ERR_SHAPE, std::string(name) + ": iterations x items above 2^31");
+  // tickets run up to two per CTA past the last item: keep them in int range
+  if ((int64_t)L.items * iters > 0x7fffffff - (1 << 20))
+    return fail(ADJWT_ERR_SHAPE, std::string(name) + ": iterations x items above 2^31 - 2^20");
   EngineArgs a = L.args;
   a.iters = iters;
   a.objectives = objectives;
