@@ -41,18 +41,18 @@ def adj():
     return adj
 
 
-def _problems(adj):
+def _problems(adj, mix=MIX, seed=900):
     out = []
-    for i, (rows, cols, J, w, mode, k, sigma, bbc, grad) in enumerate(MIX):
+    for i, (rows, cols, J, w, mode, k, sigma, bbc, grad) in enumerate(mix):
         p = oblur.gaussian_psf(k, sigma) if sigma is not None else random_taps(k, 77 + i)
-        img = piecewise_smooth_image(rows, cols, 900 + i)
-        b = oblur.blur(img, p, p, bbc) + gaussian_noise((rows, cols), 950 + i)
+        img = piecewise_smooth_image(rows, cols, seed + i)
+        b = oblur.blur(img, p, p, bbc) + gaussian_noise((rows, cols), seed + 50 + i)
         prob = ofista.Problem(rows, cols, J, w, mode, p, p, bbc, b, LAM, gradient=grad)
         wt = adj.WtPlan(rows, cols, J, w, mode)
         bl = adj.BlurPlan(rows, cols, p, p, bbc)
         db = image_dev(wt, b)
         f = adj.Fista(wt, bl, db, LAM, 1.0, gradient=grad)
-        L = 1.05 * f.lipschitz(wt.pack(random_vector(wt.logical_size, 970 + i)), iters=30)
+        L = 1.05 * f.lipschitz(wt.pack(random_vector(wt.logical_size, seed + 70 + i)), iters=30)
         f.set_lipschitz(L)
         out.append({"oracle": prob, "fista": f, "wt": wt, "bl": bl, "b": db, "L": L})
     return out
@@ -84,6 +84,44 @@ def test_batch_iterates_and_objectives_match_the_oracle(adj):
             assert rel_err(xg, xs[i]) <= 1e-4, (i, done, rel_err(xg, xs[i]))
             Fo = p["oracle"].objective(xs[i])
             assert abs(F[i] - Fo) <= 1e-5 * Fo, (i, done, F[i], Fo)
+    assert adj.device_status() == 0
+
+
+# Large enough that stages hand out several consecutive tiles per item: W
+# level 1 of 600 x 520 has 323 tiles (four per item, the last item three),
+# of 520 x 456 255 tiles (three per item); the blur stages 171 and 136
+# windows (two per item, the first with a single-tile last item).
+MIX_LARGE = [
+    (600, 520, 3, "cdf97", "sym", 15, 2.0, "sym", "adjoint"),
+    (520, 456, 2, "db2", "per", 7, 1.2, "per", "adjoint"),
+    (96, 96, 2, "db4", "zero", 5, 0.9, "zero", "adjoint"),
+]
+
+
+def test_batch_with_several_tiles_per_item_matches_the_oracle(adj):
+    """Problems whose large stages take several tiles per item: every iterate
+    within 1e-4 of the float64 oracle after 5 iterations in one launch, and
+    the objective within 1e-5."""
+    probs = _problems(adj, MIX_LARGE, seed=1200)
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    # one tile per item, W level 1 (32 x 32 tiles) and the blur (32 x 64
+    # windows) alone would take 900 items
+    tiles = sum(-(-r // 32) * -(-c // 32) + -(-r // 32) * -(-c // 64) for r, c, *_ in MIX_LARGE)
+    assert tiles == 900
+    assert batch.info()["items_per_iteration"] < tiles
+    batch.reset()
+    batch.run(5)
+    F = batch.objective().cpu().numpy()
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        x = np.zeros(p["wt"].logical_size)
+        y, t = x.copy(), 1.0
+        for _ in range(5):
+            x, y, t = ofista.fista_step(p["oracle"], x, y, t, p["L"])
+        xg = p["wt"].unpack(p["fista"].x).cpu().numpy()
+        assert rel_err(xg, x) <= 1e-4, (i, rel_err(xg, x))
+        Fo = p["oracle"].objective(x)
+        assert abs(F[i] - Fo) <= 1e-5 * Fo, (i, F[i], Fo)
     assert adj.device_status() == 0
 
 
