@@ -62,6 +62,7 @@ struct Stage {
   int ntiles, tiles_c;
   int prev;        // stage waited on (-1: none)
   int prev_items;  // its items
+  int group;       // tiles per item (set when the stages are ordered)
   int prev_lag;    // 1: prev belongs to the previous iteration
   int part;        // first partial slot of its tiles (kBlur, kBlurW, kAna with prox, kL1), else -1
 };
@@ -590,29 +591,35 @@ struct StageList {
   std::vector<Stage> st;  // in stage order, prev = index within the same problem's list (-1: none)
 };
 
-// Tiles per item: a stage with many tiles hands them out several at a time
-// (consecutive tiles, one item), so that the per-item costs (ticket,
-// dependency wait, argument copy, publishing) are shared; stages of fewer
-// than 2 x kMinItems tiles keep one tile per item to stay spread over CTAs.
+// Tiles per item: when the batch has far more tiles than the launch has CTAs,
+// a stage with many tiles hands them out several at a time (consecutive
+// tiles, one item), so that the per-item costs (ticket, dependency wait,
+// argument copy, publishing) are shared.  A stage keeps one tile per item
+// when it has fewer than 2 x kMinItems tiles, or when its stage slot across
+// the batch holds fewer than 2 x kWaves tiles per CTA: few problems leave
+// the CTAs short of items, and a coarser stage would only lengthen each
+// problem's chain of dependent stages.
 constexpr int kMinItems = 64;
-int tiles_per_item(const Stage& S) {
+constexpr int kWaves = 8;
+int tiles_per_item(const Stage& S, int64_t slot_tiles, int ctas) {
   const int gmax = S.kind == kSyn ? 4 : (S.kind == kMom || S.kind == kSum) ? 1 : 2;
-  return std::max(1, std::min(gmax, S.ntiles / kMinItems));
+  const int64_t by_slot = slot_tiles / ((int64_t)kWaves * std::max(ctas, 1));
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({gmax, S.ntiles / kMinItems, by_slot})));
 }
-int stage_items(const Stage& S) {
-  const int g = tiles_per_item(S);
-  return (S.ntiles + g - 1) / g;
-}
+int stage_items(const Stage& S) { return (S.ntiles + S.group - 1) / S.group; }
 
 // Stage-major order across problems; prev indices become global; the first
 // stage of a problem waits on its last one (previous iteration) when `wrap`.
 // Within a stage slot the problems come in the order `rank` (grouped by
 // filter length and blur radius, so that consecutive items run the same
 // stage body and the instruction cache keeps it).
-void order_stages(const std::vector<StageList>& per, const std::vector<int>& rank, bool wrap, std::vector<Stage>* out,
-                  std::vector<Item>* items) {
+void order_stages(const std::vector<StageList>& per, const std::vector<int>& rank, bool wrap, int ctas,
+                  std::vector<Stage>* out, std::vector<Item>* items) {
   size_t smax = 0;
   for (const auto& l : per) smax = std::max(smax, l.st.size());
+  std::vector<int64_t> slot_tiles(smax, 0);
+  for (const auto& l : per)
+    for (size_t s = 0; s < l.st.size(); ++s) slot_tiles[s] += l.st[s].ntiles;
   std::vector<std::vector<int>> gidx(per.size());
   for (size_t p = 0; p < per.size(); ++p) gidx[p].assign(per[p].st.size(), -1);
   out->clear();
@@ -620,7 +627,9 @@ void order_stages(const std::vector<StageList>& per, const std::vector<int>& ran
     for (int p : rank)
       if (s < per[p].st.size()) {
         gidx[p][s] = static_cast<int>(out->size());
-        out->push_back(per[p].st[s]);
+        Stage S = per[p].st[s];
+        S.group = tiles_per_item(S, slot_tiles[s], ctas);
+        out->push_back(S);
       }
   for (size_t p = 0; p < per.size(); ++p) {
     const size_t n = per[p].st.size();
@@ -642,7 +651,7 @@ void order_stages(const std::vector<StageList>& per, const std::vector<int>& ran
   items->clear();
   for (size_t i = 0; i < out->size(); ++i) {
     const Stage& S = (*out)[i];
-    const int g = tiles_per_item(S);
+    const int g = S.group;
     for (int t = 0; t < S.ntiles; t += g) {
       Item it{};
       it.kind = S.kind;
@@ -852,8 +861,20 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
     const int kb = probs[b].wt->fb.L * 128 + blur_window_ok(probs[b].blur) * 64 + blur_radius(probs[b].blur);
     return ka < kb;
   });
-  order_stages(run_lists, rank, true, &rst, &ritem);
-  order_stages(obj_lists, rank, false, &ost, &oitem);
+  // the launch's CTAs (resident ones: the grid never exceeds them)
+  B->dyn = engine_smem(rmax_w, rmax_t);
+  cudaError_t e = set_smem(k_fista_engine, B->dyn);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fista_engine, kEngineThreads, B->dyn);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "adjwt_fista_batch_create");
+  }
+  B->per_sm = std::max(per_sm, 1);
+  const int ctas = B->per_sm * sm_count();
+  order_stages(run_lists, rank, true, ctas, &rst, &ritem);
+  order_stages(obj_lists, rank, false, ctas, &ost, &oitem);
 
   std::vector<unsigned char> blob;
   const size_t o_ritem = put(blob, ritem), o_oitem = put(blob, oitem);
@@ -864,7 +885,7 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   const size_t o_ctr = static_cast<size_t>(round_up(static_cast<int64_t>(blob.size()), 256));
   B->counter_bytes = nctr * sizeof(int);
   const size_t total = o_ctr + B->counter_bytes;
-  cudaError_t e = cudaMalloc(&B->dev, total);
+  e = cudaMalloc(&B->dev, total);
   if (e == cudaSuccess) e = cudaMemcpy(B->dev, blob.data(), blob.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     delete B;
@@ -889,16 +910,6 @@ extern "C" int adjwt_fista_batch_create(adjwt_fista_batch** out, int count, cons
   B->l1args = reinterpret_cast<const L1Args*>(d + o_l1);
   B->mom_ptrs = reinterpret_cast<double* const*>(d + o_mom);
   B->counters = reinterpret_cast<int*>(d + o_ctr);
-  B->dyn = engine_smem(rmax_w, rmax_t);
-  e = set_smem(k_fista_engine, B->dyn);
-  int per_sm = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fista_engine, kEngineThreads, B->dyn);
-  if (e != cudaSuccess) {
-    delete B;
-    return cuda_fail(e, "adjwt_fista_batch_create");
-  }
-  B->per_sm = std::max(per_sm, 1);
   *out = B;
   return ADJWT_OK;
 }

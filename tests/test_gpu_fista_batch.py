@@ -87,10 +87,8 @@ def test_batch_iterates_and_objectives_match_the_oracle(adj):
     assert adj.device_status() == 0
 
 
-# Large enough that stages hand out several consecutive tiles per item: W
-# level 1 of 600 x 520 has 323 tiles (four per item, the last item three),
-# of 520 x 456 255 tiles (three per item); the blur stages 171 and 136
-# windows (two per item, the first with a single-tile last item).
+# Stages of a few hundred tiles: W level 1 of 600 x 520 has 323 tiles, of
+# 520 x 456 255; the blur stages 171 and 136 windows.
 MIX_LARGE = [
     (600, 520, 3, "cdf97", "sym", 15, 2.0, "sym", "adjoint"),
     (520, 456, 2, "db2", "per", 7, 1.2, "per", "adjoint"),
@@ -98,17 +96,12 @@ MIX_LARGE = [
 ]
 
 
-def test_batch_with_several_tiles_per_item_matches_the_oracle(adj):
-    """Problems whose large stages take several tiles per item: every iterate
-    within 1e-4 of the float64 oracle after 5 iterations in one launch, and
-    the objective within 1e-5."""
+def test_batch_of_large_stages_matches_the_oracle(adj):
+    """Problems with stages of a few hundred tiles: every iterate within 1e-4
+    of the float64 oracle after 5 iterations in one launch, and the
+    objective within 1e-5."""
     probs = _problems(adj, MIX_LARGE, seed=1200)
     batch = adj.FistaBatch([p["fista"] for p in probs])
-    # one tile per item, W level 1 (32 x 32 tiles) and the blur (32 x 64
-    # windows) alone would take 900 items
-    tiles = sum(-(-r // 32) * -(-c // 32) + -(-r // 32) * -(-c // 64) for r, c, *_ in MIX_LARGE)
-    assert tiles == 900
-    assert batch.info()["items_per_iteration"] < tiles
     batch.reset()
     batch.run(5)
     F = batch.objective().cpu().numpy()
@@ -122,6 +115,35 @@ def test_batch_with_several_tiles_per_item_matches_the_oracle(adj):
         assert rel_err(xg, x) <= 1e-4, (i, rel_err(xg, x))
         Fo = p["oracle"].objective(x)
         assert abs(F[i] - Fo) <= 1e-5 * Fo, (i, F[i], Fo)
+    assert adj.device_status() == 0
+
+
+def test_batch_with_several_tiles_per_item_matches_one_problem_at_a_time(adj):
+    """Eight 1048 x 984 problems: the W level-1 stage slot holds 8 x 1023
+    tiles, over 16 per CTA of a full GPU, so the engine hands out its tiles
+    two per item (the last item of each problem one).  After 8 iterations
+    the engine's iterates equal fista_step's (one problem at a time, the
+    per-level kernels) within float32 tolerance, and the batch needs fewer
+    items per iteration than the eight problems batched one by one."""
+    mix = [(1048, 984, 3, w, mode, 9, 1.5, mode, "adjoint")
+           for w, mode in (("cdf97", "sym"), ("db2", "per"), ("db4", "sym"), ("cdf97", "zero"))] * 2
+    probs = _problems(adj, mix, seed=1400)
+    # alone, a problem's stages keep one tile per item
+    single = sum(adj.FistaBatch([p["fista"]]).info()["items_per_iteration"] for p in probs)
+    batch = adj.FistaBatch([p["fista"] for p in probs])
+    assert batch.info()["items_per_iteration"] < single
+    batch.reset()
+    batch.run(8)
+    torch.cuda.synchronize()
+    got = [p["fista"].x.clone() for p in probs]
+    for i, p in enumerate(probs):
+        f = p["fista"]
+        f.reset()
+        for _ in range(8):
+            f.step()
+        torch.cuda.synchronize()
+        r = float((got[i] - f.x).norm() / f.x.norm())
+        assert r <= 1e-5, (i, r)
     assert adj.device_status() == 0
 
 
