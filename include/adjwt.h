@@ -311,10 +311,13 @@ int fista_step(const adjwt_fista_problem* prob, adjwt_fista_state* state, void* 
 /* Batched FISTA engine (the batching extension; the paper solves one
  * problem at a time).  Many independent problems (Eq. 1, each with its own
  * plans, observation, lambda, L_f and gradient mode) advance `iters` FISTA
- * iterations in ONE persistent kernel launch: every (problem, stage, tile)
- * is an item (stages: the momentum update, W level J..1, the fused
- * R^*(R u - b), W^* + prox level 1..J; tiles of 32 x 32 wavelet outputs and
- * 64 x 64 blur outputs), numbered stage-major across problems and taken by
+ * iterations in ONE persistent kernel launch: the work is cut into items of
+ * one stage of one problem (stages: the momentum update, W level J..1, the
+ * fused R^*(R u - b), W^* + prox level 1..J; tiles of 32 x 32 wavelet
+ * outputs and 32 x 64 blur outputs, 64 x 64 under SYM with non-palindromic
+ * taps; an item is one tile, or two to four consecutive tiles when the
+ * batch holds far more tiles than the launch has CTAs), numbered
+ * stage-major across problems and taken by
  * the CTAs in order; a stage starts once the previous stage of its problem
  * is done.  Waits are bounded (ADJWT_ERR_TIMEOUT in the device status word;
  * the launch then drains).  The objective F(x_k) of every problem runs as a
