@@ -287,85 +287,85 @@ __global__ void __launch_bounds__(kEngineThreads, 3) k_fista_engine(const Engine
     __syncthreads();
     if (!s_word[1]) break;
     for (int q = 0; q < I.ntl; ++q) {
-    if (q > 0) __syncthreads();  // the previous tile is done with shared memory
-    const int tile = I.tile + q;
-    const int ty = tile / I.tiles_c, tx = tile - ty * I.tiles_c;
-    switch (I.kind) {
-      case kMom:
-        if (tid == 0) {
-          // device-resident momentum (the method cited in Sec. I-B):
-          // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, beta_k = (t_k - 1) / t_{k+1}
-          double* m = e.prob[I.problem].mom;
-          const double t = __ldcg(m);
-          const double t1 = 0.5 * (1.0 + sqrt(__dadd_rn(1.0, __dmul_rn(4.0 * t, t))));
-          m[1] = (t - 1.0) / t1;
-          m[0] = t1;
+      if (q > 0) __syncthreads();  // the previous tile is done with shared memory
+      const int tile = I.tile + q;
+      const int ty = tile / I.tiles_c, tx = tile - ty * I.tiles_c;
+      switch (I.kind) {
+        case kMom:
+          if (tid == 0) {
+            // device-resident momentum (the method cited in Sec. I-B):
+            // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, beta_k = (t_k - 1) / t_{k+1}
+            double* m = e.prob[I.problem].mom;
+            const double t = __ldcg(m);
+            const double t1 = 0.5 * (1.0 + sqrt(__dadd_rn(1.0, __dmul_rn(4.0 * t, t))));
+            m[1] = (t - 1.0) / t1;
+            m[0] = t1;
+          }
+          break;
+        case kSyn:
+          with_L(I.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
+          break;
+        case kGat: {
+          const int64_t idx = (int64_t)tile * kGatherPixels + tid;
+          if (idx < (int64_t)s_args.syn.Nr * s_args.syn.Nc) {
+            const int tr = static_cast<int>(idx / s_args.syn.Nc);
+            const int tc = static_cast<int>(idx - (int64_t)tr * s_args.syn.Nc);
+            with_L(I.param, [&](auto Lc) { engine_gat<decltype(Lc)::value>(s_args.syn, tr, tc); });
+          }
+          break;
         }
-        break;
-      case kSyn:
-        with_L(I.param, [&](auto Lc) { engine_syn<decltype(Lc)::value>(s_args.syn, ty, tx, dyn); });
-        break;
-      case kGat: {
-        const int64_t idx = (int64_t)tile * kGatherPixels + tid;
-        if (idx < (int64_t)s_args.syn.Nr * s_args.syn.Nc) {
-          const int tr = static_cast<int>(idx / s_args.syn.Nc);
-          const int tc = static_cast<int>(idx - (int64_t)tr * s_args.syn.Nc);
-          with_L(I.param, [&](auto Lc) { engine_gat<decltype(Lc)::value>(s_args.syn, tr, tc); });
+        case kAna: {
+          float l1 = 0.0f;
+          with_L(I.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
+          if (I.part >= 0) {
+            const double tot = block_sum<kEngineThreads>((double)l1, red);
+            if (tid == 0) e.prob[I.problem].parts[I.part + tile] = tot;
+          }
+          break;
         }
-        break;
-      }
-      case kAna: {
-        float l1 = 0.0f;
-        with_L(I.param, [&](auto Lc) { l1 = engine_ana<decltype(Lc)::value>(s_args.ana, ty, tx, dyn); });
-        if (I.part >= 0) {
-          const double tot = block_sum<kEngineThreads>((double)l1, red);
+        case kBlur: {
+          float sq = 0.0f;
+          with_R(I.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
+          if (I.part >= 0) {
+            const double tot = block_sum<kEngineThreads>((double)sq, red);
+            if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
+          }
+          break;
+        }
+        case kBlurW: {
+          const BlurWinArgs* w = &e.blurw[I.args];
+          float sq = 0.0f;
+          with_R(I.param, [&](auto Rc) {
+            sq = engine_blur_window<decltype(Rc)::value>(s_args.blur, &w->umap, &w->bmap, ty, tx, dyn);
+          });
+          if (I.part >= 0) {
+            const double tot = block_sum<kEngineThreads>((double)sq, red);
+            if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
+          }
+          break;
+        }
+        case kL1: {
+          const L1Args la = l1args[I.args];
+          const int64_t i0 = (int64_t)tile * kL1Chunk;
+          float acc = 0.0f;
+          for (int64_t i = i0 + tid; i < la.n && i < i0 + kL1Chunk; i += kEngineThreads) acc += fabsf(__ldcg(la.x + i));
+          const double tot = block_sum<kEngineThreads>((double)acc, red);
           if (tid == 0) e.prob[I.problem].parts[I.part + tile] = tot;
+          break;
         }
-        break;
+        case kSum:
+          if (tid == 0) {
+            // F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1, partials added in a fixed order
+            const ProbDev pd = e.prob[I.problem];
+            double r = 0.0, l1 = 0.0;
+            for (int i = 0; i < pd.nblur; ++i) r += __ldcg(pd.parts + i);
+            for (int i = 0; i < pd.nl1; ++i) l1 += __ldcg(pd.parts + pd.nblur + i);
+            e.objectives[I.problem] = r + pd.lambda * l1;
+          }
+          break;
+        default:
+          break;
       }
-      case kBlur: {
-        float sq = 0.0f;
-        with_R(I.param, [&](auto Rc) { sq = engine_blur<decltype(Rc)::value>(s_args.blur, ty, tx, dyn, &s_border); });
-        if (I.part >= 0) {
-          const double tot = block_sum<kEngineThreads>((double)sq, red);
-          if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
-        }
-        break;
-      }
-      case kBlurW: {
-        const BlurWinArgs* w = &e.blurw[I.args];
-        float sq = 0.0f;
-        with_R(I.param, [&](auto Rc) {
-          sq = engine_blur_window<decltype(Rc)::value>(s_args.blur, &w->umap, &w->bmap, ty, tx, dyn);
-        });
-        if (I.part >= 0) {
-          const double tot = block_sum<kEngineThreads>((double)sq, red);
-          if (tid == 0) e.prob[I.problem].parts[I.part + tile] = 0.5 * tot;
-        }
-        break;
-      }
-      case kL1: {
-        const L1Args la = l1args[I.args];
-        const int64_t i0 = (int64_t)tile * kL1Chunk;
-        float acc = 0.0f;
-        for (int64_t i = i0 + tid; i < la.n && i < i0 + kL1Chunk; i += kEngineThreads) acc += fabsf(__ldcg(la.x + i));
-        const double tot = block_sum<kEngineThreads>((double)acc, red);
-        if (tid == 0) e.prob[I.problem].parts[I.part + tile] = tot;
-        break;
-      }
-      case kSum:
-        if (tid == 0) {
-          // F(x) = 1/2 ||R W x - b||^2 + lambda ||x||_1, partials added in a fixed order
-          const ProbDev pd = e.prob[I.problem];
-          double r = 0.0, l1 = 0.0;
-          for (int i = 0; i < pd.nblur; ++i) r += __ldcg(pd.parts + i);
-          for (int i = 0; i < pd.nl1; ++i) l1 += __ldcg(pd.parts + pd.nblur + i);
-          e.objectives[I.problem] = r + pd.lambda * l1;
-        }
-        break;
-      default:
-        break;
-    }
     }
     cur_st = st;
     if (tid == 0) {
