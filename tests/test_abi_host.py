@@ -367,3 +367,48 @@ def test_tma_cta_cap_validation(lib):
         assert lib.adjwt_wt_plan_tma_ctas(h, 0, 1, None) == -1
     finally:
         lib.adjwt_wt_plan_destroy(h)
+
+
+def test_fista_batch_entry_validation(lib):
+    """The batched engine's entry points reject bad calls on the host, before
+    any device memory is touched: NULL handles and arrays, counts outside
+    1..65535, a problem without plans, and plans of different images (a
+    zeroed host buffer stands in for a blur plan of an empty image; fake
+    device addresses are never dereferenced)."""
+    from paper_1707_02018_gb300._lib import FistaProblem
+    rc, wt = _plan(lib, 64, 48, 2, 1, 3)   # db2, PER: no boundary tables to upload
+    assert rc == 0
+    zero_plan = (C.c_char * 4096)()
+    R = C.cast(zero_plan, C.c_void_p)
+    a, ws = 0x10000000, 0x30000000
+    probs = (FistaProblem * 2)(FistaProblem(wt, R, a, 0.01, 2.0, 0), FistaProblem(wt, R, a, 0.01, 2.0, 0))
+    xs = (C.c_void_p * 2)(a, a + 4096)
+    ys = (C.c_void_p * 2)(a + 8192, a + 12288)
+    h = C.c_void_p(0x1234)
+    try:
+        assert lib.adjwt_fista_batch_workspace_size(0, probs) == 0
+        assert lib.adjwt_fista_batch_workspace_size(2, None) == 0
+        create = lib.adjwt_fista_batch_create
+        assert create(None, 2, probs, xs, ys, ws, 1 << 30) == -1             # no output handle
+        assert create(C.byref(h), 0, probs, xs, ys, ws, 1 << 30) == -1       # empty batch
+        assert h.value is None                                                # cleared on failure
+        assert create(C.byref(h), 65536, probs, xs, ys, ws, 1 << 30) == -1   # too many problems
+        assert create(C.byref(h), 2, None, xs, ys, ws, 1 << 30) == -1        # no problems
+        assert create(C.byref(h), 2, probs, None, ys, ws, 1 << 30) == -1     # no x array
+        assert create(C.byref(h), 2, probs, xs, None, ws, 1 << 30) == -1     # no y array
+        assert create(C.byref(h), 2, probs, xs, ys, ws, 1 << 30) == -2       # blur plan of another image
+        probs[1].wt = None
+        assert lib.adjwt_fista_batch_workspace_size(2, probs) == 0
+        probs[0].blur = None
+        assert create(C.byref(h), 2, probs, xs, ys, ws, 1 << 30) == -1      # problem 0 without a blur plan
+        assert h.value is None
+        n = C.c_int()
+        assert lib.adjwt_fista_batch_info(None, C.byref(n), None, None) == -1
+        assert lib.adjwt_fista_batch_run(None, 1, None) == -1
+        assert lib.adjwt_fista_batch_objective(None, a, None) == -1
+        assert lib.adjwt_fista_batch_reset(None, None) == -1
+        assert lib.adjwt_fista_batch_set_iteration(None, 3, None) == -1
+        assert lib.adjwt_fista_batch_wait_selftest(None, None) == -1
+        lib.adjwt_fista_batch_destroy(None)
+    finally:
+        lib.adjwt_wt_plan_destroy(wt)
