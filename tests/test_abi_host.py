@@ -412,3 +412,52 @@ def test_fista_batch_entry_validation(lib):
         lib.adjwt_fista_batch_destroy(None)
     finally:
         lib.adjwt_wt_plan_destroy(wt)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="fake-pointer validation runs on the host only")
+def test_more_entry_validation(lib):
+    """Operators, FISTA helpers and the trace pool reject bad calls before any
+    launch: NULL plans and problems, shapes out of range, a non-finite or
+    negative threshold, trace indices outside the records.  Fake device
+    addresses are never dereferenced."""
+    from paper_1707_02018_gb300._lib import FistaProblem
+    a, ws = 0x10000000, 0x30000000
+    assert lib.adjwt_version() == 1
+    assert lib.blur_normal(None, a, a, a, None, None, 0, None) == -1
+    assert lib.wt_analysis(None, a, a, ws, 1 << 20, None) == -1
+    assert lib.conv_residual(-1, 10, 3, a, a, a, a, None) == -2
+    assert lib.conv_residual(1, 0, 3, a, a, a, a, None) == -2
+    assert lib.conv_residual(70000, 10, 3, a, a, a, a, None) == -2
+    assert lib.conv_residual(0, 10, 3, None, None, None, None, None) == 0   # empty batch: nothing to do
+    assert lib.bce_gradient(0, 10, 3, a, a, a, 0.1, 0.5, a, a, ws, 1 << 20, None) == -2
+    assert lib.bce_gradient(2, 10, 5000, a, a, a, 0.1, 0.5, a, a, ws, 1 << 20, None) == -2   # k above 4096
+    assert lib.bce_gradient(2, 10, 3, a, a, a, 0.1, 0.0, a, a, ws, 1 << 20, None) == -1      # delta = 0
+    assert lib.bce_gradient(2, 10, 3, a, a, a, -1.0, 0.5, a, a, ws, 1 << 20, None) == -1     # lambda_tv < 0
+    assert lib.adjwt_soft_threshold(-1, a, 0.1, a, None) == -2
+    assert lib.adjwt_soft_threshold(0, None, 0.1, None, None) == 0
+    assert lib.adjwt_soft_threshold(8, None, 0.1, a, None) == -1
+    assert lib.adjwt_soft_threshold(8, a, -0.5, a, None) == -1
+    assert lib.adjwt_soft_threshold(8, a, float("nan"), a, None) == -1
+    out = C.c_double()
+    assert lib.fista_step_device(None, a, a, ws, 1 << 20, None, None) == -1
+    assert lib.adjwt_fista_objective(None, a, ws, 1 << 20, C.byref(out), None) == -1
+    assert lib.adjwt_fista_lipschitz(None, a, 5, ws, 1 << 20, C.byref(out), None) == -1
+    assert lib.adjwt_fista_device_reset(None, ws, 1 << 20, None) == -1
+    rc, wt = _plan(lib, 64, 48, 2, 1, 3)   # db2, PER
+    assert rc == 0
+    zero_plan = (C.c_char * 4096)()
+    try:
+        prob = FistaProblem(wt, C.cast(zero_plan, C.c_void_p), a, 0.01, 2.0, 0)
+        assert lib.fista_step_device(C.byref(prob), a, a, ws, 1 << 20, None, None) == -2        # plans of two images
+        assert lib.adjwt_fista_lipschitz(C.byref(prob), a, 5, ws, 1 << 20, C.byref(out), None) == -2
+        assert lib.adjwt_fista_device_reset(C.byref(prob), ws, 1 << 20, None) == -2
+        assert lib.wt_analysis(wt, None, a, ws, 1 << 20, None) == -1                            # NULL image
+    finally:
+        lib.adjwt_wt_plan_destroy(wt)
+    n = lib.adjwt_trace_count()
+    assert n >= 0
+    name, tag, ms = C.c_char_p(), C.c_int(), C.c_float()
+    assert lib.adjwt_trace_get(-1, C.byref(name), C.byref(tag), C.byref(ms)) == -1
+    assert lib.adjwt_trace_get(n, C.byref(name), C.byref(tag), C.byref(ms)) == -1
+    assert lib.adjwt_trace_span(0, n, C.byref(ms)) == -1
+    assert lib.adjwt_trace_span(0, 0, None) == -1
